@@ -1,0 +1,142 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module is shared by the tests, the benchmark and the oracle checks.  It
+draws locations and values only; it holds none of the MRA arithmetic (no
+partition, no remainder covariance, no likelihood).  Values z are draws of a
+zero-mean Gaussian process with the exponential covariance
+sigma2 * exp(-d / beta) plus a N(0, tau2) nugget, made either exactly (dense
+Cholesky, small n) or by circulant embedding on a regular grid (large n).
+
+Workloads (sizes follow the configurations the library is measured on):
+
+* ``small``    n=4,096 i.i.d. uniform on [0,1]^2, exact GP (sigma2=1, beta=0.1,
+               tau2=0.05); tree M=3, J=4, r=16.
+* ``grid``     n=131,072 on a jittered 382x382 grid with 10% of the cells
+               dropped at random and a random trim to exactly n; GP by
+               circulant embedding on the grid (sigma2=1, beta=0.05,
+               tau2=0.01), values carried to the jittered points; M=7, J=4,
+               r=32 (30 knots per region).  Stand-in for the paper's small
+               MODIS scene (a gridded satellite field with missing cells).
+* ``clustered`` n=2,097,152: 70% in 8 Gaussian clusters (sd 0.03, centres
+               uniform), 30% uniform; GP by circulant embedding on a 1024^2 grid
+               over the bounding box, nearest-cell value; M=9, J=4, r=32; a
+               4x4x4 log-spaced theta grid.  Stand-in for the skewed leaf
+               counts of the AMSR data.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+WORKLOADS = {
+    "small": dict(n=4096, M=3, J=4, r=16, theta=(1.0, 0.1, 0.05)),
+    "grid": dict(n=131072, M=7, J=4, r=32, theta=(1.0, 0.05, 0.01)),
+    "clustered": dict(n=2097152, M=9, J=4, r=32, theta=(1.0, 0.05, 0.01)),
+}
+
+SEED_BASE = 1905
+
+
+def _exp_cov(d, sigma2, beta):
+    return sigma2 * np.exp(-d / beta)
+
+
+def gp_exact(x, y, sigma2, beta, tau2, rng):
+    """Exact zero-mean GP draw at (x, y) by a dense Cholesky, plus nugget."""
+    d = np.sqrt((x[:, None] - x[None, :]) ** 2 + (y[:, None] - y[None, :]) ** 2)
+    C = _exp_cov(d, sigma2, beta)
+    C[np.diag_indices_from(C)] += 1e-10
+    L = np.linalg.cholesky(C)
+    return L @ rng.standard_normal(len(x)) + math.sqrt(tau2) * rng.standard_normal(len(x))
+
+
+def gp_grid(nx, ny, hx, hy, sigma2, beta, rng):
+    """GP on an nx x ny grid of spacing (hx, hy) by circulant embedding on the
+    2nx x 2ny torus; negative eigenvalues (if any) are clipped to zero."""
+    Nx, Ny = 2 * nx, 2 * ny
+    ix = np.arange(Nx)
+    iy = np.arange(Ny)
+    dx = np.minimum(ix, Nx - ix) * hx
+    dy = np.minimum(iy, Ny - iy) * hy
+    d = np.sqrt(dx[:, None] ** 2 + dy[None, :] ** 2)
+    c = _exp_cov(d, sigma2, beta)
+    lam = np.fft.fft2(c).real
+    lam = np.maximum(lam, 0.0)
+    w = rng.standard_normal((Nx, Ny)) + 1j * rng.standard_normal((Nx, Ny))
+    f = np.fft.fft2(np.sqrt(lam / (Nx * Ny)) * w)
+    return f.real[:nx, :ny]
+
+
+def small(seed: int = SEED_BASE + 1, n: int = 4096):
+    rng = np.random.default_rng(seed)
+    x = rng.random(n)
+    y = rng.random(n)
+    s2, b, t2 = WORKLOADS["small"]["theta"]
+    z = gp_exact(x, y, s2, b, t2, rng)
+    return dict(x=x, y=y, z=z, M=3, J=4, r=16, theta=np.array([[s2, b, t2]]))
+
+
+def grid(seed: int = SEED_BASE + 2, n: int = 131072):
+    rng = np.random.default_rng(seed)
+    G = int(math.ceil(math.sqrt(n / 0.9)))
+    h = 1.0 / G
+    s2, b, t2 = WORKLOADS["grid"]["theta"]
+    field = gp_grid(G, G, h, h, s2, b, rng)
+    cells = np.arange(G * G)
+    kept = rng.permutation(cells)[: int(round(0.9 * G * G))]
+    if len(kept) < n:
+        raise ValueError("grid too small for n")
+    kept = np.sort(rng.permutation(kept)[:n])
+    i, j = kept // G, kept % G
+    x = (i + 0.5 + rng.uniform(-0.5, 0.5, n)) * h
+    y = (j + 0.5 + rng.uniform(-0.5, 0.5, n)) * h
+    z = field[i, j] + math.sqrt(t2) * rng.standard_normal(n)
+    return dict(x=x, y=y, z=z, M=7, J=4, r=32, theta=np.array([[s2, b, t2]]))
+
+
+def theta_grid_4x4x4():
+    """64 theta on a log-spaced 4x4x4 grid: sigma2 in [0.5, 2], beta in
+    [0.02, 0.2], tau2 in [0.005, 0.05]."""
+    s = np.geomspace(0.5, 2.0, 4)
+    b = np.geomspace(0.02, 0.2, 4)
+    t = np.geomspace(0.005, 0.05, 4)
+    S, B, T = np.meshgrid(s, b, t, indexing="ij")
+    return np.stack([S.ravel(), B.ravel(), T.ravel()], axis=1)
+
+
+def clustered(seed: int = SEED_BASE + 3, n: int = 2097152, grid_n: int = 1024):
+    rng = np.random.default_rng(seed)
+    nc = int(round(0.7 * n))
+    centres = rng.random((8, 2))
+    lab = rng.integers(0, 8, nc)
+    pc = centres[lab] + 0.03 * rng.standard_normal((nc, 2))
+    pu = rng.random((n - nc, 2))
+    p = np.concatenate([pc, pu])
+    p = p[rng.permutation(n)]
+    x, y = p[:, 0].copy(), p[:, 1].copy()
+    s2, b, t2 = WORKLOADS["clustered"]["theta"]
+    x0, x1, y0, y1 = x.min(), x.max(), y.min(), y.max()
+    hx = (x1 - x0) / (grid_n - 1)
+    hy = (y1 - y0) / (grid_n - 1)
+    field = gp_grid(grid_n, grid_n, hx, hy, s2, b, rng)
+    ix = np.clip(np.rint((x - x0) / hx).astype(np.int64), 0, grid_n - 1)
+    iy = np.clip(np.rint((y - y0) / hy).astype(np.int64), 0, grid_n - 1)
+    z = field[ix, iy] + math.sqrt(t2) * rng.standard_normal(n)
+    return dict(x=x, y=y, z=z, M=9, J=4, r=32, theta=theta_grid_4x4x4())
+
+
+def uniform(n: int, seed: int, sigma2=1.0, beta=0.1, tau2=0.05, exact=True):
+    """Small uniform draw for tests (exact GP values when exact=True)."""
+    rng = np.random.default_rng(seed)
+    x = rng.random(n)
+    y = rng.random(n)
+    if exact and n <= 6000:
+        z = gp_exact(x, y, sigma2, beta, tau2, rng)
+    else:
+        z = rng.standard_normal(n)
+    return x, y, z
+
+
+def make(name: str, **kw):
+    return {"small": small, "grid": grid, "clustered": clustered}[name](**kw)
