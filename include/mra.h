@@ -1,0 +1,180 @@
+/*
+ * mra.h -- C ABI of the GB300 (sm_103a) multi-resolution approximation (MRA)
+ * Gaussian-process log-likelihood library (libmra.so).
+ *
+ * The method (Huang, Blake & Hammerling, "Pushing the Limit: A Hybrid
+ * Parallel Implementation of the Multi-resolution Approximation for Massive
+ * Data", Sec. 1.1-1.2): the domain is split recursively into J (2 or 4)
+ * sub-regions for M levels; every region above the finest level carries
+ * r_hat = ceil(sqrt r) * floor(r / ceil(sqrt r)) knots on a regular grid; the
+ * knots of a finest-level region are the observations inside it.  The process
+ * is a sum of predictive processes on the remainder covariances C_1 .. C_M of
+ * Sec. 1.1.  mra_loglik evaluates log N(z; 0, Sigma_MRA + tau2 I) at
+ * theta = (sigma2, beta, tau2) for the exponential covariance
+ * sigma2 * exp(-|s1 - s2| / beta) ("likelihood" mode, Sec. 2.2.5; sill ALPHA,
+ * range BETA, nugget TAU of the user-parameter table, Sec. 2.2.3, with TAU read
+ * as the nugget variance tau2).
+ *
+ * Conventions for every entry point:
+ *   - Host pointers are plain CPU memory and are only read during the call
+ *     (the library copies what it keeps).  "Device" pointers are CUDA global
+ *     memory on the context's device.
+ *   - A mra_ctx owns all the device memory it allocates; mra_free releases it.
+ *   - A context is not reentrant: calls on one context must not overlap.
+ *     Several contexts may coexist.
+ *   - Every entry point returns a mra_status; on failure mra_last_error gives a
+ *     one-line reason.  No entry point aborts, traps or prints.
+ */
+#ifndef MRA_H
+#define MRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mra_ctx mra_ctx;
+
+typedef enum {
+    MRA_OK = 0,
+    MRA_EINVAL = 1,    /* bad argument: sizes, J not 2/4, theta not positive, ... */
+    MRA_ENOMEM = 2,    /* a host or device allocation failed, or the budget is too small */
+    MRA_ENOTPD = 3,    /* a Cholesky factor met a non-positive pivot (singular prior) */
+    MRA_ECUDA = 4,     /* a CUDA runtime call failed (message in mra_last_error) */
+    MRA_ETIMEDOUT = 5, /* reserved: a bounded device wait ran out */
+    MRA_EEMPTY = 6     /* no observation left after the eliminations of Sec. 1.2 */
+} mra_status;
+
+enum { MRA_FP64 = 0, MRA_MIXED = 1 };
+
+typedef struct {
+    double offset;     /* knot offset f of Sec. 1.2; < 0 selects the paper's default e/100 */
+    int dedup;         /* ELIMINATION_DUPLICATES_FLAG: drop repeated locations, keep the first */
+    int precision;     /* MRA_FP64 (default) or MRA_MIXED */
+    int device;        /* CUDA device ordinal; -1 builds the partition on the host only
+                          (stats and tree queries work, likelihood calls give MRA_EINVAL) */
+    int max_batch;     /* theta evaluated per device pass; 0 = choose from hbm_budget */
+    size_t hbm_budget; /* bytes of per-theta scratch the context may hold; 0 = 60% of free HBM */
+} mra_opts;
+
+typedef struct {
+    int64_t n_in, n_used;       /* observations given / used */
+    int64_t n_nan, n_dup, n_knot; /* dropped: NaN value, duplicate location, on a coarse knot */
+    int64_t n_regions, n_leaves;
+    int M, J, r, r_hat;
+    int64_t max_leaf, empty_leaves;
+    int max_batch;
+    double flops_per_theta;     /* algorithmic FP operations of one evaluation (r_hat, not padding) */
+    double cov_evals_per_theta; /* covariance-function evaluations of one evaluation */
+    size_t device_bytes;        /* device memory held by the context */
+    int launches_per_pass;      /* kernels launched by the last device pass (one batch chunk) */
+    double flops_by_kernel[8];  /* flops_per_theta split by kernel family, in the order
+                                   prior, leafbasis, leafpost, leafpost_big, leafgram, up, root */
+} mra_stats_t;
+
+typedef struct {
+    char name[24];    /* kernel family: prior, leafbasis, leafpost, leafpost_big, leafgram, up, root */
+    int64_t launches; /* launches recorded since the last read */
+    double ms;        /* summed device time of those launches (CUDA events on the call's stream) */
+} mra_kernel_time;
+
+/* Fill *opt with the defaults (offset e/100, no dedup, FP64, device 0, auto batch). */
+void mra_default_opts(mra_opts *opt);
+
+/*
+ * mra_build -- partition, knots and observation layout (Sec. 1.2).
+ *   lon, lat, z : host arrays of n doubles (locations and values).  A NaN value
+ *                 marks a prediction site and is dropped; non-finite locations
+ *                 give MRA_EINVAL.
+ *   M >= 1 levels, J in {2, 4}, r >= 1 knots requested (r_hat placed).
+ *   The domain is the bounding box with its top and right edges pushed out by
+ *   1% of the extent; regions are half-open [x0,x1) x [y0,y1); J = 4 halves both
+ *   sides, J = 2 halves the longer side (ties: x).  Observations that sit exactly
+ *   on a knot of levels 1..M-1 are dropped; duplicates too when opt->dedup.
+ *   opt may be NULL (defaults).  On success *out owns a device copy of the tree
+ *   and of the used observations in leaf order; on failure *out is NULL and
+ *   mra_last_error(NULL) gives the reason.
+ *   Errors: MRA_EINVAL (sizes, J, r, M, offset outside [0, 0.5), degenerate
+ *   domain), MRA_EEMPTY (nothing left), MRA_ENOMEM, MRA_ECUDA.
+ */
+mra_status mra_build(const double *lon, const double *lat, const double *z, int64_t n, int M,
+                     int J, int r, const mra_opts *opt, mra_ctx **out);
+
+/*
+ * mra_loglik -- log-likelihood at a batch of theta (Sec. 2.2.5 "likelihood").
+ *   theta  : host, batch x 3 doubles, row b = (sigma2, beta, tau2), all > 0.
+ *   loglik : host, batch doubles, written for every b; NaN where theta b is
+ *            invalid or a factorisation failed.
+ *   Returns the first non-OK per-theta status (MRA_EINVAL, MRA_ENOTPD) or a
+ *   call-level error.  Synchronous.
+ */
+mra_status mra_loglik(mra_ctx *ctx, const double *theta, int batch, double *loglik);
+
+/*
+ * mra_loglik_device -- as mra_loglik with device pointers, enqueued on
+ *   `stream` (a cudaStream_t; NULL = legacy default stream) and not synchronised.
+ *   theta_dev : device, batch x 3 doubles.  loglik_dev : device, batch doubles.
+ *   status_dev: optional device int array of batch entries (per-theta mra_status),
+ *               may be NULL.
+ *   Returns MRA_OK once every kernel is enqueued; per-theta failures only show
+ *   in loglik_dev (NaN) and status_dev.
+ */
+mra_status mra_loglik_device(mra_ctx *ctx, const double *theta_dev, int batch, double *loglik_dev,
+                             int *status_dev, void *stream);
+
+/* Select MRA_FP64 or MRA_MIXED for later calls. */
+mra_status mra_set_precision(mra_ctx *ctx, int precision);
+
+/* Counts, sizes and the algorithmic work of one evaluation. */
+mra_status mra_stats(const mra_ctx *ctx, mra_stats_t *out);
+
+/*
+ * mra_tree_export -- the built partition, for inspection and tests.
+ *   Any pointer may be NULL.  Sizes: kx, ky: (n_regions - n_leaves) * r_hat
+ *   knots of levels 1..M-1 (global region id order, knot index q*nx + p);
+ *   leaf_off: n_leaves + 1 offsets into the leaf-ordered observations;
+ *   perm: n_used input indices in leaf order; bounds: 4 * n_regions doubles
+ *   (x0, x1, y0, y1).  Region ids: level 1 first, children of (m, i) are
+ *   (m+1, J i + j).
+ */
+mra_status mra_tree_export(const mra_ctx *ctx, double *kx, double *ky, int64_t *leaf_off,
+                           int64_t *perm, double *bounds);
+
+/*
+ * mra_region_terms -- per-region partial terms at one theta (host pointers,
+ *   n_regions doubles each): d_R = log-determinant and u_R = quadratic form of
+ *   the data below R after R's level is integrated out (leaves: log|V| and
+ *   z'V^{-1}z), and log|W^m_R| = log|C_m(Q_R, Q_R)| for regions above the
+ *   leaves (NaN at leaves).  loglik: host, 1 double.  Synchronous.
+ */
+mra_status mra_region_terms(mra_ctx *ctx, const double *theta, double *d, double *u,
+                            double *logdetW, double *loglik);
+
+/*
+ * mra_profile -- enable (1) or disable (0) per-kernel device timing: every
+ *   later launch is bracketed by two CUDA events recorded on the call's
+ *   stream.  Enabling clears the records.  Costs two event records per launch.
+ */
+mra_status mra_profile(mra_ctx *ctx, int enable);
+
+/*
+ * mra_profile_read -- wait for the recorded events, write up to cap entries
+ *   (one per kernel family that launched) into out (host), clear the records
+ *   and return the number of families (-1 on error).
+ */
+int mra_profile_read(mra_ctx *ctx, mra_kernel_time *out, int cap);
+
+/* Last error message of the context (never NULL).  With ctx == NULL: the reason
+ * the calling thread's last mra_build failed (mra_build returns no context on
+ * failure). */
+const char *mra_last_error(const mra_ctx *ctx);
+
+/* Release the context and all its device memory.  NULL is a no-op. */
+void mra_free(mra_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRA_H */

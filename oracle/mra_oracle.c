@@ -351,13 +351,19 @@ void oracle_tree_export(void *h, double *kx, double *ky, int64_t *leaf_off, int6
 /* ------------------------------------------------------- dense algebra -- */
 
 /* In-place lower Cholesky of the n x n row-major A (upper part left as is).
- * Returns 0, or -1 when a pivot is not positive. */
+ * Returns 0, or -1 when the matrix is singular: Sec. 1.2 notes that coincident
+ * knots make the covariance singular; in finite precision a pivot at or below
+ * O_SINGULAR times the largest diagonal entry of A is taken as singular. */
+#define O_SINGULAR 1e-12
 static int ochol(double *A, int n)
 {
+    double scale = 0.0;
+    for (int j = 0; j < n; j++)
+        if (A[j * n + j] > scale) scale = A[j * n + j];
     for (int j = 0; j < n; j++) {
         double s = A[j * n + j];
         for (int k = 0; k < j; k++) s -= A[j * n + k] * A[j * n + k];
-        if (!(s > 0.0)) return -1;
+        if (!(s > O_SINGULAR * scale)) return -1;
         double ljj = sqrt(s);
         A[j * n + j] = ljj;
         for (int i = j + 1; i < n; i++) {

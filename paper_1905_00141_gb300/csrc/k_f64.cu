@@ -1,0 +1,6 @@
+// FP64 instantiation of the MRA kernels (r_hat padded to 16 or 32).
+#include "mra_launch.cuh"
+namespace mra {
+MRA_INSTANTIATE(double, 16)
+MRA_INSTANTIATE(double, 32)
+} // namespace mra

@@ -1,0 +1,1064 @@
+// mra_api.cu -- the C ABI of libmra (include/mra.h): partition build on the
+// host, device layout, and the per-level launch sequence of one likelihood
+// evaluation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mra.h"
+#include "mra_internal.h"
+
+using namespace mra;
+
+namespace {
+
+const double kDefaultOffset = 2.718281828459045235360287 / 100.0; // e/100 (Sec. 1.2)
+
+// ------------------------------------------------------------ partition --
+// Sec. 1.2: bounding box pushed out by 1% at the top and right, half-open
+// regions, J = 4 quadrants or J = 2 halves of the longer side (decided per
+// level from the nominal side lengths, which halve exactly; ties cut x),
+// ceil(sqrt r) x floor(r / ceil(sqrt r)) knots at x0 + L (f + p (1-2f)/(n-1)).
+struct Partition {
+    int M = 0, J = 0, r = 0, nx = 0, ny = 0, R = 0;
+    double f = 0.0;
+    std::vector<int64_t> lvl_off; // [M+2], index m = first global id of level m
+    std::vector<double> bx0, bx1, by0, by1;
+    std::vector<char> cut_x;      // per level m < M (J = 2)
+    std::vector<double> kx, ky;   // [n_nonleaf * R]
+    std::vector<int64_t> leaf_off;
+    std::vector<double> sx, sy, sz;
+    std::vector<int64_t> perm;
+    int64_t n_in = 0, n_used = 0, n_nan = 0, n_dup = 0, n_knot = 0;
+    int64_t nreg() const { return lvl_off[M + 1]; }
+    int64_t nleaf() const { return lvl_off[M + 1] - lvl_off[M]; }
+    int64_t nnonleaf() const { return lvl_off[M]; }
+};
+
+int side_bars(int r)
+{
+    int a = 1;
+    while (a * a < r) a++;
+    return a;
+}
+
+void knot_grid(double x0, double x1, double y0, double y1, int nx, int ny, double f, double *kx, double *ky)
+{
+    const double Lx = x1 - x0, Ly = y1 - y0;
+    for (int q = 0; q < ny; q++) {
+        const double yq = ny > 1 ? y0 + Ly * (f + (double)q * (1.0 - 2.0 * f) / (double)(ny - 1)) : y0 + 0.5 * Ly;
+        for (int p = 0; p < nx; p++) {
+            kx[q * nx + p] = nx > 1 ? x0 + Lx * (f + (double)p * (1.0 - 2.0 * f) / (double)(nx - 1)) : x0 + 0.5 * Lx;
+            ky[q * nx + p] = yq;
+        }
+    }
+}
+
+mra_status build_partition(const double *x, const double *y, const double *z, int64_t n, int M, int J, int r,
+                           double f, int dedup, Partition &P, std::string &err)
+{
+    if (n < 0 || M < 1 || M > MRA_MAXM - 1 || (J != 2 && J != 4) || r < 1) {
+        err = "invalid n, M, J or r";
+        return MRA_EINVAL;
+    }
+    if (!(f >= 0.0 && f < 0.5)) {
+        err = "offset must lie in [0, 0.5)";
+        return MRA_EINVAL;
+    }
+    double total = 0.0, pw = 1.0;
+    for (int m = 1; m <= M; m++) {
+        total += pw;
+        pw *= J;
+    }
+    if (total > 268435456.0) {
+        err = "too many regions (J^M)";
+        return MRA_EINVAL;
+    }
+    for (int64_t i = 0; i < n; i++)
+        if (!std::isfinite(x[i]) || !std::isfinite(y[i])) {
+            err = "non-finite location";
+            return MRA_EINVAL;
+        }
+    P.M = M;
+    P.J = J;
+    P.r = r;
+    P.f = f;
+    P.nx = side_bars(r);
+    P.ny = r / P.nx;
+    P.R = P.nx * P.ny;
+    P.n_in = n;
+
+    std::vector<int64_t> idx;
+    idx.reserve((size_t)n);
+    for (int64_t i = 0; i < n; i++) {
+        if (std::isnan(z[i]))
+            P.n_nan++;
+        else
+            idx.push_back(i);
+    }
+    if (dedup && !idx.empty()) {
+        std::vector<int64_t> s(idx);
+        std::sort(s.begin(), s.end(), [&](int64_t a, int64_t b) {
+            if (x[a] != x[b]) return x[a] < x[b];
+            if (y[a] != y[b]) return y[a] < y[b];
+            return a < b;
+        });
+        std::vector<char> gone((size_t)n, 0);
+        for (size_t k = 1; k < s.size(); k++)
+            if (x[s[k]] == x[s[k - 1]] && y[s[k]] == y[s[k - 1]]) {
+                gone[(size_t)s[k]] = 1;
+                P.n_dup++;
+            }
+        std::vector<int64_t> kept;
+        kept.reserve(idx.size());
+        for (int64_t i : idx)
+            if (!gone[(size_t)i]) kept.push_back(i);
+        idx.swap(kept);
+    }
+    if (idx.empty()) {
+        err = "no observation left";
+        return MRA_EEMPTY;
+    }
+    double xmin = x[idx[0]], xmax = xmin, ymin = y[idx[0]], ymax = ymin;
+    for (int64_t i : idx) {
+        xmin = std::min(xmin, x[i]);
+        xmax = std::max(xmax, x[i]);
+        ymin = std::min(ymin, y[i]);
+        ymax = std::max(ymax, y[i]);
+    }
+    if (!(xmax > xmin) || !(ymax > ymin)) {
+        err = "degenerate domain (zero extent)";
+        return MRA_EINVAL;
+    }
+    P.lvl_off.assign((size_t)M + 2, 0);
+    int64_t cnt = 1;
+    for (int m = 1; m <= M; m++) {
+        P.lvl_off[(size_t)m + 1] = P.lvl_off[(size_t)m] + cnt;
+        cnt *= J;
+    }
+    const int64_t NR = P.nreg();
+    P.bx0.resize((size_t)NR);
+    P.bx1.resize((size_t)NR);
+    P.by0.resize((size_t)NR);
+    P.by1.resize((size_t)NR);
+    P.bx0[0] = xmin;
+    P.bx1[0] = xmax + 0.01 * (xmax - xmin);
+    P.by0[0] = ymin;
+    P.by1[0] = ymax + 0.01 * (ymax - ymin);
+    P.cut_x.assign((size_t)M + 1, 1);
+    double lx = P.bx1[0] - P.bx0[0], ly = P.by1[0] - P.by0[0];
+    for (int m = 1; m < M; m++) {
+        const bool cx = lx >= ly;
+        P.cut_x[(size_t)m] = cx;
+        if (J == 4) {
+            lx *= 0.5;
+            ly *= 0.5;
+        } else if (cx) {
+            lx *= 0.5;
+        } else {
+            ly *= 0.5;
+        }
+        for (int64_t g = P.lvl_off[(size_t)m]; g < P.lvl_off[(size_t)m + 1]; g++) {
+            const int64_t i = g - P.lvl_off[(size_t)m];
+            const int64_t c0 = P.lvl_off[(size_t)m + 1] + i * J;
+            const double X0 = P.bx0[(size_t)g], X1 = P.bx1[(size_t)g], Y0 = P.by0[(size_t)g], Y1 = P.by1[(size_t)g];
+            const double mx = 0.5 * (X0 + X1), my = 0.5 * (Y0 + Y1);
+            for (int j = 0; j < J; j++) {
+                double a0 = X0, a1 = X1, b0 = Y0, b1 = Y1;
+                if (J == 4) {
+                    (j & 1 ? a0 : a1) = mx;
+                    (j & 2 ? b0 : b1) = my;
+                } else if (cx) {
+                    (j ? a0 : a1) = mx;
+                } else {
+                    (j ? b0 : b1) = my;
+                }
+                P.bx0[(size_t)(c0 + j)] = a0;
+                P.bx1[(size_t)(c0 + j)] = a1;
+                P.by0[(size_t)(c0 + j)] = b0;
+                P.by1[(size_t)(c0 + j)] = b1;
+            }
+        }
+    }
+    const int64_t NK = P.nnonleaf();
+    P.kx.resize((size_t)(NK * P.R));
+    P.ky.resize((size_t)(NK * P.R));
+    for (int64_t g = 0; g < NK; g++)
+        knot_grid(P.bx0[(size_t)g], P.bx1[(size_t)g], P.by0[(size_t)g], P.by1[(size_t)g], P.nx, P.ny, f,
+                  &P.kx[(size_t)(g * P.R)], &P.ky[(size_t)(g * P.R)]);
+    if (NK > 0) {
+        std::vector<std::pair<double, double>> ks((size_t)(NK * P.R));
+        for (size_t k = 0; k < ks.size(); k++) ks[k] = {P.kx[k], P.ky[k]};
+        std::sort(ks.begin(), ks.end());
+        std::vector<int64_t> kept;
+        kept.reserve(idx.size());
+        for (int64_t i : idx) {
+            if (std::binary_search(ks.begin(), ks.end(), std::make_pair(x[i], y[i])))
+                P.n_knot++;
+            else
+                kept.push_back(i);
+        }
+        idx.swap(kept);
+    }
+    const int64_t NL = P.nleaf();
+    std::vector<int64_t> leaf(idx.size());
+    for (size_t k = 0; k < idx.size(); k++) {
+        const double a = x[idx[k]], b = y[idx[k]];
+        int64_t i = 0;
+        for (int m = 1; m < M; m++) {
+            const int64_t g = P.lvl_off[(size_t)m] + i;
+            const double mx = 0.5 * (P.bx0[(size_t)g] + P.bx1[(size_t)g]);
+            const double my = 0.5 * (P.by0[(size_t)g] + P.by1[(size_t)g]);
+            int j;
+            if (J == 4)
+                j = (a >= mx) | ((b >= my) << 1);
+            else
+                j = P.cut_x[(size_t)m] ? (a >= mx) : (b >= my);
+            i = i * J + j;
+        }
+        leaf[k] = i;
+    }
+    P.leaf_off.assign((size_t)NL + 1, 0);
+    for (int64_t l : leaf) P.leaf_off[(size_t)l + 1]++;
+    for (int64_t i = 0; i < NL; i++) P.leaf_off[(size_t)i + 1] += P.leaf_off[(size_t)i];
+    std::vector<int64_t> pos(P.leaf_off.begin(), P.leaf_off.end() - 1);
+    P.n_used = (int64_t)idx.size();
+    P.sx.resize(idx.size());
+    P.sy.resize(idx.size());
+    P.sz.resize(idx.size());
+    P.perm.resize(idx.size());
+    for (size_t k = 0; k < idx.size(); k++) {
+        const int64_t p = pos[(size_t)leaf[k]]++;
+        P.sx[(size_t)p] = x[idx[k]];
+        P.sy[(size_t)p] = y[idx[k]];
+        P.sz[(size_t)p] = z[idx[k]];
+        P.perm[(size_t)p] = idx[k];
+    }
+    if (P.n_used == 0) {
+        err = "no observation left";
+        return MRA_EEMPTY;
+    }
+    return MRA_OK;
+}
+
+} // namespace
+
+// --------------------------------------------------------------- context --
+struct mra_ctx {
+    Partition P;
+    int RP = 0, lgJ = 0, precision = MRA_FP64, device = 0;
+    std::string err;
+    // device tree
+    double *d_kx = nullptr, *d_ky = nullptr, *d_sx = nullptr, *d_sy = nullptr, *d_sz = nullptr;
+    int64_t *d_leaf_off = nullptr;
+    Chunk *d_chunks = nullptr;
+    int nchunks = 0;
+    int64_t *d_leaves32 = nullptr, *d_leaves64 = nullptr;
+    int nl32 = 0, nl64 = 0, nmax64 = 64;
+    BigLeaf *d_big = nullptr;
+    int nbig = 0;
+    int64_t vbig_elems = 0;
+    // per-theta scratch: one allocation for `cap` theta, sized for FP64
+    int cap = 0;     // theta the scratch currently holds
+    int max_cap = 1; // theta per device pass allowed by the memory budget
+    unsigned char *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    size_t per_theta_bytes = 0;
+    int *d_status = nullptr;
+    double *d_theta_stage = nullptr, *d_ll_stage = nullptr;
+    int stage_cap = 0;
+    double *d_reg_du = nullptr, *d_reg_lw = nullptr;
+    size_t bytes_held = 0;
+    // optional per-kernel device timing (events around every launch)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+    int launches_last = 0;
+    int64_t max_leaf = 0, empty_leaves = 0;
+    double flops = 0.0, covs = 0.0;
+    double flops_k[8] = {0};
+};
+
+namespace {
+
+mra_status cuda_fail(mra_ctx *c, cudaError_t e, const char *what)
+{
+    c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return MRA_ECUDA;
+}
+
+template <typename T>
+mra_status dev_upload(mra_ctx *c, T **dst, const T *src, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)dst, count * sizeof(T));
+    if (e != cudaSuccess) {
+        c->err = "cudaMalloc failed for the tree";
+        return MRA_ENOMEM;
+    }
+    c->bytes_held += count * sizeof(T);
+    if (src) {
+        e = cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+    }
+    return MRA_OK;
+}
+
+// Element counts of one theta's scratch (in units of the storage type for the
+// T-typed parts, doubles for the rest).
+struct Plan {
+    size_t prior = 0, prior_lvl[MRA_MAXM + 1] = {0};
+    size_t U = 0, y = 0, leafdu = 0, V = 0;
+    size_t Ain = 0, Ainw = 0, Aindu = 0;
+    size_t Atil[MRA_MAXM + 1] = {0}, Atilw[MRA_MAXM + 1] = {0}, Atildu[MRA_MAXM + 1] = {0};
+    size_t t_elems = 0, d_elems = 0; // totals
+};
+
+Plan make_plan(const mra_ctx *c)
+{
+    const Partition &P = c->P;
+    const int M = P.M, J = P.J, RP = c->RP;
+    const size_t B2 = (size_t)RP * RP;
+    Plan p;
+    size_t acc = 0;
+    for (int m = 1; m < M; m++) {
+        p.prior_lvl[m] = acc;
+        acc += (size_t)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]) * m * B2;
+    }
+    p.prior = acc;
+    p.U = (size_t)P.n_used * (size_t)(M - 1) * RP;
+    p.y = (size_t)P.n_used;
+    p.leafdu = 2 * (size_t)P.nleaf();
+    p.V = (size_t)c->vbig_elems;
+    if (M >= 2) {
+        const size_t nP = (size_t)(P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1]);
+        p.Ain = nP * (size_t)(M - 1) * M / 2 * B2;
+        p.Ainw = nP * (size_t)(M - 1) * RP;
+        p.Aindu = 2 * nP;
+        for (int m = 2; m <= M - 1; m++) {
+            const size_t nr = (size_t)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]);
+            p.Atil[m] = nr * (size_t)(m - 1) * m / 2 * B2;
+            p.Atilw[m] = nr * (size_t)(m - 1) * RP;
+            p.Atildu[m] = 2 * nr;
+        }
+    }
+    (void)J;
+    p.t_elems = p.prior + p.U + p.Ain;
+    for (int m = 2; m <= M - 1; m++) p.t_elems += p.Atil[m];
+    p.d_elems = p.y + p.leafdu + p.V + p.Ainw + p.Aindu;
+    for (int m = 2; m <= M - 1; m++) p.d_elems += p.Atilw[m] + p.Atildu[m];
+    return p;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Carve one theta-batch view of the scratch for storage type T.
+template <typename T>
+Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
+{
+    Work<T> w;
+    memset(&w, 0, sizeof(w));
+    unsigned char *base = c->d_scratch;
+    size_t off = 0;
+    auto takeT = [&](size_t elems) {
+        T *q = (T *)(base + off);
+        off = align256(off + elems * (size_t)B * sizeof(T));
+        return q;
+    };
+    auto takeD = [&](size_t elems) {
+        double *q = (double *)(base + off);
+        off = align256(off + elems * (size_t)B * sizeof(double));
+        return q;
+    };
+    // the layout is computed for sizeof(double) per T element so that both
+    // precisions share one allocation
+    auto takeT8 = [&](size_t elems) {
+        T *q = (T *)(base + off);
+        off = align256(off + elems * (size_t)B * sizeof(double));
+        return q;
+    };
+    (void)takeT;
+    w.prior = takeT8(p.prior);
+    w.prior_stride = p.prior;
+    for (int m = 0; m <= MRA_MAXM; m++) w.prior_lvl[m] = p.prior_lvl[m];
+    w.U = takeT8(p.U);
+    w.U_stride = p.U;
+    w.ybuf = takeD(p.y);
+    w.y_stride = p.y;
+    w.leaf_du = takeD(p.leafdu);
+    w.leafdu_stride = p.leafdu;
+    w.Vbig = takeD(p.V);
+    w.V_stride = p.V;
+    w.Ain = takeT8(p.Ain);
+    w.Ain_stride = p.Ain;
+    w.Ain_w = takeD(p.Ainw);
+    w.Ainw_stride = p.Ainw;
+    w.Ain_du = takeD(p.Aindu);
+    w.Aindu_stride = p.Aindu;
+    for (int m = 2; m <= c->P.M - 1; m++) {
+        w.Atil[m] = takeT8(p.Atil[m]);
+        w.Atil_stride[m] = p.Atil[m];
+        w.Atil_w[m] = takeD(p.Atilw[m]);
+        w.Atilw_stride[m] = p.Atilw[m];
+        w.Atil_du[m] = takeD(p.Atildu[m]);
+        w.Atildu_stride[m] = p.Atildu[m];
+    }
+    w.status = c->d_status;
+    return w;
+}
+
+size_t scratch_bytes_for(const Plan &p, const mra_ctx *c, int B)
+{
+    size_t s = 0;
+    auto add = [&](size_t elems) { s = align256(s + elems * (size_t)B * sizeof(double)); };
+    add(p.prior);
+    add(p.U);
+    add(p.y);
+    add(p.leafdu);
+    add(p.V);
+    add(p.Ain);
+    add(p.Ainw);
+    add(p.Aindu);
+    for (int m = 2; m <= c->P.M - 1; m++) {
+        add(p.Atil[m]);
+        add(p.Atilw[m]);
+        add(p.Atildu[m]);
+    }
+    return s;
+}
+
+DevTree dev_tree(const mra_ctx *c)
+{
+    DevTree t;
+    memset(&t, 0, sizeof(t));
+    t.M = c->P.M;
+    t.J = c->P.J;
+    t.lgJ = c->lgJ;
+    t.R = c->P.R;
+    t.RP = c->RP;
+    t.n_used = c->P.n_used;
+    t.kx = c->d_kx;
+    t.ky = c->d_ky;
+    t.sx = c->d_sx;
+    t.sy = c->d_sy;
+    t.sz = c->d_sz;
+    t.leaf_off = c->d_leaf_off;
+    for (int m = 0; m <= c->P.M + 1; m++) t.lvl_off[m] = c->P.lvl_off[(size_t)m];
+    return t;
+}
+
+enum { K_PRIOR, K_LEAFBASIS, K_LEAFPOST, K_LEAFPOST_BIG, K_LEAFGRAM, K_UP, K_ROOT, K_COUNT };
+const char *kKernelNames[K_COUNT] = {"prior", "leafbasis", "leafpost", "leafpost_big", "leafgram", "up", "root"};
+
+// Launch one kernel, bracketed by CUDA events when profiling is on.
+template <typename F>
+int timed_launch(mra_ctx *c, int kind, cudaStream_t s, F &&launch)
+{
+    if (!c->prof_on) {
+        c->launches_last++;
+        return launch();
+    }
+    if (c->ev_used + 2 > c->ev.size()) {
+        for (int k = 0; k < 64; k++) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return (int)cudaErrorMemoryAllocation;
+            c->ev.push_back(e);
+        }
+        c->ev_kind.resize(c->ev.size() / 2);
+    }
+    cudaEventRecord(c->ev[c->ev_used], s);
+    const int rc = launch();
+    cudaEventRecord(c->ev[c->ev_used + 1], s);
+    c->ev_kind[c->ev_used / 2] = kind;
+    c->ev_used += 2;
+    c->launches_last++;
+    return rc;
+}
+
+template <typename T, int RP>
+int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
+{
+    const DevTree t = dev_tree(c);
+    const int M = c->P.M;
+    int e;
+    c->launches_last = 0;
+    for (int m = 1; m < M; m++)
+        if ((e = timed_launch(c, K_PRIOR, s, [&] { return launch_prior<T, RP>(t, w, m, B, s); }))) return e;
+    if (M > 1 && c->nchunks > 0)
+        if ((e = timed_launch(c, K_LEAFBASIS, s,
+                              [&] { return launch_leafbasis<T, RP>(t, w, c->d_chunks, c->nchunks, B, s); })))
+            return e;
+    if (c->nl32 > 0)
+        if ((e = timed_launch(c, K_LEAFPOST, s,
+                              [&] { return launch_leafpost_small<T, RP>(t, w, c->d_leaves32, c->nl32, 32, B, s); })))
+            return e;
+    if (c->nl64 > 0)
+        if ((e = timed_launch(c, K_LEAFPOST, s, [&] {
+                 return launch_leafpost_small<T, RP>(t, w, c->d_leaves64, c->nl64, c->nmax64, B, s);
+             })))
+            return e;
+    if (c->nbig > 0)
+        if ((e = timed_launch(c, K_LEAFPOST_BIG, s,
+                              [&] { return launch_leafpost_big<T, RP>(t, w, c->d_big, c->nbig, B, s); })))
+            return e;
+    if (M > 1) {
+        const int nP = (int)(c->P.lvl_off[(size_t)M] - c->P.lvl_off[(size_t)M - 1]);
+        if ((e = timed_launch(c, K_LEAFGRAM, s, [&] { return launch_leafgram<T, RP>(t, w, nP, B, s); }))) return e;
+        for (int m = M - 1; m >= 1; m--)
+            if ((e = timed_launch(c, K_UP, s, [&] { return launch_up<T, RP>(t, w, m, B, s); }))) return e;
+    } else {
+        if ((e = timed_launch(c, K_ROOT, s, [&] { return launch_root_single<T, RP>(t, w, B, s); }))) return e;
+    }
+    return 0;
+}
+
+template <typename T>
+int dispatch_rp(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
+{
+    if (c->RP == 16) return run_pass<T, 16>(c, w, B, s);
+    return run_pass<T, 32>(c, w, B, s);
+}
+
+size_t max_smem_needed(const mra_ctx *c, int nmax64)
+{
+    const int M = c->P.M;
+    size_t mx = 0;
+    auto upd = [&](size_t v) { mx = std::max(mx, v); };
+    for (int m = 1; m < M; m++) {
+        if (c->RP == 16) {
+            upd(smem_prior<double, 16>(m));
+            upd(smem_up<double, 16>(m));
+        } else {
+            upd(smem_prior<double, 32>(m));
+            upd(smem_up<double, 32>(m));
+        }
+    }
+    if (c->RP == 16) {
+        upd(smem_leafbasis<double, 16>(M));
+        upd(smem_leafpost_small<double, 16>(M, 32));
+        if (nmax64 > 0) upd(smem_leafpost_small<double, 16>(M, nmax64));
+    } else {
+        upd(smem_leafbasis<double, 32>(M));
+        upd(smem_leafpost_small<double, 32>(M, 32));
+        if (nmax64 > 0) upd(smem_leafpost_small<double, 32>(M, nmax64));
+    }
+    return mx;
+}
+
+// Algorithmic FP operations of one evaluation per kernel family (r_hat, not
+// the padding; symmetric products counted once; FMA = 2), and covariance
+// evaluations.
+void count_work(mra_ctx *c)
+{
+    const Partition &P = c->P;
+    const double R = P.R;
+    const int M = P.M, J = P.J;
+    double f[K_COUNT] = {0};
+    double cv = 0.0;
+    for (int m = 1; m < M; m++) {
+        const double nr = (double)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]);
+        double per = 0.0;
+        for (int l = 1; l < m; l++) per += 2.0 * (l - 1) * R * R * R + R * R * R; // W^l and W^l Linv'
+        per += (m - 1) * R * R * (R + 1) + 2.0 * R * R * R / 3.0;                 // self block, chol, inverse
+        f[K_PRIOR] += nr * per;
+        cv += nr * ((m - 1) * R * R + R * (R + 1) / 2);
+        f[K_UP] += nr * (R * R * R / 3.0 + (m - 1) * R * R * R + R * R + (m - 1) * (m - 2) * R * R * R +
+                         (m - 1) * R * R * (R + 1) + 2.0 * (m - 1) * R * R);
+    }
+    if (M > 1) {
+        double perrow = 0.0;
+        for (int l = 1; l < M; l++) perrow += 2.0 * (l - 1) * R * R + R * R;
+        f[K_LEAFBASIS] += (double)P.n_used * perrow;
+        cv += (double)P.n_used * (M - 1) * R;
+        const int64_t nP = P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1];
+        for (int64_t p = 0; p < nP; p++) {
+            const double N = (double)(P.leaf_off[(size_t)((p + 1) * J)] - P.leaf_off[(size_t)(p * J)]);
+            f[K_LEAFGRAM] += N * R * R * (M - 1) * (M - 2) + N * R * (R + 1) * (M - 1) + 2.0 * N * (M - 1) * R;
+        }
+    }
+    for (int64_t l = 0; l < P.nleaf(); l++) {
+        const double n = (double)(P.leaf_off[(size_t)l + 1] - P.leaf_off[(size_t)l]);
+        const double fl = (M - 1) * R * n * (n + 1) + n * n * n / 3.0 + (M - 1) * R * n * n + n * n;
+        if (n <= c->nmax64 || c->d_sx == nullptr)
+            f[K_LEAFPOST] += fl;
+        else
+            f[K_LEAFPOST_BIG] += fl;
+        cv += n * (n + 1) / 2;
+    }
+    double tot = 0.0;
+    for (int k = 0; k < K_COUNT; k++) {
+        c->flops_k[k] = f[k];
+        tot += f[k];
+    }
+    c->flops = tot;
+    c->covs = cv;
+}
+
+mra_status ensure_capacity(mra_ctx *c, int B)
+{
+    if (B <= c->cap) return MRA_OK;
+    Plan p = make_plan(c);
+    const size_t bytes = scratch_bytes_for(p, c, B);
+    if (c->d_scratch) {
+        cudaFree(c->d_scratch);
+        c->bytes_held -= c->scratch_bytes;
+        c->d_scratch = nullptr;
+    }
+    if (c->d_status) {
+        cudaFree(c->d_status);
+        c->d_status = nullptr;
+    }
+    cudaError_t e = cudaMalloc((void **)&c->d_scratch, bytes);
+    if (e != cudaSuccess) {
+        c->cap = 0;
+        c->err = "cannot allocate per-theta scratch";
+        return MRA_ENOMEM;
+    }
+    e = cudaMalloc((void **)&c->d_status, sizeof(int) * (size_t)B);
+    if (e != cudaSuccess) {
+        cudaFree(c->d_scratch);
+        c->d_scratch = nullptr;
+        c->cap = 0;
+        c->err = "cannot allocate status";
+        return MRA_ENOMEM;
+    }
+    c->scratch_bytes = bytes;
+    c->bytes_held += bytes;
+    c->cap = B;
+    return MRA_OK;
+}
+
+int max_batch_for(mra_ctx *c, size_t budget)
+{
+    Plan p = make_plan(c);
+    const size_t per = scratch_bytes_for(p, c, 1) + 4096;
+    c->per_theta_bytes = per;
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)8 << 30;
+        budget = (size_t)(0.6 * (double)fr);
+    }
+    size_t b = budget / per;
+    if (b < 1) b = 1;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+mra_status enqueue(mra_ctx *c, const double *theta_dev, int batch, double *loglik_dev, int *status_dev,
+                   cudaStream_t s, bool with_regions)
+{
+    int done = 0;
+    while (done < batch) {
+        const int B = std::min(batch - done, std::max(c->max_cap, 1));
+        if (mra_status st = ensure_capacity(c, B)) return st;
+        Plan p = make_plan(c);
+        cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int) * (size_t)B, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+        int rc;
+        if (c->precision == MRA_MIXED) {
+            Work<float> w = make_work<float>(c, p, B);
+            w.theta = theta_dev + 3 * (size_t)done;
+            w.loglik = loglik_dev + done;
+            if (with_regions) {
+                w.reg_du = c->d_reg_du;
+                w.reg_lw = c->d_reg_lw;
+            }
+            rc = dispatch_rp<float>(c, w, B, s);
+        } else {
+            Work<double> w = make_work<double>(c, p, B);
+            w.theta = theta_dev + 3 * (size_t)done;
+            w.loglik = loglik_dev + done;
+            if (with_regions) {
+                w.reg_du = c->d_reg_du;
+                w.reg_lw = c->d_reg_lw;
+            }
+            rc = dispatch_rp<double>(c, w, B, s);
+        }
+        if (rc) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+        if (status_dev) {
+            e = cudaMemcpyAsync(status_dev + done, c->d_status, sizeof(int) * (size_t)B, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
+        }
+        done += B;
+    }
+    return MRA_OK;
+}
+
+mra_status ensure_stage(mra_ctx *c, int batch)
+{
+    if (batch <= c->stage_cap) return MRA_OK;
+    cudaFree(c->d_theta_stage);
+    cudaFree(c->d_ll_stage);
+    c->d_theta_stage = nullptr;
+    c->d_ll_stage = nullptr;
+    if (cudaMalloc((void **)&c->d_theta_stage, sizeof(double) * 3 * (size_t)batch) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_ll_stage, sizeof(double) * (size_t)batch + sizeof(int) * (size_t)batch) !=
+            cudaSuccess) {
+        c->stage_cap = 0;
+        c->err = "cannot allocate theta staging";
+        return MRA_ENOMEM;
+    }
+    c->stage_cap = batch;
+    return MRA_OK;
+}
+
+} // namespace
+
+// ---------------------------------------------------------------- C ABI --
+extern "C" {
+
+void mra_default_opts(mra_opts *opt)
+{
+    if (!opt) return;
+    opt->offset = -1.0;
+    opt->dedup = 0;
+    opt->precision = MRA_FP64;
+    opt->device = 0;
+    opt->max_batch = 0;
+    opt->hbm_budget = 0;
+}
+
+static thread_local std::string g_build_err = "no context";
+
+static mra_status build_ctx(const double *lon, const double *lat, const double *z, int64_t n, int M, int J, int r,
+                            const mra_opts *opt_in, mra_ctx **out);
+
+mra_status mra_build(const double *lon, const double *lat, const double *z, int64_t n, int M, int J, int r,
+                     const mra_opts *opt_in, mra_ctx **out)
+{
+    if (!out) return MRA_EINVAL;
+    *out = nullptr;
+    mra_ctx *c = nullptr;
+    mra_status st = build_ctx(lon, lat, z, n, M, J, r, opt_in, &c);
+    if (st != MRA_OK) {
+        g_build_err = c ? c->err : std::string("out of host memory");
+        mra_free(c);
+        return st;
+    }
+    *out = c;
+    return MRA_OK;
+}
+
+static mra_status build_ctx(const double *lon, const double *lat, const double *z, int64_t n, int M, int J, int r,
+                            const mra_opts *opt_in, mra_ctx **out)
+{
+    if (n > 0 && (!lon || !lat || !z)) return MRA_EINVAL;
+    mra_opts opt;
+    mra_default_opts(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.precision != MRA_FP64 && opt.precision != MRA_MIXED) return MRA_EINVAL;
+    mra_ctx *c = new (std::nothrow) mra_ctx();
+    if (!c) return MRA_ENOMEM;
+    *out = c;
+    c->precision = opt.precision;
+    c->device = opt.device;
+    const double f = opt.offset < 0.0 ? kDefaultOffset : opt.offset;
+    mra_status st = build_partition(lon, lat, z, n, M, J, r, f, opt.dedup, c->P, c->err);
+    if (st != MRA_OK) return st;
+    const Partition &P = c->P;
+    if (P.R > 32) {
+        c->err = "r_hat > 32 is not supported by this build";
+        *out = c;
+        return MRA_EINVAL;
+    }
+    c->RP = P.R <= 16 ? 16 : 32;
+    c->lgJ = J == 4 ? 2 : 1;
+    if (opt.device < 0) { // host-only partition: stats and tree queries, no likelihood
+        for (int64_t l = 0; l < P.nleaf(); l++) {
+            const int64_t nl = P.leaf_off[(size_t)l + 1] - P.leaf_off[(size_t)l];
+            c->max_leaf = std::max(c->max_leaf, nl);
+            c->empty_leaves += nl == 0;
+        }
+        count_work(c);
+        return MRA_OK;
+    }
+    cudaError_t e = cudaSetDevice(opt.device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    // work lists
+    std::vector<Chunk> chunks;
+    if (M > 1) {
+        const int64_t nP = P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1];
+        for (int64_t p = 0; p < nP; p++) {
+            const int64_t r0 = P.leaf_off[(size_t)(p * J)], r1 = P.leaf_off[(size_t)((p + 1) * J)];
+            for (int64_t rb = r0; rb < r1; rb += MRA_CH) {
+                Chunk ch;
+                ch.parent = (int32_t)p;
+                ch.n = (int32_t)std::min<int64_t>(MRA_CH, r1 - rb);
+                ch.row0 = rb;
+                chunks.push_back(ch);
+            }
+        }
+    }
+    int nmax64 = 64;
+    while (nmax64 > 32 && max_smem_needed(c, nmax64) > 227 * 1024) nmax64 -= 8;
+    if (max_smem_needed(c, nmax64 > 32 ? nmax64 : 0) > 227 * 1024) {
+        c->err = "M too large for the shared-memory kernels at this r";
+        *out = c;
+        return MRA_EINVAL;
+    }
+    c->nmax64 = nmax64;
+    std::vector<int64_t> l32, l64;
+    std::vector<BigLeaf> big;
+    int64_t voff = 0;
+    for (int64_t l = 0; l < P.nleaf(); l++) {
+        const int64_t nl = P.leaf_off[(size_t)l + 1] - P.leaf_off[(size_t)l];
+        c->max_leaf = std::max(c->max_leaf, nl);
+        if (nl == 0) {
+            c->empty_leaves++;
+        } else if (nl <= 32) {
+            l32.push_back(l);
+        } else if (nl <= nmax64) {
+            l64.push_back(l);
+        } else {
+            big.push_back(BigLeaf{l, voff});
+            voff += 2 * nl * nl; // V (FP64) and a copy of its factor in the storage type
+        }
+    }
+    c->vbig_elems = voff;
+    // device tree, knots padded to RP
+    std::vector<double> kxp((size_t)(P.nnonleaf() * c->RP), 0.0), kyp((size_t)(P.nnonleaf() * c->RP), 0.0);
+    for (int64_t g = 0; g < P.nnonleaf(); g++)
+        for (int j = 0; j < P.R; j++) {
+            kxp[(size_t)(g * c->RP + j)] = P.kx[(size_t)(g * P.R + j)];
+            kyp[(size_t)(g * c->RP + j)] = P.ky[(size_t)(g * P.R + j)];
+        }
+    if ((st = dev_upload(c, &c->d_kx, kxp.data(), kxp.size())) || (st = dev_upload(c, &c->d_ky, kyp.data(), kyp.size())) ||
+        (st = dev_upload(c, &c->d_sx, P.sx.data(), P.sx.size())) || (st = dev_upload(c, &c->d_sy, P.sy.data(), P.sy.size())) ||
+        (st = dev_upload(c, &c->d_sz, P.sz.data(), P.sz.size())) ||
+        (st = dev_upload(c, &c->d_leaf_off, P.leaf_off.data(), P.leaf_off.size())) ||
+        (st = dev_upload(c, &c->d_chunks, chunks.data(), chunks.size())) ||
+        (st = dev_upload(c, &c->d_leaves32, l32.data(), l32.size())) ||
+        (st = dev_upload(c, &c->d_leaves64, l64.data(), l64.size())) || (st = dev_upload(c, &c->d_big, big.data(), big.size()))) {
+        *out = c;
+        return st;
+    }
+    c->nchunks = (int)chunks.size();
+    c->nl32 = (int)l32.size();
+    c->nl64 = (int)l64.size();
+    c->nbig = (int)big.size();
+    count_work(c);
+    const int mb = max_batch_for(c, opt.hbm_budget);
+    c->max_cap = opt.max_batch > 0 ? std::min(opt.max_batch, 1024) : mb;
+    st = ensure_capacity(c, 1);
+    if (st != MRA_OK) {
+        *out = c;
+        return st;
+    }
+    *out = c;
+    return MRA_OK;
+}
+
+mra_status mra_set_precision(mra_ctx *c, int precision)
+{
+    if (!c) return MRA_EINVAL;
+    if (precision != MRA_FP64 && precision != MRA_MIXED) {
+        c->err = "precision must be MRA_FP64 or MRA_MIXED";
+        return MRA_EINVAL;
+    }
+    c->precision = precision;
+    return MRA_OK;
+}
+
+mra_status mra_loglik_device(mra_ctx *c, const double *theta_dev, int batch, double *loglik_dev, int *status_dev,
+                             void *stream)
+{
+    if (!c) return MRA_EINVAL;
+    if (!c->d_sx) {
+        c->err = "context was built without a device";
+        return MRA_EINVAL;
+    }
+    if (batch < 0 || (batch > 0 && (!theta_dev || !loglik_dev))) {
+        c->err = "bad batch or null pointer";
+        return MRA_EINVAL;
+    }
+    if (batch == 0) return MRA_OK;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return enqueue(c, theta_dev, batch, loglik_dev, status_dev, (cudaStream_t)stream, false);
+}
+
+mra_status mra_loglik(mra_ctx *c, const double *theta, int batch, double *loglik)
+{
+    if (!c) return MRA_EINVAL;
+    if (!c->d_sx) {
+        c->err = "context was built without a device";
+        return MRA_EINVAL;
+    }
+    if (batch < 0 || (batch > 0 && (!theta || !loglik))) {
+        c->err = "bad batch or null pointer";
+        return MRA_EINVAL;
+    }
+    if (batch == 0) return MRA_OK;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    if (mra_status st = ensure_stage(c, batch)) return st;
+    int *d_st = (int *)(c->d_ll_stage + batch);
+    e = cudaMemcpy(c->d_theta_stage, theta, sizeof(double) * 3 * (size_t)batch, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy theta");
+    mra_status st = enqueue(c, c->d_theta_stage, batch, c->d_ll_stage, d_st, (cudaStream_t)0, false);
+    if (st != MRA_OK) return st;
+    std::vector<int> hs((size_t)batch);
+    e = cudaMemcpy(loglik, c->d_ll_stage, sizeof(double) * (size_t)batch, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), d_st, sizeof(int) * (size_t)batch, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy loglik");
+    for (int b = 0; b < batch; b++)
+        if (hs[(size_t)b] != MRA_OK) {
+            c->err = hs[(size_t)b] == MRA_EINVAL ? "theta must be finite and positive" : "Cholesky factor not positive definite";
+            return (mra_status)hs[(size_t)b];
+        }
+    return MRA_OK;
+}
+
+mra_status mra_region_terms(mra_ctx *c, const double *theta, double *d, double *u, double *logdetW, double *loglik)
+{
+    if (!c || !theta) return MRA_EINVAL;
+    if (!c->d_sx) {
+        c->err = "context was built without a device";
+        return MRA_EINVAL;
+    }
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const int64_t NR = c->P.nreg(), NK = c->P.nnonleaf();
+    if (!c->d_reg_du) {
+        if (cudaMalloc((void **)&c->d_reg_du, sizeof(double) * 2 * (size_t)NR) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_reg_lw, sizeof(double) * (size_t)std::max<int64_t>(NK, 1)) != cudaSuccess) {
+            c->err = "cannot allocate region records";
+            return MRA_ENOMEM;
+        }
+        c->bytes_held += sizeof(double) * (2 * (size_t)NR + (size_t)std::max<int64_t>(NK, 1));
+    }
+    if (mra_status st = ensure_stage(c, 1)) return st;
+    std::vector<double> nanv((size_t)std::max<int64_t>(NK, 1), std::nan(""));
+    e = cudaMemset(c->d_reg_du, 0, sizeof(double) * 2 * (size_t)NR);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_reg_lw, nanv.data(), sizeof(double) * nanv.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_theta_stage, theta, sizeof(double) * 3, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "region setup");
+    int *d_st = (int *)(c->d_ll_stage + 1);
+    mra_status st = enqueue(c, c->d_theta_stage, 1, c->d_ll_stage, d_st, (cudaStream_t)0, true);
+    if (st != MRA_OK) return st;
+    std::vector<double> du((size_t)(2 * NR)), lw((size_t)std::max<int64_t>(NK, 1));
+    int hs = 0;
+    double ll = 0.0;
+    e = cudaMemcpy(du.data(), c->d_reg_du, sizeof(double) * du.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(lw.data(), c->d_reg_lw, sizeof(double) * lw.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&ll, c->d_ll_stage, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&hs, d_st, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "region readback");
+    for (int64_t g = 0; g < NR; g++) {
+        if (d) d[g] = du[(size_t)(2 * g)];
+        if (u) u[g] = du[(size_t)(2 * g + 1)];
+        if (logdetW) logdetW[g] = g < NK ? lw[(size_t)g] : std::nan("");
+    }
+    if (loglik) *loglik = ll;
+    return (mra_status)hs;
+}
+
+mra_status mra_stats(const mra_ctx *c, mra_stats_t *o)
+{
+    if (!c || !o) return MRA_EINVAL;
+    memset(o, 0, sizeof(*o));
+    const Partition &P = c->P;
+    o->n_in = P.n_in;
+    o->n_used = P.n_used;
+    o->n_nan = P.n_nan;
+    o->n_dup = P.n_dup;
+    o->n_knot = P.n_knot;
+    if (!P.lvl_off.empty()) {
+        o->n_regions = P.nreg();
+        o->n_leaves = P.nleaf();
+    }
+    o->M = P.M;
+    o->J = P.J;
+    o->r = P.r;
+    o->r_hat = P.R;
+    o->max_leaf = c->max_leaf;
+    o->empty_leaves = c->empty_leaves;
+    o->max_batch = c->cap;
+    o->flops_per_theta = c->flops;
+    o->cov_evals_per_theta = c->covs;
+    o->device_bytes = c->bytes_held;
+    o->launches_per_pass = c->launches_last;
+    for (int k = 0; k < 8; k++) o->flops_by_kernel[k] = c->flops_k[k];
+    return MRA_OK;
+}
+
+mra_status mra_tree_export(const mra_ctx *c, double *kx, double *ky, int64_t *leaf_off, int64_t *perm, double *bounds)
+{
+    if (!c || c->P.lvl_off.empty()) return MRA_EINVAL;
+    const Partition &P = c->P;
+    if (kx) std::copy(P.kx.begin(), P.kx.end(), kx);
+    if (ky) std::copy(P.ky.begin(), P.ky.end(), ky);
+    if (leaf_off) std::copy(P.leaf_off.begin(), P.leaf_off.end(), leaf_off);
+    if (perm) std::copy(P.perm.begin(), P.perm.end(), perm);
+    if (bounds)
+        for (int64_t g = 0; g < P.nreg(); g++) {
+            bounds[4 * g + 0] = P.bx0[(size_t)g];
+            bounds[4 * g + 1] = P.bx1[(size_t)g];
+            bounds[4 * g + 2] = P.by0[(size_t)g];
+            bounds[4 * g + 3] = P.by1[(size_t)g];
+        }
+    return MRA_OK;
+}
+
+mra_status mra_profile(mra_ctx *c, int enable)
+{
+    if (!c) return MRA_EINVAL;
+    c->prof_on = enable != 0;
+    c->ev_used = 0;
+    return MRA_OK;
+}
+
+int mra_profile_read(mra_ctx *c, mra_kernel_time *out, int cap)
+{
+    if (!c || (cap > 0 && !out)) return -1;
+    double ms[K_COUNT] = {0};
+    int64_t cnt[K_COUNT] = {0};
+    for (size_t k = 0; k + 1 < c->ev_used + 1 && k < c->ev_used; k += 2) {
+        float t = 0.f;
+        if (cudaEventSynchronize(c->ev[k + 1]) != cudaSuccess) return -1;
+        if (cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]) != cudaSuccess) return -1;
+        ms[c->ev_kind[k / 2]] += t;
+        cnt[c->ev_kind[k / 2]]++;
+    }
+    c->ev_used = 0;
+    int n = 0;
+    for (int k = 0; k < K_COUNT; k++) {
+        if (cnt[k] == 0) continue;
+        if (n < cap) {
+            memset(&out[n], 0, sizeof(out[n]));
+            strncpy(out[n].name, kKernelNames[k], sizeof(out[n].name) - 1);
+            out[n].launches = cnt[k];
+            out[n].ms = ms[k];
+        }
+        n++;
+    }
+    return n;
+}
+
+const char *mra_last_error(const mra_ctx *c)
+{
+    if (!c) return g_build_err.c_str();
+    return c->err.c_str();
+}
+
+void mra_free(mra_ctx *c)
+{
+    if (!c) return;
+    if (c->device >= 0 && c->d_sx) cudaSetDevice(c->device);
+    void *ptrs[] = {c->d_kx, c->d_ky, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks, c->d_leaves32,
+                    c->d_leaves64, c->d_big, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
+                    c->d_reg_du, c->d_reg_lw};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+}
+
+} // extern "C"

@@ -1,0 +1,102 @@
+// mra_internal.h -- device-side data layout shared by the kernels and the host
+// orchestration of libmra.  Not part of the public ABI (include/mra.h).
+//
+// Layout in HBM (one context):
+//   knots      kx, ky [n_nonleaf][RP]      regions of levels 1..M-1, padded to RP
+//   obs        sx, sy, sz [n_used]          leaf order
+//   leaf_off   [n_leaf + 1]
+// Per theta (stride-separated copies for a batch of B theta):
+//   prior      level m, region i: m blocks RP x RP (row-major): What^1..What^{m-1}
+//              then Linv = L^{-1}, L the Cholesky factor of W^m = C_m(Q, Q).
+//   U          [n_used][(M-1) RP]: the whitened leaf basis What^l of every
+//              observation, overwritten in place by Y = L_V^{-1} U.
+//   y          [n_used]            L_V^{-1} z
+//   Ain        level M-1 regions: A = sum over the leaf children of Y'Y,
+//              packed upper blocks (k <= l), pair index l(l-1)/2 + k-1
+//   Atil[m]    level m regions (2 <= m <= M-1): ATilde after the region's step,
+//              blocks (k <= l <= m-1), same packing, plus w (double) and (d, u).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#define MRA_MAXM 24
+#define MRA_NT 256
+#define MRA_CH 32 /* observation rows per leaf-basis chunk */
+
+namespace mra {
+
+struct DevTree {
+    int M, J, lgJ, R, RP;
+    int64_t n_used;
+    const double *kx, *ky;
+    const double *sx, *sy, *sz;
+    const int64_t *leaf_off;
+    int64_t lvl_off[MRA_MAXM + 2]; // first global region id of level m (1-based)
+};
+
+template <typename T>
+struct Work {
+    const double *theta; // [B][3]
+    int *status;         // [B]
+    double *loglik;      // [B]
+    T *prior;
+    size_t prior_stride;
+    size_t prior_lvl[MRA_MAXM + 1]; // element offset of level m inside one theta's prior
+    T *U;
+    size_t U_stride;
+    double *ybuf;
+    size_t y_stride;
+    double *leaf_du; // [nleaf][2]
+    size_t leafdu_stride;
+    double *Vbig; // big-leaf V scratch
+    size_t V_stride;
+    T *Ain;       // [nP][npairs(M-1)][RP*RP]
+    double *Ain_w; // [nP][(M-1) RP]
+    double *Ain_du; // [nP][2]
+    size_t Ain_stride, Ainw_stride, Aindu_stride;
+    T *Atil[MRA_MAXM + 1];
+    double *Atil_w[MRA_MAXM + 1];
+    double *Atil_du[MRA_MAXM + 1];
+    size_t Atil_stride[MRA_MAXM + 1], Atilw_stride[MRA_MAXM + 1], Atildu_stride[MRA_MAXM + 1];
+    double *reg_du; // [nreg][2] or null
+    double *reg_lw; // [n_nonleaf] or null
+    size_t regdu_stride, reglw_stride;
+};
+
+struct Chunk {
+    int32_t parent; // level M-1 region index
+    int32_t n;      // rows in this chunk (<= MRA_CH)
+    int64_t row0;   // first observation row
+};
+
+struct BigLeaf {
+    int64_t leaf;
+    int64_t voff; // element offset of its V in Vbig
+};
+
+// Launchers (one instantiation per precision T and padding RP).
+template <typename T, int RP>
+int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream);
+template <typename T, int RP>
+int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int B,
+                     void *stream);
+template <typename T, int RP>
+int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves,
+                          int nmax, int B, void *stream);
+template <typename T, int RP>
+int launch_leafpost_big(const DevTree &t, const Work<T> &w, const BigLeaf *leaves, int nleaves,
+                        int B, void *stream);
+template <typename T, int RP>
+int launch_leafgram(const DevTree &t, const Work<T> &w, int nP, int B, void *stream);
+template <typename T, int RP>
+int launch_up(const DevTree &t, const Work<T> &w, int m, int B, void *stream);
+template <typename T, int RP>
+int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream);
+
+// Dynamic shared memory (bytes) each kernel needs; 0 when beyond the limit.
+template <typename T, int RP> size_t smem_prior(int m);
+template <typename T, int RP> size_t smem_leafbasis(int M);
+template <typename T, int RP> size_t smem_leafpost_small(int M, int nmax);
+template <typename T, int RP> size_t smem_up(int m);
+
+} // namespace mra

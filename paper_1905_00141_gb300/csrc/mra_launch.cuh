@@ -1,0 +1,111 @@
+// mra_launch.cuh -- host launchers of the MRA kernels, instantiated per
+// precision in k_f64.cu and k_f32.cu.
+#pragma once
+#include "mra_kernels.cuh"
+
+namespace mra {
+
+// Raise the dynamic shared-memory limit of a kernel once per process.
+template <typename K>
+static int set_smem(K kernel, size_t bytes, size_t *done)
+{
+    if (bytes <= *done) return 0;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return (int)e;
+    *done = bytes;
+    return 0;
+}
+
+template <typename T, int RP> size_t smem_prior(int m) { return smem_prior_bytes<T, RP>(m); }
+template <typename T, int RP> size_t smem_leafbasis(int M) { return smem_leafbasis_bytes<T, RP>(M); }
+template <typename T, int RP> size_t smem_leafpost_small(int M, int nmax) { return smem_leafpost_bytes<T, RP>(M, nmax); }
+template <typename T, int RP> size_t smem_up(int m) { return smem_up_bytes<T, RP>(m); }
+
+template <typename T, int RP>
+int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream)
+{
+    static size_t done = 0;
+    const size_t sm = smem_prior_bytes<T, RP>(m);
+    if (int e = set_smem(k_prior<T, RP>, sm, &done)) return e;
+    dim3 grid((unsigned)(t.lvl_off[m + 1] - t.lvl_off[m]), (unsigned)B);
+    k_prior<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int RP>
+int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int B, void *stream)
+{
+    static size_t done = 0;
+    if (nchunks == 0) return 0;
+    const size_t sm = smem_leafbasis_bytes<T, RP>(t.M);
+    if (int e = set_smem(k_leafbasis<T, RP>, sm, &done)) return e;
+    dim3 grid((unsigned)nchunks, (unsigned)B);
+    k_leafbasis<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, chunks);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int RP>
+int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves, int nmax,
+                          int B, void *stream)
+{
+    static size_t done = 0;
+    if (nleaves == 0) return 0;
+    const size_t sm = smem_leafpost_bytes<T, RP>(t.M, nmax);
+    if (int e = set_smem(k_leafpost_small<T, RP>, sm, &done)) return e;
+    dim3 grid((unsigned)nleaves, (unsigned)B);
+    k_leafpost_small<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, leaves, nmax);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int RP>
+int launch_leafpost_big(const DevTree &t, const Work<T> &w, const BigLeaf *leaves, int nleaves, int B,
+                        void *stream)
+{
+    if (nleaves == 0) return 0;
+    dim3 grid((unsigned)nleaves, (unsigned)B);
+    k_leafpost_big<T, RP><<<grid, NT, 0, (cudaStream_t)stream>>>(t, w, leaves);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int RP>
+int launch_leafgram(const DevTree &t, const Work<T> &w, int nP, int B, void *stream)
+{
+    dim3 grid((unsigned)nP, (unsigned)(npairs(t.M - 1) + 1), (unsigned)B);
+    k_leafgram<T, RP><<<grid, NT, 0, (cudaStream_t)stream>>>(t, w);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int RP>
+int launch_up(const DevTree &t, const Work<T> &w, int m, int B, void *stream)
+{
+    static size_t done = 0;
+    const size_t sm = smem_up_bytes<T, RP>(m);
+    if (int e = set_smem(k_up<T, RP>, sm, &done)) return e;
+    dim3 grid((unsigned)(t.lvl_off[m + 1] - t.lvl_off[m]), (unsigned)B);
+    k_up<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int RP>
+int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream)
+{
+    k_root_single<T><<<(unsigned)B, 32, 0, (cudaStream_t)stream>>>(t, w);
+    return (int)cudaGetLastError();
+}
+
+#define MRA_INSTANTIATE(T, RP)                                                                              \
+    template size_t smem_prior<T, RP>(int);                                                                 \
+    template size_t smem_leafbasis<T, RP>(int);                                                             \
+    template size_t smem_leafpost_small<T, RP>(int, int);                                                   \
+    template size_t smem_up<T, RP>(int);                                                                    \
+    template int launch_prior<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                   \
+    template int launch_leafbasis<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, void *); \
+    template int launch_leafpost_small<T, RP>(const DevTree &, const Work<T> &, const int64_t *, int, int,   \
+                                              int, void *);                                                 \
+    template int launch_leafpost_big<T, RP>(const DevTree &, const Work<T> &, const BigLeaf *, int, int,    \
+                                            void *);                                                        \
+    template int launch_leafgram<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                \
+    template int launch_up<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                      \
+    template int launch_root_single<T, RP>(const DevTree &, const Work<T> &, int, void *);
+
+} // namespace mra

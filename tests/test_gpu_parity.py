@@ -1,0 +1,143 @@
+"""GPU (sm_103a) likelihood against the FP64 oracle, through the C ABI.
+
+Tolerances (|loglik_gpu - loglik_oracle| / n): FP64 path 1e-10, mixed path
+1e-6 (the mixed target of the workload definition).  Both sides evaluate the
+same likelihood by different routes: the oracle in the paper's K form, the
+GPU in the whitened form, so agreement checks the arithmetic, not a shared
+code path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_00141_gb300 import build as mbuild
+from paper_1905_00141_gb300 import mra, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOLMIX = 1e-6
+THETAS = np.array([[1.0, 0.1, 0.05], [2.5, 0.3, 0.01], [0.7, 0.02, 0.2]])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    mbuild.build()
+    oracle.build()
+
+
+def _parity(x, y, z, M, J, r, thetas=THETAS, precisions=("fp64", "mixed"), **kw):
+    ref, st = oracle.loglik(x, y, z, M, J, r, thetas, **kw)
+    assert st == 0
+    out = {}
+    with mra.MRA(x, y, z, M, J, r, **kw) as g:
+        n = g.stats()["n_used"]
+        for p in precisions:
+            g.set_precision(p)
+            got = g.loglik(thetas)
+            err = np.abs(got - ref) / n
+            tol = TOL64 if p == "fp64" else TOLMIX
+            assert np.all(err <= tol), (p, got, ref, err)
+            out[p] = err
+    return out
+
+
+@pytest.mark.parametrize("n,M,J,r,seed", [
+    (300, 1, 4, 16, 1),     # the root is one leaf of 300 (large-leaf path)
+    (600, 2, 4, 16, 2),
+    (2000, 3, 4, 9, 3),     # r_hat = 9, padded to 16
+    (3000, 4, 2, 30, 4),    # J = 2, r_hat = 30, padded to 32
+    (3000, 5, 4, 32, 5),
+    (4000, 6, 2, 16, 6),
+    (1500, 4, 4, 2, 7),     # r_hat = 2
+])
+def test_parity_small_trees(n, M, J, r, seed):
+    x, y, z = synth.uniform(n, seed)
+    _parity(x, y, z, M, J, r)
+
+
+def test_parity_ragged_leaves_and_empty_subtrees():
+    x, y, z = synth.uniform(3000, 11)
+    hole = (x < 0.5) & (y < 0.5) & ~((x < 0.02) | (y < 0.02))
+    x, y, z = x[~hole], y[~hole], z[~hole]
+    # a dense cluster makes leaves of > 64 observations next to empty ones
+    rng = np.random.default_rng(5)
+    cx = 0.8 + 0.01 * rng.standard_normal(400)
+    cy = 0.8 + 0.01 * rng.standard_normal(400)
+    x, y = np.concatenate([x, cx]), np.concatenate([y, cy])
+    z = np.concatenate([z, rng.standard_normal(400)])
+    with mra.MRA(x, y, z, 4, 4, 16) as g:
+        s = g.stats()
+        assert s["empty_leaves"] > 0 and s["max_leaf"] > 64
+    _parity(x, y, z, 4, 4, 16)
+
+
+def test_parity_small_workload():
+    d = synth.small()
+    _parity(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], d["theta"])
+
+
+def test_parity_grid_workload_full_size():
+    d = synth.grid()
+    th = np.array([[1.0, 0.05, 0.01], [1.3, 0.08, 0.02]])
+    err = _parity(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], th)
+    print("grid |dl|/n", {k: v.tolist() for k, v in err.items()})
+
+
+def test_region_terms_match_oracle():
+    x, y, z = synth.uniform(3000, 21)
+    th = np.array([1.2, 0.15, 0.03])
+    t = oracle.Tree(x, y, z, 4, 4, 16)
+    ro = t.region_terms(th)
+    with mra.MRA(x, y, z, 4, 4, 16) as g:
+        rg = g.region_terms(th)
+    assert rg["status"] == 0 and ro["status"] == 0
+    scale = np.abs(ro["d"]).max() + np.abs(ro["u"]).max()
+    assert np.allclose(rg["d"], ro["d"], rtol=1e-9, atol=1e-10 * scale)
+    assert np.allclose(rg["u"], ro["u"], rtol=1e-9, atol=1e-10 * scale)
+    k = np.isfinite(ro["logdetW"])
+    assert np.array_equal(k, np.isfinite(rg["logdetW"]))
+    assert np.allclose(rg["logdetW"][k], ro["logdetW"][k], rtol=1e-9, atol=1e-9)
+    assert abs(rg["loglik"] - ro["loglik"]) <= TOL64 * t.n_used
+
+
+def test_batch_with_invalid_and_singular_theta():
+    x, y, z = synth.uniform(1200, 31)
+    th = np.array([[1.0, 0.1, 0.05], [np.nan, 0.1, 0.05], [1.0, -0.1, 0.05], [1.0, 1e8, 0.05],
+                   [1.0, 0.1, 0.0], [0.9, 0.2, 0.04]])
+    ref, _ = oracle.loglik(x, y, z, 3, 4, 16, th)
+    with mra.MRA(x, y, z, 3, 4, 16) as g:
+        got, st = g.loglik_status(th)
+    assert st in (mra.EINVAL, mra.ENOTPD)
+    ok = np.isfinite(ref)
+    assert np.array_equal(ok, np.isfinite(got))
+    assert list(ok) == [True, False, False, False, False, True]
+    assert np.all(np.abs(got[ok] - ref[ok]) / 1200 <= TOL64)
+
+
+def test_device_api_with_torch_stream_and_batches():
+    import torch
+    d = synth.small()
+    th = np.stack([np.geomspace(0.5, 2.0, 7), np.geomspace(0.03, 0.3, 7), np.geomspace(0.01, 0.1, 7)], 1)
+    ref, _ = oracle.loglik(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], th)
+    with mra.MRA(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], max_batch=3) as g:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            tt = torch.tensor(th, device="cuda", dtype=torch.float64)
+            st = torch.full((7,), -1, dtype=torch.int32, device="cuda")
+            out = g.loglik_torch(tt, status=st)
+        s.synchronize()
+        assert np.all(np.abs(out.cpu().numpy() - ref) / 4096 <= TOL64)
+        assert st.cpu().tolist() == [0] * 7
+        again = g.loglik(th)
+        assert np.array_equal(again, out.cpu().numpy())  # deterministic
+
+
+def test_mixed_is_not_the_fp64_path():
+    # the mixed path must actually change the arithmetic (FP32 bulk)
+    d = synth.small()
+    with mra.MRA(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"]) as g:
+        a = g.loglik(d["theta"])
+        g.set_precision("mixed")
+        b = g.loglik(d["theta"])
+    assert a[0] != b[0] and abs(a[0] - b[0]) / 4096 <= TOLMIX
