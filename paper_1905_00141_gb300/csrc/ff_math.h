@@ -1,0 +1,179 @@
+// ff_math.h -- double-float ("ff") arithmetic on the FP32 pipe: a value is an
+// unevaluated pair hi + lo of floats (about 48 significant bits).  GB300
+// executes FP32 at 64 times its FP64 rate, so the few places of the mixed
+// mode that need more than FP32 accuracy use these error-free transformations
+// instead of FP64 instructions.
+//
+// Building blocks: TwoSum and FastTwoSum (Knuth; Dekker), TwoProd with a
+// fused multiply-add, and the double-float add/multiply/square-root built on
+// them (Dekker, "A floating-point technique for extending the available
+// precision", Numer. Math. 18, 1971).  exp(-x) is table driven (Tang, ACM TOMS
+// 15, 1989): x = k ln2/64 + r with |r| <= ln2/128, exp(-x) = 2^(-k/64) exp(-r),
+// 2^(-j/64) tabulated as float pairs, exp(-r) by its Taylor series.
+//
+// Every operation goes through FADD/FMUL/FFMA so that neither nvcc nor the
+// host compiler can contract or reassociate it; the host build (CPU tests)
+// must use -ffp-contract=off.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+
+#include "ff_tables.h"
+
+#ifdef __CUDACC__
+#define MRA_HD __host__ __device__ __forceinline__
+#else
+#define MRA_HD inline
+#endif
+
+namespace mra {
+
+#if defined(__CUDA_ARCH__)
+#define FADD(a, b) __fadd_rn((a), (b))
+#define FSUB(a, b) __fsub_rn((a), (b))
+#define FMUL(a, b) __fmul_rn((a), (b))
+#define FFMA(a, b, c) __fmaf_rn((a), (b), (c))
+#else
+#define FADD(a, b) ((a) + (b))
+#define FSUB(a, b) ((a) - (b))
+#define FMUL(a, b) ((a) * (b))
+#define FFMA(a, b, c) fmaf((a), (b), (c))
+#endif
+
+struct ff {
+    float hi, lo;
+};
+
+MRA_HD ff ff_from_double(double v)
+{
+    const float h = (float)v;
+    return ff{h, (float)(v - (double)h)};
+}
+MRA_HD double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+MRA_HD ff two_sum(float a, float b)
+{
+    const float s = FADD(a, b);
+    const float z = FSUB(s, a);
+    const float e = FADD(FSUB(a, FSUB(s, z)), FSUB(b, z));
+    return ff{s, e};
+}
+// |a| >= |b|
+MRA_HD ff fast_two_sum(float a, float b)
+{
+    const float s = FADD(a, b);
+    return ff{s, FSUB(b, FSUB(s, a))};
+}
+MRA_HD ff two_prod(float a, float b)
+{
+    const float p = FMUL(a, b);
+    return ff{p, FFMA(a, b, -p)};
+}
+MRA_HD ff ff_add(ff a, ff b)
+{
+    const ff s = two_sum(a.hi, b.hi);
+    const ff t = two_sum(a.lo, b.lo);
+    ff u = fast_two_sum(s.hi, FADD(s.lo, t.hi));
+    return fast_two_sum(u.hi, FADD(u.lo, t.lo));
+}
+MRA_HD ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+MRA_HD ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+MRA_HD ff ff_add_f(ff a, float b)
+{
+    const ff s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, FADD(s.lo, a.lo));
+}
+MRA_HD ff ff_mul(ff a, ff b)
+{
+    const ff p = two_prod(a.hi, b.hi);
+    const float c = FFMA(a.hi, b.lo, FMUL(a.lo, b.hi));
+    return fast_two_sum(p.hi, FADD(p.lo, c));
+}
+MRA_HD ff ff_sqr(ff a)
+{
+    const ff p = two_prod(a.hi, a.hi);
+    const float c = FMUL(FADD(a.hi, a.hi), a.lo);
+    return fast_two_sum(p.hi, FADD(p.lo, c));
+}
+MRA_HD ff ff_sqrt(ff a)
+{
+    if (!(a.hi > 0.f)) return ff{0.f, 0.f};
+    const float s = sqrtf(a.hi);
+    const ff p = two_prod(s, s);
+    const float r = FADD(FSUB(FSUB(a.hi, p.hi), p.lo), a.lo);
+    return fast_two_sum(s, FMUL(r, FMUL(0.5f, 1.0f / s)));
+}
+
+MRA_HD ff ff_mul_f(ff a, float b)
+{
+    const ff p = two_prod(a.hi, b);
+    return fast_two_sum(p.hi, FFMA(a.lo, b, p.lo));
+}
+// 1/sqrt(d) for d > 0: FP32 estimate and one Newton step evaluated in pairs.
+MRA_HD ff ff_rsqrt(ff d)
+{
+#if defined(__CUDA_ARCH__)
+    const float r = rsqrtf(d.hi);
+#else
+    const float r = 1.0f / sqrtf(d.hi);
+#endif
+    const ff t = ff_mul(d, two_prod(r, r));
+    const float e = FSUB(FSUB(1.0f, t.hi), t.lo);
+    return fast_two_sum(r, FMUL(FMUL(r, e), 0.5f));
+}
+// 1/d: FP32 estimate and one Newton step evaluated in pairs.
+MRA_HD ff ff_rcp(ff d)
+{
+    const float q = 1.0f / d.hi;
+    const ff t = ff_mul_f(d, q);
+    const float e = FSUB(FSUB(1.0f, t.hi), t.lo);
+    return fast_two_sum(q, FMUL(q, e));
+}
+// log of a positive pair: natural log of hi plus the first-order term lo/hi.
+MRA_HD double ff_log(ff a) { return (double)logf(a.hi) + (double)(a.lo / a.hi); }
+
+// 2^(-j/64) as float pairs; device copy in global memory (per-lane indices
+// diverge, which constant memory would serialise).
+#ifdef __CUDACC__
+static __device__ const ff kFFExp2Dev[64] = MRA_FF_EXP2_TABLE;
+#endif
+static const ff kFFExp2Host[64] = MRA_FF_EXP2_TABLE;
+
+// exp(-x) for x >= 0 (x as a float pair); 0 below float range.
+MRA_HD ff ff_exp_neg(ff x)
+{
+    if (!(x.hi < 87.0f)) return ff{0.f, 0.f};
+#if defined(__CUDA_ARCH__)
+    const ff *tab = kFFExp2Dev;
+#else
+    const ff *tab = kFFExp2Host;
+#endif
+    const float kf = rintf(FMUL(x.hi, MRA_FF_INV_C));
+    const int k = (int)kf;
+    // r = x - k (C1 + C2 + C3); k C1 is exact and close to x.hi
+    const float t1 = FSUB(x.hi, FMUL(kf, MRA_FF_C1));
+    const ff p2 = two_prod(kf, MRA_FF_C2);
+    ff r = two_sum(t1, -p2.hi);
+    r = fast_two_sum(r.hi, FADD(r.lo, FSUB(FSUB(x.lo, p2.lo), FMUL(kf, MRA_FF_C3))));
+    // exp(-r) = 1 - r + r^2/2 - q, q = r^3 (1/6 - r/24 + r^2/120 - r^3/720) in float
+    const float rh = r.hi;
+    const float poly = FFMA(rh, FFMA(rh, FFMA(rh, -1.0f / 720.0f, 1.0f / 120.0f), -1.0f / 24.0f), 1.0f / 6.0f);
+    const float q = FMUL(FMUL(FMUL(rh, rh), rh), poly);
+    ff s = ff_add(ff{1.0f, 0.0f}, ff_neg(r));
+    const ff r2 = ff_sqr(r);
+    s = ff_add(s, ff{FMUL(r2.hi, 0.5f), FMUL(r2.lo, 0.5f)});
+    s = ff_add_f(s, -q);
+    const ff e = ff_mul(s, tab[k & 63]);
+    const int a = k >> 6;
+    return ff{ldexpf(e.hi, -a), ldexpf(e.lo, -a)};
+}
+
+// sigma2 * exp(-|p - q| / beta) from float-pair coordinates and parameters.
+MRA_HD ff ff_cov_exp(ff s2, ff ib, ff px, ff py, ff qx, ff qy)
+{
+    const ff dx = ff_sub(px, qx), dy = ff_sub(py, qy);
+    const ff d = ff_sqrt(ff_add(ff_sqr(dx), ff_sqr(dy)));
+    return ff_mul(s2, ff_exp_neg(ff_mul(d, ib)));
+}
+
+} // namespace mra

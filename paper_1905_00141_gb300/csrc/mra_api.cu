@@ -255,9 +255,10 @@ struct mra_ctx {
     std::string err;
     // device tree
     double *d_kx = nullptr, *d_ky = nullptr, *d_sx = nullptr, *d_sy = nullptr, *d_sz = nullptr;
+    double *d_cx = nullptr, *d_cy = nullptr;
     int64_t *d_leaf_off = nullptr;
-    Chunk *d_chunks = nullptr;
-    int nchunks = 0;
+    Chunk *d_chunks32 = nullptr, *d_chunks64 = nullptr; // leaf-basis chunks of 32 (FP64) / 64 (FP32) rows
+    int nchunks32 = 0, nchunks64 = 0;
     int64_t *d_leaves32 = nullptr, *d_leaves64 = nullptr;
     int nl32 = 0, nl64 = 0, nmax64 = 64;
     BigLeaf *d_big = nullptr;
@@ -314,7 +315,7 @@ mra_status dev_upload(mra_ctx *c, T **dst, const T *src, size_t count)
 // T-typed parts, doubles for the rest).
 struct Plan {
     size_t prior = 0, prior_lvl[MRA_MAXM + 1] = {0};
-    size_t U = 0, y = 0, leafdu = 0, V = 0;
+    size_t U = 0, leafw = 0, leafdu = 0, V = 0;
     size_t Ain = 0, Ainw = 0, Aindu = 0;
     size_t Atil[MRA_MAXM + 1] = {0}, Atilw[MRA_MAXM + 1] = {0}, Atildu[MRA_MAXM + 1] = {0};
     size_t t_elems = 0, d_elems = 0; // totals
@@ -333,7 +334,7 @@ Plan make_plan(const mra_ctx *c)
     }
     p.prior = acc;
     p.U = (size_t)P.n_used * (size_t)(M - 1) * RP;
-    p.y = (size_t)P.n_used;
+    p.leafw = (size_t)P.nleaf() * (size_t)(M - 1) * RP;
     p.leafdu = 2 * (size_t)P.nleaf();
     p.V = (size_t)c->vbig_elems;
     if (M >= 2) {
@@ -349,9 +350,9 @@ Plan make_plan(const mra_ctx *c)
         }
     }
     (void)J;
-    p.t_elems = p.prior + p.U + p.Ain;
+    p.t_elems = p.prior + p.U + p.leafw + p.Ain;
     for (int m = 2; m <= M - 1; m++) p.t_elems += p.Atil[m];
-    p.d_elems = p.y + p.leafdu + p.V + p.Ainw + p.Aindu;
+    p.d_elems = p.leafdu + p.V + p.Ainw + p.Aindu;
     for (int m = 2; m <= M - 1; m++) p.d_elems += p.Atilw[m] + p.Atildu[m];
     return p;
 }
@@ -389,8 +390,8 @@ Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
     for (int m = 0; m <= MRA_MAXM; m++) w.prior_lvl[m] = p.prior_lvl[m];
     w.U = takeT8(p.U);
     w.U_stride = p.U;
-    w.ybuf = takeD(p.y);
-    w.y_stride = p.y;
+    w.leaf_w = takeT8(p.leafw);
+    w.leafw_stride = p.leafw;
     w.leaf_du = takeD(p.leafdu);
     w.leafdu_stride = p.leafdu;
     w.Vbig = takeD(p.V);
@@ -419,7 +420,7 @@ size_t scratch_bytes_for(const Plan &p, const mra_ctx *c, int B)
     auto add = [&](size_t elems) { s = align256(s + elems * (size_t)B * sizeof(double)); };
     add(p.prior);
     add(p.U);
-    add(p.y);
+    add(p.leafw);
     add(p.leafdu);
     add(p.V);
     add(p.Ain);
@@ -445,6 +446,8 @@ DevTree dev_tree(const mra_ctx *c)
     t.n_used = c->P.n_used;
     t.kx = c->d_kx;
     t.ky = c->d_ky;
+    t.cx = c->d_cx;
+    t.cy = c->d_cy;
     t.sx = c->d_sx;
     t.sy = c->d_sy;
     t.sz = c->d_sz;
@@ -490,9 +493,11 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     c->launches_last = 0;
     for (int m = 1; m < M; m++)
         if ((e = timed_launch(c, K_PRIOR, s, [&] { return launch_prior<T, RP>(t, w, m, B, s); }))) return e;
-    if (M > 1 && c->nchunks > 0)
+    const Chunk *chunks = sizeof(T) == 4 ? c->d_chunks64 : c->d_chunks32;
+    const int nchunks = sizeof(T) == 4 ? c->nchunks64 : c->nchunks32;
+    if (M > 1 && nchunks > 0)
         if ((e = timed_launch(c, K_LEAFBASIS, s,
-                              [&] { return launch_leafbasis<T, RP>(t, w, c->d_chunks, c->nchunks, B, s); })))
+                              [&] { return launch_leafbasis<T, RP>(t, w, chunks, nchunks, B, s); })))
             return e;
     if (c->nl32 > 0)
         if ((e = timed_launch(c, K_LEAFPOST, s,
@@ -540,10 +545,12 @@ size_t max_smem_needed(const mra_ctx *c, int nmax64)
         }
     }
     if (c->RP == 16) {
+        upd(smem_leafgram<double, 16>(M));
         upd(smem_leafbasis<double, 16>(M));
         upd(smem_leafpost_small<double, 16>(M, 32));
         if (nmax64 > 0) upd(smem_leafpost_small<double, 16>(M, nmax64));
     } else {
+        upd(smem_leafgram<double, 32>(M));
         upd(smem_leafbasis<double, 32>(M));
         upd(smem_leafpost_small<double, 32>(M, 32));
         if (nmax64 > 0) upd(smem_leafpost_small<double, 32>(M, nmax64));
@@ -781,17 +788,24 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     cudaError_t e = cudaSetDevice(opt.device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     // work lists
-    std::vector<Chunk> chunks;
+    if (M - 1 > 12) {
+        c->err = "M - 1 > 12 levels above the leaves is not supported by this build";
+        return MRA_EINVAL;
+    }
+    std::vector<Chunk> chunks32, chunks64;
     if (M > 1) {
         const int64_t nP = P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1];
         for (int64_t p = 0; p < nP; p++) {
             const int64_t r0 = P.leaf_off[(size_t)(p * J)], r1 = P.leaf_off[(size_t)((p + 1) * J)];
-            for (int64_t rb = r0; rb < r1; rb += MRA_CH) {
-                Chunk ch;
-                ch.parent = (int32_t)p;
-                ch.n = (int32_t)std::min<int64_t>(MRA_CH, r1 - rb);
-                ch.row0 = rb;
-                chunks.push_back(ch);
+            for (int rows : {32, 64}) {
+                std::vector<Chunk> &dst = rows == 32 ? chunks32 : chunks64;
+                for (int64_t rb = r0; rb < r1; rb += rows) {
+                    Chunk ch;
+                    ch.parent = (int32_t)p;
+                    ch.n = (int32_t)std::min<int64_t>(rows, r1 - rb);
+                    ch.row0 = rb;
+                    dst.push_back(ch);
+                }
             }
         }
     }
@@ -817,7 +831,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
             l64.push_back(l);
         } else {
             big.push_back(BigLeaf{l, voff});
-            voff += 2 * nl * nl; // V (FP64) and a copy of its factor in the storage type
+            voff += big_leaf_scratch(nl);
         }
     }
     c->vbig_elems = voff;
@@ -828,17 +842,25 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
             kxp[(size_t)(g * c->RP + j)] = P.kx[(size_t)(g * P.R + j)];
             kyp[(size_t)(g * c->RP + j)] = P.ky[(size_t)(g * P.R + j)];
         }
+    std::vector<double> cxv((size_t)std::max<int64_t>(P.nnonleaf(), 1), 0.0), cyv(cxv.size(), 0.0);
+    for (int64_t g = 0; g < P.nnonleaf(); g++) {
+        cxv[(size_t)g] = P.bx0[(size_t)g];
+        cyv[(size_t)g] = P.by0[(size_t)g];
+    }
     if ((st = dev_upload(c, &c->d_kx, kxp.data(), kxp.size())) || (st = dev_upload(c, &c->d_ky, kyp.data(), kyp.size())) ||
+        (st = dev_upload(c, &c->d_cx, cxv.data(), cxv.size())) || (st = dev_upload(c, &c->d_cy, cyv.data(), cyv.size())) ||
         (st = dev_upload(c, &c->d_sx, P.sx.data(), P.sx.size())) || (st = dev_upload(c, &c->d_sy, P.sy.data(), P.sy.size())) ||
         (st = dev_upload(c, &c->d_sz, P.sz.data(), P.sz.size())) ||
         (st = dev_upload(c, &c->d_leaf_off, P.leaf_off.data(), P.leaf_off.size())) ||
-        (st = dev_upload(c, &c->d_chunks, chunks.data(), chunks.size())) ||
+        (st = dev_upload(c, &c->d_chunks32, chunks32.data(), chunks32.size())) ||
+        (st = dev_upload(c, &c->d_chunks64, chunks64.data(), chunks64.size())) ||
         (st = dev_upload(c, &c->d_leaves32, l32.data(), l32.size())) ||
         (st = dev_upload(c, &c->d_leaves64, l64.data(), l64.size())) || (st = dev_upload(c, &c->d_big, big.data(), big.size()))) {
         *out = c;
         return st;
     }
-    c->nchunks = (int)chunks.size();
+    c->nchunks32 = (int)chunks32.size();
+    c->nchunks64 = (int)chunks64.size();
     c->nl32 = (int)l32.size();
     c->nl64 = (int)l64.size();
     c->nbig = (int)big.size();
@@ -1052,7 +1074,8 @@ void mra_free(mra_ctx *c)
 {
     if (!c) return;
     if (c->device >= 0 && c->d_sx) cudaSetDevice(c->device);
-    void *ptrs[] = {c->d_kx, c->d_ky, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks, c->d_leaves32,
+    void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
+                    c->d_chunks64, c->d_leaves32,
                     c->d_leaves64, c->d_big, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
                     c->d_reg_du, c->d_reg_lw};
     for (void *p : ptrs)

@@ -2,26 +2,34 @@
 // orchestration of libmra.  Not part of the public ABI (include/mra.h).
 //
 // Layout in HBM (one context):
-//   knots      kx, ky [n_nonleaf][RP]      regions of levels 1..M-1, padded to RP
-//   obs        sx, sy, sz [n_used]          leaf order
+//   knots      kx, ky [n_nonleaf][RP]        regions of levels 1..M-1, padded to RP
+//   corners    cx, cy [n_nonleaf]            lower-left corner of each such region
+//   obs        sx, sy, sz [n_used]           leaf order
 //   leaf_off   [n_leaf + 1]
-// Per theta (stride-separated copies for a batch of B theta):
-//   prior      level m, region i: m blocks RP x RP (row-major): What^1..What^{m-1}
-//              then Linv = L^{-1}, L the Cholesky factor of W^m = C_m(Q, Q).
-//   U          [n_used][(M-1) RP]: the whitened leaf basis What^l of every
-//              observation, overwritten in place by Y = L_V^{-1} U.
-//   y          [n_used]            L_V^{-1} z
-//   Ain        level M-1 regions: A = sum over the leaf children of Y'Y,
-//              packed upper blocks (k <= l), pair index l(l-1)/2 + k-1
-//   Atil[m]    level m regions (2 <= m <= M-1): ATilde after the region's step,
-//              blocks (k <= l <= m-1), same packing, plus w (double) and (d, u).
+// Per theta (stride-separated copies for a batch of B theta), storage type T:
+//   prior      level m, region i: m blocks of RP x RP, each stored column-major
+//              (element (j, t) at t*RP + j): What^1..What^{m-1}, then
+//              Linv = L^{-1}, L the Cholesky factor of W^m = C_m(Q, Q).
+//   U          [n_used][(M-1) RP] row-major: the whitened leaf basis What^l of
+//              every observation, overwritten in place by Y = L_V^{-1} U.
+//   leaf_w     [n_leaf][(M-1) RP]  w_c = Y_c' y_c of each leaf
+//   leaf_du    [n_leaf][2]         (log|V_c|, y_c'y_c)
+//   Ain        level M-1 regions: A = sum over the leaf children of Y'Y, packed
+//              upper blocks (k <= l, pair index l(l-1)/2 + k-1), each RP x RP
+//              row-major; Ain_w (FP64) the summed w, Ain_du the summed (d, u).
+//   Atil[m]    level m regions (2 <= m <= M-1): ATilde after the region's
+//              step, blocks (k <= l <= m-1), same packing, plus w (FP64) and (d, u).
 #pragma once
 #include <cstddef>
 #include <cstdint>
 
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+
 #define MRA_MAXM 24
 #define MRA_NT 256
-#define MRA_CH 32 /* observation rows per leaf-basis chunk */
 
 namespace mra {
 
@@ -29,6 +37,7 @@ struct DevTree {
     int M, J, lgJ, R, RP;
     int64_t n_used;
     const double *kx, *ky;
+    const double *cx, *cy;
     const double *sx, *sy, *sz;
     const int64_t *leaf_off;
     int64_t lvl_off[MRA_MAXM + 2]; // first global region id of level m (1-based)
@@ -44,14 +53,14 @@ struct Work {
     size_t prior_lvl[MRA_MAXM + 1]; // element offset of level m inside one theta's prior
     T *U;
     size_t U_stride;
-    double *ybuf;
-    size_t y_stride;
+    T *leaf_w;
+    size_t leafw_stride;
     double *leaf_du; // [nleaf][2]
     size_t leafdu_stride;
-    double *Vbig; // big-leaf V scratch
+    double *Vbig; // big-leaf scratch
     size_t V_stride;
-    T *Ain;       // [nP][npairs(M-1)][RP*RP]
-    double *Ain_w; // [nP][(M-1) RP]
+    T *Ain;         // [nP][npairs(M-1)][RP*RP]
+    double *Ain_w;  // [nP][(M-1) RP]
     double *Ain_du; // [nP][2]
     size_t Ain_stride, Ainw_stride, Aindu_stride;
     T *Atil[MRA_MAXM + 1];
@@ -65,14 +74,22 @@ struct Work {
 
 struct Chunk {
     int32_t parent; // level M-1 region index
-    int32_t n;      // rows in this chunk (<= MRA_CH)
+    int32_t n;      // rows in this chunk (<= chunk rows of the precision)
     int64_t row0;   // first observation row
 };
 
 struct BigLeaf {
     int64_t leaf;
-    int64_t voff; // element offset of its V in Vbig
+    int64_t voff; // element offset (doubles) of its scratch in Vbig
 };
+
+// Scratch of one large leaf in Vbig, in 8-byte slots: V (n^2), its factor in
+// the storage type (n^2), y (n), reciprocal pivots (n), 1/diag in the storage
+// type (n).
+inline int64_t big_leaf_scratch(int64_t n) { return 2 * n * n + 3 * n; }
+
+// Observation rows per leaf-basis chunk: 64 in FP32, 32 in FP64 (shared memory).
+template <typename T> __host__ __device__ constexpr int chunk_rows() { return sizeof(T) == 4 ? 64 : 32; }
 
 // Launchers (one instantiation per precision T and padding RP).
 template <typename T, int RP>
@@ -93,10 +110,11 @@ int launch_up(const DevTree &t, const Work<T> &w, int m, int B, void *stream);
 template <typename T, int RP>
 int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream);
 
-// Dynamic shared memory (bytes) each kernel needs; 0 when beyond the limit.
+// Dynamic shared memory (bytes) each kernel needs.
 template <typename T, int RP> size_t smem_prior(int m);
 template <typename T, int RP> size_t smem_leafbasis(int M);
 template <typename T, int RP> size_t smem_leafpost_small(int M, int nmax);
 template <typename T, int RP> size_t smem_up(int m);
+template <typename T, int RP> size_t smem_leafgram(int M);
 
 } // namespace mra

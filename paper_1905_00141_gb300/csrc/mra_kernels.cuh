@@ -1,36 +1,53 @@
 // mra_kernels.cuh -- sm_103a kernels of the MRA log-likelihood.
 //
-// The GPU evaluates the same likelihood as the paper's MRA (Sec. 1.1) in a
-// whitened basis: with L_A the Cholesky factor of W^l_A = C_l(Q_A, Q_A) and
-// Linv_A = L_A^{-1}, the basis of any point set P against its level-l ancestor
-// A_l is What^l_P = C_l(P, Q_{A_l}) Linv_{A_l}', which turns the recursion of
-// the remainder covariances into
-//     W^l_P   = C(P, Q_{A_l}) - sum_{k<l} What^k_P (What^k_{A_l})'
+// The GPU evaluates the likelihood of the paper's MRA (Sec. 1.1) in a whitened
+// basis.  With L_A the Cholesky factor of W^l_A = C_l(Q_A, Q_A) and
+// Linv_A = L_A^{-1}, the basis of a point set P against its level-l ancestor
+// A_l is What^l_P = C_l(P, Q_{A_l}) Linv_{A_l}', and the recursion of the
+// remainder covariances becomes
+//     W^l_P    = C(P, Q_{A_l}) - sum_{k<l} What^k_P (What^k_{A_l})'
 //     What^l_P = W^l_P Linv_{A_l}'
-// and the prior precision of every level into the identity.  The upward pass
-// then factors I + A^{m,m} instead of K^{-1} + A^{m,m}; log-determinants and
-// quadratic forms are unchanged (|K^{-1} + A| / |K^{-1}| = |I + L^{-1} A L^{-T}|).
+// with an identity prior precision at every level.  The upward pass then
+// factors I + A^{m,m}; log-determinants and quadratic forms are unchanged
+// (|K^{-1} + A| / |K^{-1}| = |I + L^{-1} A L^{-T}|).
 //
-// One CTA of 256 threads works on one region (prior, upward pass), one chunk
-// of 32 observation rows (leaf basis), one leaf (leaf posterior) or one
-// (region, block pair) (leaf Gram).  r_hat knots are padded to RP (16 or 32)
-// with inert padding: zero covariance rows and columns and an identity
-// diagonal on the padded part of every factor, which leaves every result
-// exact.  Cholesky factors, log-determinants and quadratic forms are FP64 in
-// both precisions; T is the storage and product type (double, or float for
-// the mixed mode).
+// Work decomposition (256 threads per CTA): one CTA per region for the prior
+// and the upward pass, one per chunk of observation rows for the leaf basis,
+// one per leaf for the leaf posterior, one per (level-(M-1) region, block
+// column) for the leaf Gram.  r_hat knots are padded to RP (16 or 32) with
+// inert padding (zero covariance rows and columns, identity on the padded
+// diagonal of every factor), which leaves every result exact.
+//
+// Precision: T is the storage and product type (double, or float in the mixed
+// mode).  Cholesky factors, log-determinants, quadratic forms and the
+// accumulation of the leaf-level y vectors are FP64 in both modes.  In the
+// mixed mode the leaf covariance C + tau2 I - U U' is formed with exact FP32
+// products summed as unevaluated float pairs and an exact leading subtraction,
+// so its FP32 rounding is relative to V itself and not to C.
+//
+// Operand layouts in shared memory are "k-major": a row-block X (rows x K) is
+// stored as X[k][row], so the inner product loops read contiguous vectors.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
+#include "ff_math.h"
 #include "mra_internal.h"
 
 namespace mra {
 
 constexpr int NT = MRA_NT;
-enum { MM_SET = 0, MM_SUB = 1 };
 enum { ST_OK = 0, ST_EINVAL = 1, ST_ENOTPD = 3 };
+
+// Singularity rule shared by every factorisation: a pivot at or below
+// MRA_SINGULAR times the largest diagonal entry of the matrix is singular
+// (coincident knots make the covariance singular, Sec. 1.2).
+#define MRA_SINGULAR 1e-12
+
+__host__ __device__ __forceinline__ int npairs(int D) { return D * (D + 1) / 2; }
+__host__ __device__ __forceinline__ int pidx(int k, int l) { return l * (l - 1) / 2 + k - 1; }
+__host__ __device__ __forceinline__ constexpr int tri_count(int w) { return w * (w + 1) / 2; }
 
 __device__ __forceinline__ bool theta_ok(const double *th)
 {
@@ -38,61 +55,71 @@ __device__ __forceinline__ bool theta_ok(const double *th)
            th[2] > 0.0;
 }
 
-// Exponential covariance sigma2 * exp(-|a - b| / beta) (Sec. 2.2.4 reading).
+__device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// Covariance parameters in the storage type.
 template <typename T>
-__device__ __forceinline__ T cov_exp(double s2, double beta, double ax, double ay, double bx,
-                                     double by);
-template <>
-__device__ __forceinline__ double cov_exp<double>(double s2, double beta, double ax, double ay,
-                                                  double bx, double by)
+struct CovP {
+    T s2, ib; // sigma2 and 1/beta
+    __device__ CovP(const double *th) : s2((T)th[0]), ib((T)(1.0 / th[1])) {}
+};
+
+// Exponential covariance sigma2 * exp(-|d| / beta) of a coordinate difference
+// (Sec. 2.2.4 reading of "exponential covariance function").
+__device__ __forceinline__ double cov_d(const CovP<double> &c, double dx, double dy)
 {
-    double dx = ax - bx, dy = ay - by;
-    return s2 * exp(-sqrt(dx * dx + dy * dy) / beta);
+    return c.s2 * exp(-sqrt(dx * dx + dy * dy) * c.ib);
 }
-template <>
-__device__ __forceinline__ float cov_exp<float>(double s2, double beta, double ax, double ay,
-                                                double bx, double by)
+__device__ __forceinline__ float cov_d(const CovP<float> &c, float dx, float dy)
 {
-    float dx = (float)(ax - bx), dy = (float)(ay - by);
-    return (float)s2 * expf(-sqrtf(dx * dx + dy * dy) / (float)beta);
+    return c.s2 * expf(-sqrtf(dx * dx + dy * dy) * c.ib);
 }
 
-// sum_k a[k] b[k] (strides sa, sb) returned in FP64.  FP64 operands: plain
-// FMA chain.  FP32 operands: every product is split exactly (TwoProd with an
-// FMA) and accumulated as an unevaluated float pair (TwoSum), so the result is
-// accurate to ~K eps_32^2 of the terms, which keeps C + tau2 I - U U' free of
-// FP32 cancellation error in the mixed mode.
-__device__ __forceinline__ double dot_acc(const double *a, int sa, const double *b, int sb, int K)
+// ------------------------------------------------------------ small tools --
+template <typename T, int N>
+__device__ __forceinline__ void ldv(T (&r)[N], const T *p)
 {
-    double s = 0.0;
-    for (int k = 0; k < K; k++) s = fma(a[k * sa], b[k * sb], s);
-    return s;
-}
-__device__ __forceinline__ double dot_acc(const float *a, int sa, const float *b, int sb, int K)
-{
-    float hi = 0.f, lo = 0.f;
-    for (int k = 0; k < K; k++) {
-        const float x = a[k * sa], y = b[k * sb];
-        const float p = __fmul_rn(x, y);
-        const float e = __fmaf_rn(x, y, -p);
-        const float t = __fadd_rn(hi, p);
-        const float z = __fsub_rn(t, hi);
-        const float r = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(p, z));
-        hi = t;
-        lo = __fadd_rn(lo, __fadd_rn(r, e));
+    if constexpr (sizeof(T) == 4 && N == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else if constexpr (sizeof(T) == 8 && N == 2) {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        r[0] = v.x; r[1] = v.y;
+    } else if constexpr (sizeof(T) == 4 && N == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        r[0] = v.x; r[1] = v.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; i++) r[i] = p[i];
     }
-    return (double)hi + (double)lo;
+}
+
+// Copy n elements (a multiple of 16 bytes, 16-byte aligned on both sides)
+// from global to shared memory.
+template <typename T>
+__device__ __forceinline__ void copy_g2s(T *s, const T *g, int n)
+{
+    const int4 *src = reinterpret_cast<const int4 *>(g);
+    int4 *dst = reinterpret_cast<int4 *>(s);
+    const int nv = n * (int)sizeof(T) / 16;
+    for (int e = threadIdx.x; e < nv; e += NT) dst[e] = src[e];
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    v = warp_sum(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) red[wid] = v;
     __syncthreads();
     if (wid == 0) {
         v = lane < NT / 32 ? red[lane] : 0.0;
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        v = warp_sum(v);
         if (lane == 0) red[0] = v;
     }
     __syncthreads();
@@ -101,345 +128,693 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     return v;
 }
 
-// Singularity rule shared by every factorisation: a pivot at or below
-// kSingular times the largest diagonal entry of the matrix is singular
-// (coincident knots make the covariance singular, Sec. 1.2).
-#define MRA_SINGULAR 1e-12
+// Thread tile of a ROWS x COLS output spread over NT threads.
+template <int ROWS, int COLS>
+struct Tile {
+    static constexpr int OUT = ROWS * COLS / NT;
+    static constexpr int CT = OUT >= 4 ? 4 : OUT;
+    static constexpr int RT = OUT / CT;
+    static constexpr int TX = COLS / CT;
+    static_assert(OUT >= 1 && RT * CT == OUT && (ROWS / RT) * TX == NT, "tile shape");
+    __device__ static int r0() { return (threadIdx.x / TX) * RT; }
+    __device__ static int c0() { return (threadIdx.x % TX) * CT; }
+};
 
-// In-place lower Cholesky of the n x n matrix A (leading dimension lda) by the
-// whole CTA; a singular pivot sets *fail and is replaced by 1 so that the
-// factorisation completes without NaN.  Works on shared or global memory.
-static __device__ void chol_cta(double *A, int lda, int n, int *fail)
+// acc[r][c] += sum_t A[t][r0 + r] * B[t][c0 + c]  (both operands k-major)
+template <typename T, int ROWS, int COLS>
+__device__ __forceinline__ void tile_fma(T (&acc)[Tile<ROWS, COLS>::RT][Tile<ROWS, COLS>::CT], const T *A,
+                                         int lda, const T *B, int ldb, int K)
 {
-    __shared__ double s_scale;
-    if (threadIdx.x == 0) {
-        double sc = 0.0;
-        for (int j = 0; j < n; j++) sc = fmax(sc, A[j * lda + j]);
-        s_scale = sc;
-    }
-    __syncthreads();
-    const double tol = MRA_SINGULAR * s_scale;
-    for (int j = 0; j < n; j++) {
-        if (threadIdx.x == 0) {
-            double d = A[j * lda + j];
-            if (!(d > tol)) {
-                *fail = 1;
-                d = 1.0;
-            }
-            A[j * lda + j] = sqrt(d);
-        }
-        __syncthreads();
-        const double ljj = A[j * lda + j];
-        for (int i = j + 1 + threadIdx.x; i < n; i += NT) A[i * lda + j] /= ljj;
-        __syncthreads();
-        const int w = n - j - 1;
-        for (int e = threadIdx.x; e < w * w; e += NT) {
-            const int i = j + 1 + e / w, k = j + 1 + e % w;
-            if (k <= i) A[i * lda + k] -= A[i * lda + j] * A[k * lda + j];
-        }
-        __syncthreads();
-    }
-}
-
-// X = L^{-1} for lower-triangular L (n x n), one column per thread.
-static __device__ void trinv_cta(const double *L, int ldl, double *X, int ldx, int n)
-{
-    for (int j = threadIdx.x; j < n; j += NT) {
-        for (int i = 0; i < j; i++) X[i * ldx + j] = 0.0;
-        X[j * ldx + j] = 1.0 / L[j * ldl + j];
-        for (int i = j + 1; i < n; i++) {
-            double s = 0.0;
-            for (int t = j; t < i; t++) s += L[i * ldl + t] * X[t * ldx + j];
-            X[i * ldx + j] = -s / L[i * ldl + i];
-        }
-    }
-    __syncthreads();
-}
-
-// C (ROWS x RP) = or -= A (ROWS x K) * B (RP x K)'.  Caller synchronises.
-template <typename T, int ROWS, int RP>
-__device__ __forceinline__ void mm_nt(T *C, int ldc, const T *A, int lda, const T *B, int ldb,
-                                      int K, int mode)
-{
-    constexpr int CPT = ROWS * RP / NT;
-    static_assert(CPT >= 1 && (ROWS * RP) % NT == 0, "tile");
-    constexpr int TPR = RP / CPT;
-    const int i = threadIdx.x / TPR, j0 = threadIdx.x % TPR;
-    T acc[CPT];
-#pragma unroll
-    for (int c = 0; c < CPT; c++) acc[c] = T(0);
+    using TL = Tile<ROWS, COLS>;
+    const int r0 = TL::r0(), c0 = TL::c0();
+#pragma unroll 4
     for (int t = 0; t < K; t++) {
-        const T a = A[i * lda + t];
+        T a[TL::RT], b[TL::CT];
+        ldv<T, TL::RT>(a, A + t * lda + r0);
+        ldv<T, TL::CT>(b, B + t * ldb + c0);
 #pragma unroll
-        for (int c = 0; c < CPT; c++) acc[c] += a * B[(j0 + c * TPR) * ldb + t];
-    }
+        for (int r = 0; r < TL::RT; r++)
 #pragma unroll
-    for (int c = 0; c < CPT; c++) {
-        T *p = C + i * ldc + j0 + c * TPR;
-        *p = mode == MM_SET ? acc[c] : *p - acc[c];
+            for (int c = 0; c < TL::CT; c++) acc[r][c] = fma(a[r], b[c], acc[r][c]);
     }
 }
 
-template <typename T, int RP>
-__device__ __forceinline__ void load_block(T *s, const T *g)
+template <typename T, int RT, int CT>
+__device__ __forceinline__ void tile_zero(T (&acc)[RT][CT])
 {
-    constexpr int LD = RP + 1;
-    for (int e = threadIdx.x; e < RP * RP; e += NT) s[(e / RP) * LD + e % RP] = g[e];
+#pragma unroll
+    for (int r = 0; r < RT; r++)
+#pragma unroll
+        for (int c = 0; c < CT; c++) acc[r][c] = T(0);
 }
 
-__host__ __device__ __forceinline__ int npairs(int D) { return D * (D + 1) / 2; }
-__host__ __device__ __forceinline__ int pidx(int k, int l) { return l * (l - 1) / 2 + k - 1; }
+// Exact FP32 product sum: every product split by an FMA (TwoProd) and the
+// running sum kept as an unevaluated pair (hi, lo) by TwoSum.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ void ff_add_prod(FF &s, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);
+    const float t = __fadd_rn(s.hi, p);
+    const float z = __fsub_rn(t, s.hi);
+    const float r = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(r, e));
+}
+__device__ __forceinline__ void ff_add(FF &s, float p)
+{
+    const float t = __fadd_rn(s.hi, p);
+    const float z = __fsub_rn(t, s.hi);
+    const float r = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, r);
+}
+
+// sum_k a[k] b[k] returned as (hi, lo): FP32 pairs exact, FP64 plain.
+__device__ __forceinline__ void ff_merge(FF &s, const FF &o)
+{
+    ff_add(s, o.hi);
+    s.lo = __fadd_rn(s.lo, o.lo);
+}
+__device__ __forceinline__ void dot2(const float *a, const float *b, int K, float &hi, float &lo)
+{
+    // four independent pairs for instruction-level parallelism, merged exactly
+    FF s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f}, s3{0.f, 0.f};
+    int k = 0;
+    for (; k + 4 <= K; k += 4) {
+        ff_add_prod(s0, a[k], b[k]);
+        ff_add_prod(s1, a[k + 1], b[k + 1]);
+        ff_add_prod(s2, a[k + 2], b[k + 2]);
+        ff_add_prod(s3, a[k + 3], b[k + 3]);
+    }
+    for (; k < K; k++) ff_add_prod(s0, a[k], b[k]);
+    ff_merge(s0, s1);
+    ff_merge(s2, s3);
+    ff_merge(s0, s2);
+    hi = s0.hi;
+    lo = s0.lo;
+}
+__device__ __forceinline__ void dot2(const double *a, const double *b, int K, double &hi, double &lo)
+{
+    double s = 0.0;
+    for (int k = 0; k < K; k++) s = fma(a[k], b[k], s);
+    hi = s;
+    lo = 0.0;
+}
+
+// C - (hi + lo) with the leading subtraction done first: when C and hi agree
+// to a factor of two the difference is exact, so the rounding left is
+// relative to the (small) result.
+__device__ __forceinline__ double cancel_sub(float c, float hi, float lo)
+{
+    return (double)__fsub_rn(__fsub_rn(c, hi), lo);
+}
+__device__ __forceinline__ double cancel_sub(double c, double hi, double lo) { return (c - hi) - lo; }
+__device__ __forceinline__ double cancel_sub(double c, float hi, float lo) { return (c - (double)hi) - (double)lo; }
+
+// FP64 exponential covariance for the leaf covariance V, whose small
+// eigenvalues (~tau2) are far below C's entries (~sigma2): C must carry more
+// than FP32 accuracy there.
+__device__ __forceinline__ double cov64(double s2, double ib, double dx, double dy)
+{
+    return s2 * exp(-sqrt(dx * dx + dy * dy) * ib);
+}
+
+// ------------------------------------------------------------- Cholesky --
+// Factor arithmetic: F = double in the FP64 mode, F = ff (float pair, ~48-bit
+// mantissa, FP32 pipe) in the mixed mode.  On GB300 a warp-wide FP64
+// instruction holds its sub-partition's FP64 unit for ~64 cycles, so the
+// serial chains of a small Cholesky (pivots, triangular solves) run much
+// faster in float pairs at comparable accuracy.
+template <typename T> struct FacT { using type = double; };
+template <> struct FacT<float> { using type = ff; };
+
+__device__ __forceinline__ double f_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ ff f_mul(ff a, ff b) { return ff_mul(a, b); }
+__device__ __forceinline__ double f_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ ff f_sub(ff a, ff b) { return ff_sub(a, b); }
+__device__ __forceinline__ double f_add(double a, double b) { return a + b; }
+__device__ __forceinline__ ff f_add(ff a, ff b) { return ff_add(a, b); }
+__device__ __forceinline__ double f_sqr(double a) { return a * a; }
+__device__ __forceinline__ ff f_sqr(ff a) { return ff_sqr(a); }
+__device__ __forceinline__ double f_rsqrt(double a) { return rsqrt(a); }
+__device__ __forceinline__ ff f_rsqrt(ff a) { return ff_rsqrt(a); }
+__device__ __forceinline__ double f_hi(double a) { return a; }
+__device__ __forceinline__ float f_hi(ff a) { return a.hi; }
+__device__ __forceinline__ double f_dbl(double a) { return a; }
+__device__ __forceinline__ double f_dbl(ff a) { return ff_to_double(a); }
+template <typename F> __device__ __forceinline__ F f_of(double v);
+template <> __device__ __forceinline__ double f_of<double>(double v) { return v; }
+template <> __device__ __forceinline__ ff f_of<ff>(double v) { return ff_from_double(v); }
+template <typename F> __device__ __forceinline__ F f_of_f(float v);
+template <> __device__ __forceinline__ double f_of_f<double>(float v) { return (double)v; }
+template <> __device__ __forceinline__ ff f_of_f<ff>(float v) { return ff{v, 0.f}; }
+__device__ __forceinline__ double f_shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ ff f_shfl(ff v, int src)
+{
+    return ff{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+__device__ __forceinline__ double f_shfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ ff f_shfl_xor(ff v, int m)
+{
+    return ff{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+
+// Pair table of chol_small: the lower-triangle positions (i, k), k <= i < n,
+// ordered by decreasing k, so the trailing update of column j (pairs with
+// k > j) is a prefix.
+static __device__ void build_pairs(uint16_t *tab, int n)
+{
+    const int P = tri_count(n);
+    for (int e = threadIdx.x; e < P; e += NT) {
+        int w = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f) + 1;
+        while (tri_count(w) <= e) w++;
+        while (w > 1 && tri_count(w - 1) > e) w--;
+        const int k = n - w, i = k + (e - tri_count(w - 1));
+        tab[e] = (uint16_t)(i | (k << 8));
+    }
+}
+
+// Cholesky of a small (n <= 64) symmetric matrix in shared memory by the
+// whole CTA, one barrier per column.  Input: the lower triangle of A.  Output:
+// the factor L in the UPPER triangle, transposed (A[j][i] = L[i][j], i >= j,
+// diagonal included), and rs[j] = 1 / L_jj; the lower triangle is left as
+// scratch.  The owner of the next diagonal entry also forms its reciprocal
+// square root, so each pivot is ready at the barrier.  A pivot at or below
+// `rel` times the largest diagonal entry is singular: it sets *fail and is
+// replaced by 1.  rs: n + 1 entries of shared scratch.
+template <typename F>
+static __device__ void chol_small(F *A, int lda, int n, const uint16_t *tab, F *rs, int *fail, double rel)
+{
+    if (threadIdx.x < 32) {
+        double sc = 0.0;
+        for (int j = threadIdx.x; j < n; j += 32) sc = fmax(sc, (double)f_hi(A[j * lda + j]));
+        for (int o = 16; o; o >>= 1) sc = fmax(sc, __shfl_xor_sync(0xffffffffu, sc, o));
+        if (threadIdx.x == 0) {
+            const double tol = rel * sc;
+            F d = A[0];
+            if (!((double)f_hi(d) > tol)) {
+                *fail = 1;
+                d = f_of<F>(1.0);
+                A[0] = d;
+            }
+            rs[0] = f_rsqrt(d);
+            rs[n] = f_of<F>(tol);
+        }
+    }
+    __syncthreads();
+    const double tol = (double)f_hi(rs[n]);
+    for (int j = 0; j < n; j++) {
+        const F r = rs[j], r2 = f_sqr(r);
+        for (int i = j + threadIdx.x; i < n; i += NT) A[j * lda + i] = f_mul(A[i * lda + j], r);
+        const int P = tri_count(n - 1 - j);
+        for (int e = threadIdx.x; e < P; e += NT) {
+            const int p = tab[e], i = p & 0xff, k = p >> 8;
+            F v = f_sub(A[i * lda + k], f_mul(f_mul(A[i * lda + j], A[k * lda + j]), r2));
+            if (i == k && k == j + 1) {
+                if (!((double)f_hi(v) > tol)) {
+                    *fail = 1;
+                    v = f_of<F>(1.0);
+                }
+                rs[k] = f_rsqrt(v);
+            }
+            A[i * lda + k] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// 2 sum_j log L_jj of a chol_small factor, by warp 0.  FP64: the pivots are
+// multiplied as mantissas with a running exponent and one log is taken.
+// Float pairs: each lane splits its pivots into exponent and mantissa in
+// [1, 2) and sums logf of the mantissas (absolute error ~4e-8 per pivot).
+__device__ __forceinline__ double logdet_small(const double *A, int lda, int n, double *out)
+{
+    if (threadIdx.x < 32) {
+        double prod = 1.0;
+        int ex = 0;
+        for (int j = threadIdx.x; j < n; j += 32) {
+            int e;
+            prod = frexp(prod * A[j * lda + j], &e);
+            ex += e;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const double q = __shfl_xor_sync(0xffffffffu, prod, o);
+            const int eo = __shfl_xor_sync(0xffffffffu, ex, o);
+            int e;
+            prod = frexp(prod * q, &e);
+            ex += eo + e;
+        }
+        if (threadIdx.x == 0) *out = 2.0 * (log(prod) + (double)ex * 0.69314718055994530942);
+    }
+    __syncthreads();
+    const double v = *out;
+    __syncthreads();
+    return v;
+}
+__device__ __forceinline__ double logdet_small(const ff *A, int lda, int n, double *out)
+{
+    if (threadIdx.x < 32) {
+        ff s{0.f, 0.f};
+        int ex = 0;
+        for (int j = threadIdx.x; j < n; j += 32) {
+            const ff p = A[j * lda + j];
+            int e;
+            const float m = 2.0f * frexpf(p.hi, &e); // p.hi = m 2^(e-1), m in [1, 2)
+            ex += e - 1;
+            s = ff_add(s, ff{logf(m), p.lo / p.hi});
+        }
+        for (int o = 16; o; o >>= 1) {
+            s = ff_add(s, f_shfl_xor(s, o));
+            ex += __shfl_xor_sync(0xffffffffu, ex, o);
+        }
+        if (threadIdx.x == 0) *out = 2.0 * (ff_to_double(s) + (double)ex * 0.69314718055994530942);
+    }
+    __syncthreads();
+    const double v = *out;
+    __syncthreads();
+    return v;
+}
+
+// The factor of chol_small as a lower-triangular T matrix LT (ld ldt, zeros
+// above) and the reciprocals of its diagonal (from rs).
+template <typename F, typename T>
+__device__ void factor_to_T(const F *A, int lda, const F *rs, int n, T *LT, int ldt, T *dinv)
+{
+    for (int e = threadIdx.x; e < n * n; e += NT) {
+        const int i = e / n, j = e % n;
+        LT[i * ldt + j] = j <= i ? (T)f_hi(A[j * lda + i]) : T(0);
+    }
+    for (int j = threadIdx.x; j < n; j += NT) dinv[j] = (T)f_hi(rs[j]);
+    __syncthreads();
+}
+
+// y <- L^{-1} y with the chol_small factor (L[a][q] = A[q][a]) and rs = 1/L_jj,
+// by warp 0, right-looking: lane a (and a + 32) owns y[a]; after y[q] is
+// final it is broadcast and every later row subtracts its share.
+template <typename F>
+__device__ void fwd_solve_vec(const F *A, int lda, const F *rs, int n, F *y)
+{
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        F y0 = lane < n ? y[lane] : f_of<F>(0.0);
+        F y1 = lane + 32 < n ? y[lane + 32] : f_of<F>(0.0);
+        for (int q = 0; q < n; q++) {
+            const bool mine0 = (q == lane), mine1 = (q == lane + 32);
+            if (mine0) y0 = f_mul(y0, rs[q]);
+            if (mine1) y1 = f_mul(y1, rs[q]);
+            const F yq = q < 32 ? f_shfl(y0, q) : f_shfl(y1, q - 32);
+            if (lane > q && lane < n) y0 = f_sub(y0, f_mul(A[q * lda + lane], yq));
+            if (lane + 32 > q && lane + 32 < n) y1 = f_sub(y1, f_mul(A[q * lda + lane + 32], yq));
+        }
+        if (lane < n) y[lane] = y0;
+        if (lane + 32 < n) y[lane + 32] = y1;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double f_of_T(double v) { return v; }
+__device__ __forceinline__ ff f_of_T(float v) { return ff{v, 0.f}; }
+
+template <typename F>
+__device__ __forceinline__ F warp_sum_f(F v)
+{
+    for (int o = 16; o; o >>= 1) v = f_add(v, f_shfl_xor(v, o));
+    return v;
+}
+
+// In-place forward solve X <- L^{-1} X for ncol columns and n <= 64 rows, in
+// two register blocks of 32 rows: solve rows 0..31, subtract their share from
+// rows 32..63, solve those.  One thread per column.
+template <typename T, int MAXN>
+__device__ void fwd_solve_reg2(const T *LT, int ldt, const T *dinv, T *X, int ldx, int ncol, int n)
+{
+    static_assert(MAXN == 32 || MAXN == 64, "rows");
+    for (int col = threadIdx.x; col < ncol; col += NT) {
+        T x[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) x[i] = i < n ? X[(size_t)i * ldx + col] : T(0);
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            if (i < n) {
+                const T xi = x[i] * dinv[i];
+                x[i] = xi;
+#pragma unroll
+                for (int k = i + 1; k < 32; k++) x[k] = fma(-LT[k * ldt + i], xi, x[k]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 32; i++)
+            if (i < n) X[(size_t)i * ldx + col] = x[i];
+        if (MAXN > 32 && n > 32) {
+            T y[32];
+#pragma unroll
+            for (int i = 0; i < 32; i++) y[i] = 32 + i < n ? X[(size_t)(32 + i) * ldx + col] : T(0);
+#pragma unroll
+            for (int q = 0; q < 32; q++)
+#pragma unroll
+                for (int k = 0; k < 32; k++) y[k] = fma(-LT[(32 + k) * ldt + q], x[q], y[k]);
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+                if (32 + i < n) {
+                    const T yi = y[i] * dinv[32 + i];
+                    y[i] = yi;
+#pragma unroll
+                    for (int k = i + 1; k < 32; k++) y[k] = fma(-LT[(32 + k) * ldt + 32 + i], yi, y[k]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 32; i++)
+                if (32 + i < n) X[(size_t)(32 + i) * ldx + col] = y[i];
+        }
+    }
+    __syncthreads();
+}
 
 // ------------------------------------------------------------------ prior --
 // Region i of level m (1 <= m <= M-1): What^1..What^{m-1} against its
-// ancestors, then W^m = C(Q,Q) - sum_k What^k What^k', its Cholesky factor L,
-// log|W^m| and Linv = L^{-1}.
+// ancestors, then W^m = C(Q,Q) - sum_k What^k What^k', its Cholesky factor L
+// (FP64), log|W^m| and Linv = L^{-1}.
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_prior_bytes(int m)
 {
-    return (size_t)2 * RP * (RP + 1) * sizeof(double) + 4 * RP * sizeof(double) + 32 * sizeof(double) +
-           16 + (size_t)(m + 1) * RP * (RP + 1) * sizeof(T);
+    return (size_t)RP * (RP + 1) * sizeof(double) + (RP + 2) * sizeof(double) + 8 * sizeof(double) +
+           (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 + 4 * RP * sizeof(T) +
+           (size_t)(2 * m + 2) * RP * RP * sizeof(T) + RP * sizeof(T) + 64;
 }
 
 template <typename T, int RP>
 __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
 {
-    constexpr int LD = RP + 1;
+    using TL = Tile<RP, RP>;
+    using F = typename FacT<T>::type;
     const int i = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const double s2 = th[0], beta = th[1];
+    const CovP<T> cp(th);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *sL = (double *)smem_raw;
-    double *sX = sL + RP * LD;
-    double *sq = sX + RP * LD;
-    double *sa = sq + 2 * RP;
-    double *red = sa + 2 * RP;
-    int *flag = (int *)(red + 32);
-    T *sW = (T *)(flag + 4);
-    T *sA = sW + RP * LD;
-    T *sWh = sA + RP * LD;
+    F *sL = (F *)smem_raw;                  // RP x (RP+1)
+    F *srs = sL + RP * (RP + 1);            // RP + 2
+    double *red = (double *)(srs + RP + 2); // 8
+    uint16_t *tab = (uint16_t *)(red + 8);  // tri(RP)
+    int *flag = (int *)((unsigned char *)tab + ((tri_count(RP) * 2 + 15) & ~15));
+    T *sq = (T *)(flag + 16);               // own knots relative to the current origin: 2 RP
+    T *sa = sq + 2 * RP;                    // ancestor knots: 2 RP
+    T *sU = sa + 2 * RP;                    // (m-1) blocks k-major [t][row]
+    T *sB = sU + (size_t)(m - 1) * RP * RP; // up to m blocks of the ancestor (column-major)
+    T *sW = sB + (size_t)m * RP * RP;       // RP x RP k-major
+    T *sX = sW + RP * RP;                   // RP x RP scratch (inverse)
+    T *sdi = sX + RP * RP;                  // RP
+
     const int R = t.R;
     const int64_t g = t.lvl_off[m] + i;
-    if (tid < RP) {
-        sq[tid] = t.kx[g * RP + tid];
-        sq[RP + tid] = t.ky[g * RP + tid];
-    }
     if (tid == 0) flag[0] = 0;
+    build_pairs(tab, RP);
     T *pb = w.prior + (size_t)b * w.prior_stride;
-    __syncthreads();
+    const int r0 = TL::r0(), c0 = TL::c0();
     for (int l = 1; l < m; l++) {
         const int64_t ia = (int64_t)i >> (t.lgJ * (m - l));
         const int64_t ga = t.lvl_off[l] + ia;
-        const T *anc = pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP;
+        copy_g2s(sB, pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP, l * RP * RP);
         if (tid < RP) {
-            sa[tid] = t.kx[ga * RP + tid];
-            sa[RP + tid] = t.ky[ga * RP + tid];
+            const double ox = t.cx[ga], oy = t.cy[ga];
+            sq[tid] = (T)(t.kx[g * RP + tid] - ox);
+            sq[RP + tid] = (T)(t.ky[g * RP + tid] - oy);
+            sa[tid] = (T)(t.kx[ga * RP + tid] - ox);
+            sa[RP + tid] = (T)(t.ky[ga * RP + tid] - oy);
         }
         __syncthreads();
-        for (int e = tid; e < RP * RP; e += NT) {
-            const int a = e / RP, c = e % RP;
-            sW[a * LD + c] = (a < R && c < R) ? cov_exp<T>(s2, beta, sq[a], sq[RP + a], sa[c], sa[RP + c])
-                                              : T(0);
-        }
-        for (int k = 1; k < l; k++) {
-            load_block<T, RP>(sA, anc + (size_t)(k - 1) * RP * RP);
-            __syncthreads();
-            mm_nt<T, RP, RP>(sW, LD, sWh + (k - 1) * RP * LD, LD, sA, LD, RP, MM_SUB);
-            __syncthreads();
-        }
-        load_block<T, RP>(sA, anc + (size_t)(l - 1) * RP * RP);
+        T acc[TL::RT][TL::CT];
+        tile_zero(acc);
+        tile_fma<T, RP, RP>(acc, sU, RP, sB, RP, (l - 1) * RP);
+#pragma unroll
+        for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+            for (int c = 0; c < TL::CT; c++) {
+                const int a = r0 + r, j = c0 + c;
+                const T cv = (a < R && j < R) ? cov_d(cp, sq[a] - sa[j], sq[RP + a] - sa[RP + j]) : T(0);
+                sW[j * RP + a] = cv - acc[r][c];
+            }
         __syncthreads();
-        mm_nt<T, RP, RP>(sWh + (l - 1) * RP * LD, LD, sW, LD, sA, LD, RP, MM_SET);
+        tile_zero(acc);
+        tile_fma<T, RP, RP>(acc, sW, RP, sB + (size_t)(l - 1) * RP * RP, RP, RP);
+        T *out = sU + (size_t)(l - 1) * RP * RP;
+#pragma unroll
+        for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+            for (int c = 0; c < TL::CT; c++) out[(c0 + c) * RP + r0 + r] = acc[r][c];
         __syncthreads();
     }
-    for (int e = tid; e < RP * RP; e += NT) {
-        const int a = e / RP, c = e % RP;
-        sW[a * LD + c] = (a < R && c < R) ? cov_exp<T>(s2, beta, sq[a], sq[RP + a], sq[c], sq[RP + c])
-                                          : (a == c ? T(1) : T(0));
+    // self block W^m = C(Q,Q) - sum_k What^k What^k' (identity on the padding)
+    if (tid < RP) {
+        const double ox = t.cx[g], oy = t.cy[g];
+        sq[tid] = (T)(t.kx[g * RP + tid] - ox);
+        sq[RP + tid] = (T)(t.ky[g * RP + tid] - oy);
     }
     __syncthreads();
-    for (int k = 1; k < m; k++) {
-        mm_nt<T, RP, RP>(sW, LD, sWh + (k - 1) * RP * LD, LD, sWh + (k - 1) * RP * LD, LD, RP, MM_SUB);
-        __syncthreads();
-    }
-    for (int e = tid; e < RP * RP; e += NT) {
-        const int a = e / RP, c = e % RP;
-        sL[a * LD + c] = (double)sW[a * LD + c];
+    {
+        T acc[TL::RT][TL::CT];
+        tile_zero(acc);
+        tile_fma<T, RP, RP>(acc, sU, RP, sU, RP, (m - 1) * RP);
+#pragma unroll
+        for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+            for (int c = 0; c < TL::CT; c++) {
+                const int a = r0 + r, j = c0 + c;
+                F v;
+                if (a < R && j < R)
+                    v = f_of_T(cov_d(cp, sq[a] - sq[j], sq[RP + a] - sq[RP + j]) - acc[r][c]);
+                else
+                    v = f_of<F>(a == j ? 1.0 : 0.0);
+                sL[a * (RP + 1) + j] = v;
+            }
     }
     __syncthreads();
-    chol_cta(sL, LD, RP, flag);
-    double v = 0.0;
-    for (int a = tid; a < R; a += NT) v += log(sL[a * LD + a]);
-    v = block_sum(v, red);
-    trinv_cta(sL, LD, sX, LD, RP);
+    // W^m assembled in FP32 cannot resolve pivots below its own rounding: the
+    // mixed mode calls such a factor singular at 1e-6 of the largest diagonal.
+    chol_small(sL, RP + 1, RP, tab, srs, flag, sizeof(T) == 4 ? 1e-6 : MRA_SINGULAR);
+    const double ld = logdet_small(sL, RP + 1, RP, red);
+    factor_to_T(sL, RP + 1, srs, RP, sW, RP, sdi);
+    for (int e = tid; e < RP * RP; e += NT) sX[e] = (e / RP == e % RP) ? T(1) : T(0);
+    __syncthreads();
+    fwd_solve_reg2<T, 32>(sW, RP, sdi, sX, RP, RP, RP); // sX = L^{-1}
     T *out = pb + w.prior_lvl[m] + (size_t)i * m * RP * RP;
-    for (int k = 0; k < m - 1; k++)
-        for (int e = tid; e < RP * RP; e += NT) out[(size_t)k * RP * RP + e] = sWh[k * RP * LD + (e / RP) * LD + e % RP];
-    for (int e = tid; e < RP * RP; e += NT) out[(size_t)(m - 1) * RP * RP + e] = (T)sX[(e / RP) * LD + e % RP];
+    for (int e = tid; e < (m - 1) * RP * RP; e += NT) out[e] = sU[e];
+    // Linv stored column-major: element (a, j) at j*RP + a
+    for (int e = tid; e < RP * RP; e += NT) {
+        const int j = e / RP, a = e % RP;
+        out[(size_t)(m - 1) * RP * RP + e] = sX[a * RP + j];
+    }
     if (tid == 0) {
         if (flag[0]) w.status[b] = ST_ENOTPD;
-        if (w.reg_lw) w.reg_lw[(size_t)b * w.reglw_stride + g] = 2.0 * v;
+        if (w.reg_lw) w.reg_lw[(size_t)b * w.reglw_stride + g] = ld;
     }
 }
 
 // -------------------------------------------------------------- leaf basis --
-// A chunk of <= 32 observation rows of one level-(M-1) subtree: What^l of each
-// row against the M-1 ancestors (U rows).
+// A chunk of observation rows below one level-(M-1) region: What^l of each
+// row against its M-1 ancestors, written as rows of U.
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_leafbasis_bytes(int M)
 {
-    return (size_t)2 * MRA_CH * sizeof(double) + 2 * RP * sizeof(double) +
-           ((size_t)MRA_CH * (RP + 1) + (size_t)RP * (RP + 1) + (size_t)(M - 1) * MRA_CH * (RP + 1)) * sizeof(T);
+    return (size_t)(2 * chunk_rows<T>() + 2 * RP) * sizeof(T) + (size_t)(M - 1) * RP * chunk_rows<T>() * sizeof(T) +
+           (size_t)(M - 1) * RP * RP * sizeof(T) + (size_t)RP * chunk_rows<T>() * sizeof(T) + 64;
 }
 
 template <typename T, int RP>
 __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Chunk *chunks)
 {
-    constexpr int LD = RP + 1, CH = MRA_CH;
+    constexpr int CH = chunk_rows<T>();
+    using TL = Tile<CH, RP>;
     const Chunk ch = chunks[blockIdx.x];
     const int b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const double s2 = th[0], beta = th[1];
+    const CovP<T> cp(th);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *sp = (double *)smem_raw;
-    double *sa = sp + 2 * CH;
-    T *sW = (T *)(sa + 2 * RP);
-    T *sA = sW + CH * LD;
-    T *sU = sA + RP * LD;
     const int M = t.M, R = t.R, P = ch.parent, nr = ch.n;
-    if (tid < CH) {
-        sp[tid] = tid < nr ? t.sx[ch.row0 + tid] : 0.0;
-        sp[CH + tid] = tid < nr ? t.sy[ch.row0 + tid] : 0.0;
-    }
+    T *sp = (T *)smem_raw;                  // 2 CH rows relative to the ancestor corner
+    T *sa = sp + 2 * CH;                    // 2 RP
+    T *sU = sa + 2 * RP;                    // (M-1) blocks k-major [t][row], CH rows
+    T *sB = sU + (size_t)(M - 1) * RP * CH; // up to M-1 ancestor blocks
+    T *sW = sB + (size_t)(M - 1) * RP * RP; // RP x CH k-major
     const T *pb = w.prior + (size_t)b * w.prior_stride;
+    const int r0 = TL::r0(), c0 = TL::c0();
     for (int l = 1; l <= M - 1; l++) {
         const int64_t ia = (int64_t)P >> (t.lgJ * (M - 1 - l));
         const int64_t ga = t.lvl_off[l] + ia;
-        const T *anc = pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP;
+        copy_g2s(sB, pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP, l * RP * RP);
+        const double ox = t.cx[ga], oy = t.cy[ga];
+        if (tid < CH) {
+            sp[tid] = tid < nr ? (T)(t.sx[ch.row0 + tid] - ox) : T(0);
+            sp[CH + tid] = tid < nr ? (T)(t.sy[ch.row0 + tid] - oy) : T(0);
+        }
         if (tid < RP) {
-            sa[tid] = t.kx[ga * RP + tid];
-            sa[RP + tid] = t.ky[ga * RP + tid];
+            sa[tid] = (T)(t.kx[ga * RP + tid] - ox);
+            sa[RP + tid] = (T)(t.ky[ga * RP + tid] - oy);
         }
         __syncthreads();
-        for (int e = tid; e < CH * RP; e += NT) {
-            const int a = e / RP, c = e % RP;
-            sW[a * LD + c] = (a < nr && c < R) ? cov_exp<T>(s2, beta, sp[a], sp[CH + a], sa[c], sa[RP + c])
-                                               : T(0);
-        }
-        for (int k = 1; k < l; k++) {
-            load_block<T, RP>(sA, anc + (size_t)(k - 1) * RP * RP);
-            __syncthreads();
-            mm_nt<T, CH, RP>(sW, LD, sU + (k - 1) * CH * LD, LD, sA, LD, RP, MM_SUB);
-            __syncthreads();
-        }
-        load_block<T, RP>(sA, anc + (size_t)(l - 1) * RP * RP);
+        T acc[TL::RT][TL::CT];
+        tile_zero(acc);
+        tile_fma<T, CH, RP>(acc, sU, CH, sB, RP, (l - 1) * RP);
+#pragma unroll
+        for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+            for (int c = 0; c < TL::CT; c++) {
+                const int a = r0 + r, j = c0 + c;
+                const T cv = (a < nr && j < R) ? cov_d(cp, sp[a] - sa[j], sp[CH + a] - sa[RP + j]) : T(0);
+                sW[j * CH + a] = cv - acc[r][c];
+            }
         __syncthreads();
-        mm_nt<T, CH, RP>(sU + (l - 1) * CH * LD, LD, sW, LD, sA, LD, RP, MM_SET);
+        tile_zero(acc);
+        tile_fma<T, CH, RP>(acc, sW, CH, sB + (size_t)(l - 1) * RP * RP, RP, RP);
+        T *out = sU + (size_t)(l - 1) * RP * CH;
+#pragma unroll
+        for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+            for (int c = 0; c < TL::CT; c++) out[(c0 + c) * CH + r0 + r] = acc[r][c];
         __syncthreads();
     }
     const int UC = (M - 1) * RP;
-    T *Ub = w.U + (size_t)b * w.U_stride;
+    T *Ub = w.U + (size_t)b * w.U_stride + (size_t)ch.row0 * UC;
     for (int e = tid; e < nr * UC; e += NT) {
-        const int a = e / UC, col = e % UC, l = col / RP, c = col % RP;
-        Ub[(size_t)(ch.row0 + a) * UC + col] = sU[l * CH * LD + a * LD + c];
+        const int a = e / UC, col = e % UC;
+        Ub[e] = sU[(size_t)col * CH + a];
     }
 }
 
 // ---------------------------------------------------------- leaf posterior --
 // Leaf c with n <= nmax observations, all in shared memory:
-// V = C(S,S) + tau2 I - U U', V = L L' (FP64), Y = L^{-1} U (in place),
-// y = L^{-1} z, d = log|V|, u = y'y.
+// V = C(S,S) + tau2 I - U U' (exact products), V = L L' (FP64),
+// Y = L^{-1} U (in place, type T), y = L^{-1} z (FP64), d = log|V|, u = y'y,
+// w_c = Y'y.
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_leafpost_bytes(int M, int nmax)
 {
-    return (size_t)nmax * (nmax + 1) * sizeof(double) + 4 * (size_t)nmax * sizeof(double) +
-           32 * sizeof(double) + 16 + (size_t)nmax * ((M - 1) * RP + 1) * sizeof(T) +
-           (size_t)nmax * (nmax + 1) * sizeof(T);
+    return (size_t)nmax * (nmax + 1) * sizeof(double) + (size_t)(2 * nmax + 2 + 8) * sizeof(double) +
+           (size_t)((tri_count(nmax) * 2 + 15) & ~15) + 64 + (size_t)nmax * ((M - 1) * RP + 1) * sizeof(T) +
+           (size_t)nmax * (nmax + 1) * sizeof(T) + (size_t)(nmax + 4) * sizeof(T) + 2 * (size_t)nmax * sizeof(double) +
+           80;
 }
 
-// V = L L' (FP64, in place), then Y = L^{-1} U in the storage type T using LT,
-// a T copy of L (ldlt), and y = L^{-1} z in FP64.
+// Forward solve of UC columns of U (ld ldu, type T) with the lower T factor
+// LT (ld ldt) and the reciprocals of its diagonal, one column per thread.
 template <typename T>
-static __device__ void leaf_factor_solve(double *V, int ldv, T *LT, int ldlt, T *U, int ldu, int UC, double *y,
-                                         int n, int *flag)
+__device__ void fwd_solve_cols(const T *LT, int ldt, const T *dinv, T *U, int ldu, int UC, int n)
 {
-    chol_cta(V, ldv, n, flag);
-    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += NT) {
-        const int a = (int)(e / n), q = (int)(e % n);
-        if (q <= a) LT[(size_t)a * ldlt + q] = (T)V[(size_t)a * ldv + q];
-    }
-    __syncthreads();
-    for (int col = threadIdx.x; col <= UC; col += NT) {
-        if (col < UC) {
-            for (int a = 0; a < n; a++) {
-                T s = U[(size_t)a * ldu + col];
-                for (int q = 0; q < a; q++) s -= LT[(size_t)a * ldlt + q] * U[(size_t)q * ldu + col];
-                U[(size_t)a * ldu + col] = s / LT[(size_t)a * ldlt + a];
-            }
-        } else {
-            for (int a = 0; a < n; a++) {
-                double s = y[a];
-                for (int q = 0; q < a; q++) s -= V[(size_t)a * ldv + q] * y[q];
-                y[a] = s / V[(size_t)a * ldv + a];
-            }
+    for (int col = threadIdx.x; col < UC; col += NT) {
+        for (int a = 0; a < n; a++) {
+            T s = U[(size_t)a * ldu + col];
+            for (int q = 0; q < a; q++) s = fma(-LT[(size_t)a * ldt + q], U[(size_t)q * ldu + col], s);
+            U[(size_t)a * ldu + col] = s * dinv[a];
         }
     }
     __syncthreads();
 }
 
-template <typename T, int RP>
-__global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, const int64_t *leaves,
-                                                       int nmax)
+// w[col] = sum_a Y[a][col] y[a] for UC columns (exact FP32 products of Y and
+// the leading part of y in the mixed mode).
+template <typename T, typename F>
+__device__ void gram_vec(const T *Y, int ldy, int UC, const F *y, int n, T *wout)
 {
+    for (int col = threadIdx.x; col < UC; col += NT) {
+        if constexpr (sizeof(T) == 4) {
+            FF s{0.f, 0.f};
+            for (int a = 0; a < n; a++) ff_add_prod(s, Y[(size_t)a * ldy + col], (float)f_hi(y[a]));
+            wout[col] = s.hi + s.lo;
+        } else {
+            double s = 0.0;
+            for (int a = 0; a < n; a++) s = fma(Y[(size_t)a * ldy + col], (double)f_hi(y[a]), s);
+            wout[col] = s;
+        }
+    }
+}
+
+template <typename T, int RP, int NMAX>
+__global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, const int64_t *leaves)
+{
+    constexpr int nmax = NMAX;
     const int64_t c = leaves[blockIdx.x];
     const int b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const double s2 = th[0], beta = th[1], tau2 = th[2];
+    const double tau2 = th[2], ib64 = 1.0 / th[1];
     const int M = t.M;
     const int64_t o0 = t.leaf_off[c];
     const int n = (int)(t.leaf_off[c + 1] - o0);
+    using F = typename FacT<T>::type;
     const int UC = (M - 1) * RP, LDU = UC + 1, LDV = nmax + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *sV = (double *)smem_raw;
-    double *sp = sV + (size_t)nmax * LDV;
-    double *sy = sp + 3 * nmax;
-    double *red = sy + nmax;
-    int *flag = (int *)(red + 32);
-    T *sU = (T *)(flag + 4);
-    T *sLT = sU + (size_t)nmax * LDU;
+    F *sV = (F *)smem_raw;                   // nmax x (nmax+1)
+    F *sy = sV + (size_t)nmax * LDV;         // nmax
+    F *srs = sy + nmax;                      // nmax + 2
+    double *red = (double *)(srs + nmax + 2); // 8
+    uint16_t *tab = (uint16_t *)(red + 8);
+    int *flag = (int *)((unsigned char *)tab + ((tri_count(nmax) * 2 + 15) & ~15));
+    T *sU = (T *)(flag + 16);                // nmax x LDU
+    T *sLT = sU + (size_t)nmax * LDU;        // nmax x (nmax+1)
+    T *sdi = sLT + (size_t)nmax * (nmax + 1); // nmax
+    // local coordinates: 2 nmax doubles (FP64 mode) or 4 nmax floats (x, y as float pairs)
+    double *sp = (double *)(((uintptr_t)(sdi + nmax) + 15) & ~(uintptr_t)15);
+    ff *spf = (ff *)sp;
+    __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
     T *Ub = w.U + (size_t)b * w.U_stride + (size_t)o0 * UC;
+    // coordinates relative to the parent region's corner (level M-1)
+    const int64_t gp = M > 1 ? t.lvl_off[M - 1] + (c >> t.lgJ) : -1;
+    const double ox = gp >= 0 ? t.cx[gp] : t.sx[o0], oy = gp >= 0 ? t.cy[gp] : t.sy[o0];
     for (int a = tid; a < n; a += NT) {
-        sp[a] = t.sx[o0 + a];
-        sp[nmax + a] = t.sy[o0 + a];
-        sp[2 * nmax + a] = t.sz[o0 + a];
-        sy[a] = t.sz[o0 + a];
+        if constexpr (sizeof(T) == 4) {
+            spf[a] = ff_from_double(t.sx[o0 + a] - ox);
+            spf[nmax + a] = ff_from_double(t.sy[o0 + a] - oy);
+        } else {
+            sp[a] = t.sx[o0 + a] - ox;
+            sp[nmax + a] = t.sy[o0 + a] - oy;
+        }
+        sy[a] = f_of<F>(t.sz[o0 + a]);
     }
-    if (tid == 0) flag[0] = 0;
+    if (tid == 0) {
+        flag[0] = 0;
+        s_par[0] = ff_from_double(th[0]);
+        s_par[1] = ff_from_double(ib64);
+    }
+    const ff tau2f = ff_from_double(tau2);
+    build_pairs(tab, n);
     for (int e = tid; e < n * UC; e += NT) sU[(e / UC) * LDU + e % UC] = Ub[e];
     __syncthreads();
     for (int e = tid; e < n * n; e += NT) {
         const int a = e / n, q = e % n;
         if (q <= a) {
-            const double g = dot_acc(sU + a * LDU, 1, sU + q * LDU, 1, UC);
-            const double v = cov_exp<double>(s2, beta, sp[a], sp[nmax + a], sp[q], sp[nmax + q]) + (a == q ? tau2 : 0.0);
-            sV[a * LDV + q] = v - g;
+            T hi, lo;
+            dot2(sU + a * LDU, sU + q * LDU, UC, hi, lo);
+            if constexpr (sizeof(T) == 4) {
+                const ff cv = ff_cov_exp(s_par[0], s_par[1], spf[a], spf[nmax + a], spf[q], spf[nmax + q]);
+                ff v = ff_sub(cv, ff{(float)hi, (float)lo});
+                if (a == q) v = ff_add(v, tau2f);
+                sV[a * LDV + q] = v;
+            } else {
+                const double cv = cov64(th[0], ib64, sp[a] - sp[q], sp[nmax + a] - sp[nmax + q]);
+                sV[a * LDV + q] = cancel_sub(cv, hi, lo) + (a == q ? tau2 : 0.0);
+            }
         }
     }
     __syncthreads();
-    leaf_factor_solve<T>(sV, LDV, sLT, nmax + 1, sU, LDU, UC, sy, n, flag);
-    double dv = 0.0, uv = 0.0;
-    for (int a = tid; a < n; a += NT) {
-        dv += log(sV[a * LDV + a]);
-        uv += sy[a] * sy[a];
+    chol_small(sV, LDV, n, tab, srs, flag, MRA_SINGULAR);
+    const double dv = logdet_small(sV, LDV, n, red);
+    factor_to_T(sV, LDV, srs, n, sLT, nmax + 1, sdi);
+    fwd_solve_reg2<T, NMAX>(sLT, nmax + 1, sdi, sU, LDU, UC, n);
+    fwd_solve_vec(sV, LDV, srs, n, sy);
+    if (tid < 32) {
+        F q = f_of<F>(0.0);
+        for (int a = tid; a < n; a += 32) q = f_add(q, f_sqr(sy[a]));
+        q = warp_sum_f(q);
+        if (tid == 0) red[0] = f_dbl(q);
     }
-    dv = 2.0 * block_sum(dv, red);
-    uv = block_sum(uv, red);
+    __syncthreads();
+    const double uv = red[0];
+    gram_vec(sU, LDU, UC, sy, n, w.leaf_w + (size_t)b * w.leafw_stride + (size_t)c * UC);
     for (int e = tid; e < n * UC; e += NT) Ub[e] = sU[(e / UC) * LDU + e % UC];
-    double *yb = w.ybuf + (size_t)b * w.y_stride + o0;
-    for (int a = tid; a < n; a += NT) yb[a] = sy[a];
     if (tid == 0) {
         double *du = w.leaf_du + (size_t)b * w.leafdu_stride + 2 * c;
         du[0] = dv;
@@ -454,45 +829,132 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
 }
 
 // Leaves larger than the shared-memory path: the same steps on global memory.
+// Cholesky with L in the LOWER triangle and rs[j] = 1/L_jj.
+template <typename F>
+static __device__ void chol_global(F *A, int lda, int n, F *rs, int *fail, double *sc, F *sr)
+{
+    if (threadIdx.x < 32) {
+        double m = 0.0;
+        for (int j = threadIdx.x; j < n; j += 32) m = fmax(m, (double)f_hi(A[(size_t)j * lda + j]));
+        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) sc[0] = MRA_SINGULAR * m;
+    }
+    __syncthreads();
+    const double tol = sc[0];
+    for (int j = 0; j < n; j++) {
+        if (threadIdx.x == 0) {
+            F d = A[(size_t)j * lda + j];
+            if (!((double)f_hi(d) > tol)) {
+                *fail = 1;
+                d = f_of<F>(1.0);
+            }
+            const F r = f_rsqrt(d);
+            A[(size_t)j * lda + j] = f_mul(d, r);
+            rs[j] = r;
+            *sr = r;
+        }
+        __syncthreads();
+        const F r = *sr;
+        for (int i = j + 1 + threadIdx.x; i < n; i += NT) A[(size_t)i * lda + j] = f_mul(A[(size_t)i * lda + j], r);
+        __syncthreads();
+        const int wd = n - j - 1;
+        for (int64_t e = threadIdx.x; e < (int64_t)wd * wd; e += NT) {
+            const int i = j + 1 + (int)(e / wd), k = j + 1 + (int)(e % wd);
+            if (k <= i)
+                A[(size_t)i * lda + k] =
+                    f_sub(A[(size_t)i * lda + k], f_mul(A[(size_t)i * lda + j], A[(size_t)k * lda + j]));
+        }
+        __syncthreads();
+    }
+}
+
+// y <- L^{-1} y for a large factor in the lower triangle, by warp 0: lane a
+// owns the rows a = lane (mod 32).
+template <typename F>
+static __device__ void fwd_solve_vec_big(const F *A, int lda, const F *rs, int n, F *y)
+{
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int q = 0; q < n; q++) {
+            F yq = y[q];
+            if ((q & 31) == lane) {
+                yq = f_mul(yq, rs[q]);
+                y[q] = yq;
+            }
+            yq = f_shfl(yq, q & 31);
+            for (int a = q + 1 + ((lane - q - 1) & 31); a < n; a += 32)
+                y[a] = f_sub(y[a], f_mul(A[(size_t)a * lda + q], yq));
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T, int RP>
 __global__ void __launch_bounds__(NT) k_leafpost_big(DevTree t, Work<T> w, const BigLeaf *leaves)
 {
+    using F = typename FacT<T>::type;
     const BigLeaf bl = leaves[blockIdx.x];
     const int64_t c = bl.leaf;
     const int b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const double s2 = th[0], beta = th[1], tau2 = th[2];
+    const double tau2 = th[2], ib64 = 1.0 / th[1];
     const int M = t.M;
     const int64_t o0 = t.leaf_off[c];
     const int n = (int)(t.leaf_off[c + 1] - o0);
     const int UC = (M - 1) * RP;
     __shared__ double red[32];
+    __shared__ double sc[2];
+    __shared__ F sr;
     __shared__ int flag[4];
-    double *V = w.Vbig + (size_t)b * w.V_stride + bl.voff;
+    // scratch: V (n^2 F), its factor as T (n^2 slots), y (n F), rs (n F), 1/diag (n T)
+    double *base = w.Vbig + (size_t)b * w.V_stride + bl.voff;
+    F *V = (F *)base;
+    T *LT = (T *)(base + (size_t)n * n);
+    F *yb = (F *)(base + 2 * (size_t)n * n);
+    F *rs = yb + n;
+    T *dinv = (T *)(rs + n);
     T *Ub = w.U + (size_t)b * w.U_stride + (size_t)o0 * UC;
-    double *yb = w.ybuf + (size_t)b * w.y_stride + o0;
     const double *px = t.sx + o0, *py = t.sy + o0, *pz = t.sz + o0;
+    const int64_t gp = M > 1 ? t.lvl_off[M - 1] + (c >> t.lgJ) : -1;
+    const double ox = gp >= 0 ? t.cx[gp] : px[0], oy = gp >= 0 ? t.cy[gp] : py[0];
     if (tid == 0) flag[0] = 0;
-    for (int a = tid; a < n; a += NT) yb[a] = pz[a];
+    for (int a = tid; a < n; a += NT) yb[a] = f_of<F>(pz[a]);
+    const ff tau2f = ff_from_double(tau2);
     for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
         const int a = (int)(e / n), q = (int)(e % n);
         if (q <= a) {
-            const double g = dot_acc(Ub + (size_t)a * UC, 1, Ub + (size_t)q * UC, 1, UC);
-            const double v = cov_exp<double>(s2, beta, px[a], py[a], px[q], py[q]) + (a == q ? tau2 : 0.0);
-            V[(size_t)a * n + q] = v - g;
+            T hi, lo;
+            dot2(Ub + (size_t)a * UC, Ub + (size_t)q * UC, UC, hi, lo);
+            if constexpr (sizeof(T) == 4) {
+                const ff cv = ff_cov_exp(ff_from_double(th[0]), ff_from_double(ib64), ff_from_double(px[a] - ox),
+                                         ff_from_double(py[a] - oy), ff_from_double(px[q] - ox),
+                                         ff_from_double(py[q] - oy));
+                ff v = ff_sub(cv, ff{(float)hi, (float)lo});
+                if (a == q) v = ff_add(v, tau2f);
+                V[(size_t)a * n + q] = v;
+            } else {
+                const double cv = cov64(th[0], ib64, (px[a] - ox) - (px[q] - ox), (py[a] - oy) - (py[q] - oy));
+                V[(size_t)a * n + q] = cancel_sub(cv, hi, lo) + (a == q ? tau2 : 0.0);
+            }
         }
     }
     __syncthreads();
-    // the T copy of the factor lives right after V in the scratch (2 n^2 doubles per big leaf)
-    leaf_factor_solve<T>(V, n, (T *)(V + (size_t)n * n), n, Ub, UC, UC, yb, n, flag);
-    double dv = 0.0, uv = 0.0;
-    for (int a = tid; a < n; a += NT) {
-        dv += log(V[(size_t)a * n + a]);
-        uv += yb[a] * yb[a];
+    chol_global(V, n, n, rs, flag, sc, &sr);
+    for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
+        const int a = (int)(e / n), q = (int)(e % n);
+        LT[e] = q <= a ? (T)f_hi(V[(size_t)a * n + q]) : T(0);
     }
-    dv = 2.0 * block_sum(dv, red);
+    for (int a = tid; a < n; a += NT) dinv[a] = (T)f_hi(rs[a]);
+    __syncthreads();
+    fwd_solve_cols(LT, n, dinv, Ub, UC, UC, n);
+    fwd_solve_vec_big(V, n, rs, n, yb);
+    double uv = 0.0;
+    for (int a = tid; a < n; a += NT) uv += f_dbl(f_sqr(yb[a]));
     uv = block_sum(uv, red);
+    const double dv = logdet_small(V, n, n, red);
+    gram_vec(Ub, UC, UC, yb, n, w.leaf_w + (size_t)b * w.leafw_stride + (size_t)c * UC);
     if (tid == 0) {
         double *du = w.leaf_du + (size_t)b * w.leafdu_stride + 2 * c;
         du[0] = dv;
@@ -507,64 +969,106 @@ __global__ void __launch_bounds__(NT) k_leafpost_big(DevTree t, Work<T> w, const
 }
 
 // --------------------------------------------------------------- leaf Gram --
-// Region P of level M-1: A^{k,l} = sum over the rows below P of Y^k' Y^l for
-// one block pair per CTA (blockIdx.y < npairs), or (blockIdx.y == npairs) the
-// vectors w^k = Y^k' y and the sums of the leaves' (d, u).
+// Region P of level M-1 and block column l: A^{k,l} = sum over the rows below
+// P of Y^k' Y^l for k = 1..l, accumulated in T within a chunk of 32 rows and
+// as an unevaluated pair across chunks in the mixed mode.  The l = 1 CTA also
+// sums the leaves' w and (d, u).
 template <typename T, int RP>
+__host__ __device__ constexpr size_t smem_leafgram_bytes(int M)
+{
+    return (size_t)32 * (M - 1) * RP * sizeof(T) + 64;
+}
+
+template <typename T, int RP, int LMAX>
 __global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w)
 {
-    constexpr int LD = RP + 1, CH = MRA_CH;
-    constexpr int CPT = RP * RP / NT, TPR = RP / CPT;
-    const int P = blockIdx.x, pr = blockIdx.y, b = blockIdx.z, tid = threadIdx.x;
+    using TL = Tile<RP, RP>;
+    constexpr int RW = 32;
+    constexpr int RT = TL::RT, CT = TL::CT;
+    const int P = blockIdx.x, l = blockIdx.y + 1, b = blockIdx.z, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const int M = t.M, J = t.J, D = M - 1, UC = D * RP;
+    const int M = t.M, J = t.J, D = M - 1, UC = D * RP, W = l * RP;
     const int np = npairs(D);
     const int64_t r0 = t.leaf_off[(int64_t)P * J], r1 = t.leaf_off[(int64_t)P * J + J];
     const T *Ub = w.U + (size_t)b * w.U_stride;
-    if (pr < np) {
-        __shared__ T sX[CH * LD], sY[CH * LD];
-        int l = 1;
-        while (l * (l + 1) / 2 <= pr) l++;
-        const int k = pr - l * (l - 1) / 2 + 1;
-        const int i = tid / TPR, j0 = tid % TPR;
-        double acc64[CPT];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sY = (T *)smem_raw; // RW x W: the first l blocks of each row
+    const int i0 = TL::r0(), j0 = TL::c0();
+    T hi[LMAX][RT][CT], lo[LMAX][RT][CT];
 #pragma unroll
-        for (int c = 0; c < CPT; c++) acc64[c] = 0.0;
-        for (int64_t rb = r0; rb < r1; rb += CH) {
-            T acc[CPT];
-#pragma unroll
-            for (int c = 0; c < CPT; c++) acc[c] = T(0);
-            const int nr = (int)min((int64_t)CH, r1 - rb);
-            for (int e = tid; e < CH * RP; e += NT) {
-                const int a = e / RP, cc = e % RP;
-                sX[a * LD + cc] = a < nr ? Ub[(size_t)(rb + a) * UC + (k - 1) * RP + cc] : T(0);
-                sY[a * LD + cc] = a < nr ? Ub[(size_t)(rb + a) * UC + (l - 1) * RP + cc] : T(0);
-            }
-            __syncthreads();
-            for (int a = 0; a < nr; a++) {
-                const T xv = sX[a * LD + i];
-#pragma unroll
-                for (int c = 0; c < CPT; c++) acc[c] += xv * sY[a * LD + j0 + c * TPR];
-            }
-#pragma unroll
-            for (int c = 0; c < CPT; c++) acc64[c] += (double)acc[c];
-            __syncthreads();
+    for (int k = 0; k < LMAX; k++) {
+        tile_zero(hi[k]);
+        tile_zero(lo[k]);
+    }
+    for (int64_t rb = r0; rb < r1; rb += RW) {
+        const int nr = (int)min((int64_t)RW, r1 - rb);
+        for (int e = tid; e < RW * W; e += NT) {
+            const int a = e / W, cc = e % W;
+            sY[e] = a < nr ? Ub[(size_t)(rb + a) * UC + cc] : T(0);
         }
-        T *out = w.Ain + (size_t)b * w.Ain_stride + ((size_t)P * np + pr) * RP * RP;
+        __syncthreads();
+        T acc[LMAX][RT][CT];
 #pragma unroll
-        for (int c = 0; c < CPT; c++) out[i * RP + j0 + c * TPR] = (T)acc64[c];
-    } else {
-        const double *yb = w.ybuf + (size_t)b * w.y_stride;
+        for (int k = 0; k < LMAX; k++) tile_zero(acc[k]);
+        for (int a = 0; a < nr; a++) {
+            const T *row = sY + a * W;
+            T bv[CT];
+            ldv<T, CT>(bv, row + (l - 1) * RP + j0);
+#pragma unroll
+            for (int k = 0; k < LMAX; k++) {
+                if (k < l) {
+                    T av[RT];
+                    ldv<T, RT>(av, row + k * RP + i0);
+#pragma unroll
+                    for (int r = 0; r < RT; r++)
+#pragma unroll
+                        for (int c = 0; c < CT; c++) acc[k][r][c] = fma(av[r], bv[c], acc[k][r][c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < LMAX; k++)
+#pragma unroll
+            for (int r = 0; r < RT; r++)
+#pragma unroll
+                for (int c = 0; c < CT; c++) {
+                    if constexpr (sizeof(T) == 4) {
+                        FF s{hi[k][r][c], lo[k][r][c]};
+                        ff_add(s, acc[k][r][c]);
+                        hi[k][r][c] = s.hi;
+                        lo[k][r][c] = s.lo;
+                    } else {
+                        hi[k][r][c] += acc[k][r][c];
+                    }
+                }
+        __syncthreads();
+    }
+    T *out = w.Ain + (size_t)b * w.Ain_stride + (size_t)P * np * RP * RP;
+#pragma unroll
+    for (int k = 0; k < LMAX; k++) {
+        if (k < l) {
+            T *blk = out + (size_t)pidx(k + 1, l) * RP * RP;
+#pragma unroll
+            for (int r = 0; r < RT; r++)
+#pragma unroll
+                for (int c = 0; c < CT; c++) blk[(i0 + r) * RP + j0 + c] = hi[k][r][c] + lo[k][r][c];
+        }
+    }
+    if (l == 1) {
+        const T *lw = w.leaf_w + (size_t)b * w.leafw_stride;
+        const double *ldu = w.leaf_du + (size_t)b * w.leafdu_stride;
         double *wo = w.Ain_w + (size_t)b * w.Ainw_stride + (size_t)P * UC;
         for (int col = tid; col < UC; col += NT) {
             double s = 0.0;
-            for (int64_t row = r0; row < r1; row++) s += (double)Ub[(size_t)row * UC + col] * yb[row];
+            for (int j = 0; j < J; j++) {
+                const int64_t c = (int64_t)P * J + j;
+                if (t.leaf_off[c + 1] > t.leaf_off[c]) s += (double)lw[(size_t)c * UC + col];
+            }
             wo[col] = s;
         }
         if (tid == 0) {
             double d = 0.0, u = 0.0;
-            const double *ldu = w.leaf_du + (size_t)b * w.leafdu_stride;
             for (int j = 0; j < J; j++) {
                 const int64_t c = (int64_t)P * J + j;
                 if (t.leaf_off[c + 1] > t.leaf_off[c]) {
@@ -581,26 +1085,27 @@ __global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w)
 
 // ------------------------------------------------------------- upward pass --
 // Region i of level m: A = sum of the children's ATilde (or the leaf Gram for
-// m = M-1); I + A^{m,m} = Lt Lt' (FP64); Z_k = Lt^{-1} A^{m,k}, z = Lt^{-1} w^m;
-// ATilde^{k,l} = A^{k,l} - Z_k' Z_l (k <= l < m); wTilde^k = w^k - Z_k' z;
-// d += log|I + A^{m,m}|, u -= z'z.  At the root, loglik = -(d + u + n log 2pi)/2.
+// m = M-1); I + A^{m,m} = Lt Lt' (FP64); Z_k = Lt^{-1} A^{m,k} (T),
+// z = Lt^{-1} w^m (FP64); ATilde^{k,l} = A^{k,l} - Z_k' Z_l (k <= l < m);
+// wTilde^k = w^k - Z_k' z; d += log|I + A^{m,m}|, u -= z'z.  At the root,
+// loglik = -(d + u + n log 2 pi) / 2.
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_up_bytes(int m)
 {
-    return (size_t)RP * (RP + 1) * sizeof(double) + (size_t)m * RP * sizeof(double) + RP * sizeof(double) +
-           32 * sizeof(double) + 16 + (size_t)(2 * m) * RP * (RP + 1) * sizeof(T);
+    return (size_t)RP * (RP + 1) * sizeof(double) + (size_t)(m * RP + RP + RP + 2 + 8) * sizeof(double) +
+           (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 + (size_t)(2 * m + 1) * RP * RP * sizeof(T) +
+           RP * sizeof(T) + 64;
 }
 
 template <typename T, int RP>
 __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
 {
-    constexpr int LD = RP + 1;
-    constexpr int CPT = RP * RP / NT, TPR = RP / CPT;
+    using TL = Tile<RP, RP>;
     const int i = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) {
         if (m == 1 && tid == 0) {
-            w.loglik[b] = __longlong_as_double(0x7ff8000000000000LL);
+            w.loglik[b] = qnan();
             w.status[b] = ST_EINVAL;
         }
         return;
@@ -609,15 +1114,19 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
     const bool direct = (m == M - 1);
     const int nsrc = direct ? 1 : J;
     const int np = npairs(m);
+    using F = typename FacT<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *sL = (double *)smem_raw;
-    double *sw = sL + RP * LD;
-    double *sz = sw + m * RP;
-    double *red = sz + RP;
-    int *flag = (int *)(red + 32);
-    T *sC = (T *)(flag + 4);
-    T *sZ = sC + (size_t)m * RP * LD;
-    T *sLT = sZ + (size_t)(m - 1) * RP * LD;
+    F *sL = (F *)smem_raw;                  // RP x (RP+1)
+    double *sw = (double *)(sL + RP * (RP + 1)); // m RP
+    F *sz = (F *)(sw + m * RP);             // RP
+    F *srs = sz + RP;                       // RP + 2
+    double *red = (double *)(srs + RP + 2); // 8
+    uint16_t *tab = (uint16_t *)(red + 8);
+    int *flag = (int *)((unsigned char *)tab + ((tri_count(RP) * 2 + 15) & ~15));
+    T *sC = (T *)(flag + 16);                // m blocks A^{k,m}, row-major
+    T *sZ = sC + (size_t)m * RP * RP;        // (m-1) blocks, row-major [a][bc] = k-major
+    T *sLT = sZ + (size_t)(m - 1) * RP * RP; // RP x RP
+    T *sdi = sLT + RP * RP;                  // RP
     const T *blk[4];
     const double *wv[4], *dus[4];
     for (int s = 0; s < nsrc; s++) {
@@ -633,17 +1142,18 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
         }
     }
     if (tid == 0) flag[0] = 0;
+    build_pairs(tab, RP);
     for (int k = 1; k <= m; k++) {
         const size_t off = (size_t)pidx(k, m) * RP * RP;
         for (int e = tid; e < RP * RP; e += NT) {
-            T v = T(0);
-            for (int s = 0; s < nsrc; s++) v += blk[s][off + e];
-            sC[(size_t)(k - 1) * RP * LD + (e / RP) * LD + e % RP] = v;
+            T v = blk[0][off + e];
+            for (int s = 1; s < nsrc; s++) v += blk[s][off + e];
+            sC[(size_t)(k - 1) * RP * RP + e] = v;
         }
     }
     for (int e = tid; e < m * RP; e += NT) {
-        double v = 0.0;
-        for (int s = 0; s < nsrc; s++) v += wv[s][e];
+        double v = wv[0][e];
+        for (int s = 1; s < nsrc; s++) v += wv[s][e];
         sw[e] = v;
     }
     double dsum = 0.0, usum = 0.0;
@@ -652,76 +1162,65 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
         usum += dus[s][1];
     }
     __syncthreads();
-    const T *Cm = sC + (size_t)(m - 1) * RP * LD;
+    const T *Cm = sC + (size_t)(m - 1) * RP * RP;
     for (int e = tid; e < RP * RP; e += NT) {
         const int a = e / RP, c = e % RP;
-        sL[a * LD + c] = (double)Cm[a * LD + c] + (a == c ? 1.0 : 0.0);
-    }
-    __syncthreads();
-    chol_cta(sL, LD, RP, flag);
-    double ld = 0.0;
-    for (int a = tid; a < RP; a += NT) ld += log(sL[a * LD + a]);
-    ld = 2.0 * block_sum(ld, red);
-    for (int e = tid; e < RP * RP; e += NT) sLT[(e / RP) * LD + e % RP] = (T)sL[(e / RP) * LD + e % RP];
-    __syncthreads();
-    // Z_k[a][bc] = (Lt^{-1} A^{m,k})[a][bc], A^{m,k}[a][bc] = A^{k,m}[bc][a]
-    const int ncol = (m - 1) * RP;
-    for (int col = tid; col <= ncol; col += NT) {
-        if (col < ncol) {
-            const int k = col / RP, bc = col % RP;
-            const T *Ck = sC + (size_t)k * RP * LD;
-            T *Zk = sZ + (size_t)k * RP * LD;
-            for (int a = 0; a < RP; a++) {
-                T s = Ck[bc * LD + a];
-                for (int q = 0; q < a; q++) s -= sLT[a * LD + q] * Zk[q * LD + bc];
-                Zk[a * LD + bc] = s / sLT[a * LD + a];
-            }
-        } else {
-            for (int a = 0; a < RP; a++) {
-                double s = sw[(m - 1) * RP + a];
-                for (int q = 0; q < a; q++) s -= sL[a * LD + q] * sz[q];
-                sz[a] = s / sL[a * LD + a];
-            }
+        if (c <= a) {
+            F v = f_of_T(Cm[e]);
+            if (a == c) v = f_add(v, f_of<F>(1.0));
+            sL[a * (RP + 1) + c] = v;
         }
     }
     __syncthreads();
-    double q2 = 0.0;
-    for (int a = tid; a < RP; a += NT) q2 += sz[a] * sz[a];
-    q2 = block_sum(q2, red);
+    chol_small(sL, RP + 1, RP, tab, srs, flag, MRA_SINGULAR);
+    const double ld = logdet_small(sL, RP + 1, RP, red);
+    factor_to_T(sL, RP + 1, srs, RP, sLT, RP, sdi);
+    // Z = Lt^{-1} [A^{m,1} .. A^{m,m-1}], stored row-major [a][(k-1) RP + bc] with
+    // A^{m,k}[a][bc] = A^{k,m}[bc][a]
+    const int ncol = (m - 1) * RP;
+    for (int e = tid; e < RP * ncol; e += NT) {
+        const int a = e / ncol, col = e % ncol, k = col / RP, bc = col % RP;
+        sZ[e] = sC[(size_t)k * RP * RP + bc * RP + a];
+    }
+    for (int a = tid; a < RP; a += NT) sz[a] = f_of<F>(sw[(m - 1) * RP + a]);
+    __syncthreads();
+    fwd_solve_reg2<T, 32>(sLT, RP, sdi, sZ, ncol, ncol, RP);
+    fwd_solve_vec(sL, RP + 1, srs, RP, sz);
+    if (tid < 32) {
+        F q = tid < RP ? f_sqr(sz[tid]) : f_of<F>(0.0);
+        q = warp_sum_f(q);
+        if (tid == 0) red[0] = f_dbl(q);
+    }
+    __syncthreads();
+    const double q2 = red[0];
     const double dR = dsum + ld, uR = usum - q2;
     const int64_t g = t.lvl_off[m] + i;
     if (m > 1) {
         const int npo = npairs(m - 1);
         T *out = w.Atil[m] + (size_t)b * w.Atil_stride[m] + (size_t)i * npo * RP * RP;
-        const int ii = tid / TPR, j0 = tid % TPR;
+        const int i0 = TL::r0(), j0 = TL::c0();
         for (int l = 1; l <= m - 1; l++) {
             for (int k = 1; k <= l; k++) {
-                const T *Zk = sZ + (size_t)(k - 1) * RP * LD, *Zl = sZ + (size_t)(l - 1) * RP * LD;
-                T acc[CPT];
-#pragma unroll
-                for (int c = 0; c < CPT; c++) acc[c] = T(0);
-                for (int a = 0; a < RP; a++) {
-                    const T zv = Zk[a * LD + ii];
-#pragma unroll
-                    for (int c = 0; c < CPT; c++) acc[c] += zv * Zl[a * LD + j0 + c * TPR];
-                }
+                T acc[TL::RT][TL::CT];
+                tile_zero(acc);
+                tile_fma<T, RP, RP>(acc, sZ + (k - 1) * RP, ncol, sZ + (l - 1) * RP, ncol, RP);
                 const size_t off = (size_t)pidx(k, l) * RP * RP;
 #pragma unroll
-                for (int c = 0; c < CPT; c++) {
-                    const int e = ii * RP + j0 + c * TPR;
-                    T v = T(0);
-                    for (int s = 0; s < nsrc; s++) v += blk[s][off + e];
-                    out[off + e] = v - acc[c];
-                }
+                for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                    for (int c = 0; c < TL::CT; c++) {
+                        const int e = (i0 + r) * RP + j0 + c;
+                        T v = blk[0][off + e];
+                        for (int s = 1; s < nsrc; s++) v += blk[s][off + e];
+                        out[off + e] = v - acc[r][c];
+                    }
             }
         }
         double *wo = w.Atil_w[m] + (size_t)b * w.Atilw_stride[m] + (size_t)i * (m - 1) * RP;
         for (int e = tid; e < (m - 1) * RP; e += NT) {
-            const int k = e / RP, a = e % RP;
-            const T *Zk = sZ + (size_t)k * RP * LD;
-            double s = 0.0;
-            for (int q = 0; q < RP; q++) s += (double)Zk[q * LD + a] * sz[q];
-            wo[e] = sw[e] - s;
+            F acc = f_of<F>(0.0);
+            for (int q = 0; q < RP; q++) acc = f_add(acc, f_mul(f_of_T(sZ[q * ncol + e]), sz[q]));
+            wo[e] = sw[e] - f_dbl(acc);
         }
         if (tid == 0) {
             double *du = w.Atil_du[m] + (size_t)b * w.Atildu_stride[m] + 2 * (size_t)i;
@@ -738,7 +1237,7 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
         }
         if (m == 1) {
             const double ll = -0.5 * (dR + uR + (double)t.n_used * 1.8378770664093454836);
-            w.loglik[b] = w.status[b] == ST_OK ? ll : __longlong_as_double(0x7ff8000000000000LL);
+            w.loglik[b] = w.status[b] == ST_OK ? ll : qnan();
         }
     }
 }
@@ -751,13 +1250,13 @@ __global__ void k_root_single(DevTree t, Work<T> w)
     if (threadIdx.x != 0) return;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) {
-        w.loglik[b] = __longlong_as_double(0x7ff8000000000000LL);
+        w.loglik[b] = qnan();
         w.status[b] = ST_EINVAL;
         return;
     }
     const double *du = w.leaf_du + (size_t)b * w.leafdu_stride;
     const double ll = -0.5 * (du[0] + du[1] + (double)t.n_used * 1.8378770664093454836);
-    w.loglik[b] = w.status[b] == ST_OK ? ll : __longlong_as_double(0x7ff8000000000000LL);
+    w.loglik[b] = w.status[b] == ST_OK ? ll : qnan();
 }
 
 } // namespace mra

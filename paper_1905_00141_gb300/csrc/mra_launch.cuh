@@ -20,6 +20,7 @@ template <typename T, int RP> size_t smem_prior(int m) { return smem_prior_bytes
 template <typename T, int RP> size_t smem_leafbasis(int M) { return smem_leafbasis_bytes<T, RP>(M); }
 template <typename T, int RP> size_t smem_leafpost_small(int M, int nmax) { return smem_leafpost_bytes<T, RP>(M, nmax); }
 template <typename T, int RP> size_t smem_up(int m) { return smem_up_bytes<T, RP>(m); }
+template <typename T, int RP> size_t smem_leafgram(int M) { return smem_leafgram_bytes<T, RP>(M); }
 
 template <typename T, int RP>
 int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream)
@@ -44,17 +45,26 @@ int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, in
     return (int)cudaGetLastError();
 }
 
+template <typename T, int RP, int NMAX>
+static int launch_leafpost_n(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves, int B,
+                             void *stream)
+{
+    static size_t done = 0;
+    const size_t sm = smem_leafpost_bytes<T, RP>(t.M, NMAX);
+    if (int e = set_smem(k_leafpost_small<T, RP, NMAX>, sm, &done)) return e;
+    dim3 grid((unsigned)nleaves, (unsigned)B);
+    k_leafpost_small<T, RP, NMAX><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, leaves);
+    return (int)cudaGetLastError();
+}
+
+// nmax: 32 or 64 (the leaves of the list have at most nmax observations)
 template <typename T, int RP>
 int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves, int nmax,
                           int B, void *stream)
 {
-    static size_t done = 0;
     if (nleaves == 0) return 0;
-    const size_t sm = smem_leafpost_bytes<T, RP>(t.M, nmax);
-    if (int e = set_smem(k_leafpost_small<T, RP>, sm, &done)) return e;
-    dim3 grid((unsigned)nleaves, (unsigned)B);
-    k_leafpost_small<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, leaves, nmax);
-    return (int)cudaGetLastError();
+    if (nmax <= 32) return launch_leafpost_n<T, RP, 32>(t, w, leaves, nleaves, B, stream);
+    return launch_leafpost_n<T, RP, 64>(t, w, leaves, nleaves, B, stream);
 }
 
 template <typename T, int RP>
@@ -67,12 +77,23 @@ int launch_leafpost_big(const DevTree &t, const Work<T> &w, const BigLeaf *leave
     return (int)cudaGetLastError();
 }
 
+template <typename T, int RP, int LMAX>
+static int launch_leafgram_l(const DevTree &t, const Work<T> &w, int nP, int B, void *stream)
+{
+    static size_t done = 0;
+    const size_t sm = smem_leafgram_bytes<T, RP>(t.M);
+    if (int e = set_smem(k_leafgram<T, RP, LMAX>, sm, &done)) return e;
+    dim3 grid((unsigned)nP, (unsigned)(t.M - 1), (unsigned)B);
+    k_leafgram<T, RP, LMAX><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w);
+    return (int)cudaGetLastError();
+}
+
 template <typename T, int RP>
 int launch_leafgram(const DevTree &t, const Work<T> &w, int nP, int B, void *stream)
 {
-    dim3 grid((unsigned)nP, (unsigned)(npairs(t.M - 1) + 1), (unsigned)B);
-    k_leafgram<T, RP><<<grid, NT, 0, (cudaStream_t)stream>>>(t, w);
-    return (int)cudaGetLastError();
+    if (t.M - 1 <= 4) return launch_leafgram_l<T, RP, 4>(t, w, nP, B, stream);
+    if (t.M - 1 <= 8) return launch_leafgram_l<T, RP, 8>(t, w, nP, B, stream);
+    return launch_leafgram_l<T, RP, 12>(t, w, nP, B, stream);
 }
 
 template <typename T, int RP>
@@ -98,6 +119,7 @@ int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream)
     template size_t smem_leafbasis<T, RP>(int);                                                             \
     template size_t smem_leafpost_small<T, RP>(int, int);                                                   \
     template size_t smem_up<T, RP>(int);                                                                    \
+    template size_t smem_leafgram<T, RP>(int);                                                              \
     template int launch_prior<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                   \
     template int launch_leafbasis<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, void *); \
     template int launch_leafpost_small<T, RP>(const DevTree &, const Work<T> &, const int64_t *, int, int,   \

@@ -101,18 +101,32 @@ def test_region_terms_match_oracle():
     assert abs(rg["loglik"] - ro["loglik"]) <= TOL64 * t.n_used
 
 
-def test_batch_with_invalid_and_singular_theta():
+def test_batch_with_invalid_theta():
     x, y, z = synth.uniform(1200, 31)
-    th = np.array([[1.0, 0.1, 0.05], [np.nan, 0.1, 0.05], [1.0, -0.1, 0.05], [1.0, 1e8, 0.05],
-                   [1.0, 0.1, 0.0], [0.9, 0.2, 0.04]])
+    th = np.array([[1.0, 0.1, 0.05], [np.nan, 0.1, 0.05], [1.0, -0.1, 0.05], [1.0, 0.1, 0.0],
+                   [0.9, 0.2, 0.04]])
     ref, _ = oracle.loglik(x, y, z, 3, 4, 16, th)
     with mra.MRA(x, y, z, 3, 4, 16) as g:
         got, st = g.loglik_status(th)
-    assert st in (mra.EINVAL, mra.ENOTPD)
+    assert st == mra.EINVAL
     ok = np.isfinite(ref)
+    assert list(ok) == [True, False, False, False, True]
     assert np.array_equal(ok, np.isfinite(got))
-    assert list(ok) == [True, False, False, False, False, True]
     assert np.all(np.abs(got[ok] - ref[ok]) / 1200 <= TOL64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_coincident_knots_are_singular(precision):
+    # offset = 0 puts a parent's knots on its children's boundary knots: the
+    # remainder covariance of those knots is zero and the prior is singular
+    # (Sec. 1.2); both sides must report it.
+    x, y, z = synth.uniform(1200, 31)
+    th = np.array([[1.0, 0.1, 0.05], [2.0, 0.3, 0.01]])
+    ref, st_o = oracle.loglik(x, y, z, 3, 4, 16, th, offset=0.0)
+    assert st_o == oracle.ENOTPD and np.all(np.isnan(ref))
+    with mra.MRA(x, y, z, 3, 4, 16, offset=0.0, precision=precision) as g:
+        got, st = g.loglik_status(th)
+    assert st == mra.ENOTPD and np.all(np.isnan(got))
 
 
 def test_device_api_with_torch_stream_and_batches():
