@@ -166,9 +166,43 @@ mra_status mra_profile(mra_ctx *ctx, int enable);
  */
 int mra_profile_read(mra_ctx *ctx, mra_kernel_time *out, int cap);
 
+/*
+ * mra_dense_loglik_noalloc -- the single-region likelihood (M = 1: the only
+ *   region is the leaf, so the result is the exact Gaussian log-density
+ *   log N(z; 0, C(S,S) + tau2 I) of the exponential covariance) in FP64, WITHOUT
+ *   allocating device memory.  The paper has no counterpart: this entry point
+ *   serves callers that must not allocate, e.g. code running inside a CUDA
+ *   graph capture or a real-time loop whose memory is reserved up front, and
+ *   runtimes that own every allocation on the device and forbid libraries from
+ *   calling cudaMalloc.
+ *   x_dev, y_dev, z_dev : device, n doubles each (locations and values; NaN is
+ *                         not filtered here).
+ *   n                   : 1 <= n <= 1024, else MRA_EINVAL with a message in
+ *                         mra_last_error(NULL); nothing is launched then.
+ *   theta_dev           : device, 3 doubles (sigma2, beta, tau2).
+ *   loglik_dev          : device, 1 double (NaN if theta is invalid or V is
+ *                         singular).  status_dev: optional device int
+ *                         (per-call mra_status), may be NULL.
+ *   stream              : cudaStream_t (NULL = legacy default stream); the call
+ *                         enqueues one kernel and does not synchronise.
+ *   Working memory: a fixed array of (1024^2 + 2048) doubles (about 8 MiB)
+ *   compiled into the library, present on every device that loads it until
+ *   the process exits.  The first call on a device looks up the array's device
+ *   address (cudaGetSymbolAddress, with that device current); make that first
+ *   call before any stream capture.  All calls on a device share the array and
+ *   it keeps the previous call's contents (every element a call reads it first
+ *   writes): calls whose kernels may overlap on the GPU (different streams
+ *   without ordering) race and give wrong results.  Calls no cudaMalloc,
+ *   cudaFree or other allocating routine.  Not reentrant across host threads
+ *   on the same device for the same reason.
+ */
+mra_status mra_dense_loglik_noalloc(const double *x_dev, const double *y_dev, const double *z_dev,
+                                    int64_t n, const double *theta_dev, double *loglik_dev,
+                                    int *status_dev, void *stream);
+
 /* Last error message of the context (never NULL).  With ctx == NULL: the reason
- * the calling thread's last mra_build failed (mra_build returns no context on
- * failure). */
+ * the calling thread's last mra_build (which returns no context on failure) or
+ * mra_dense_loglik_noalloc failed. */
 const char *mra_last_error(const mra_ctx *ctx);
 
 /* Release the context and all its device memory.  NULL is a no-op. */

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmra.so")
-SOURCES = ["mra_api.cu", "k_f64.cu", "k_f32.cu"]
+SOURCES = ["mra_api.cu", "k_f64.cu", "k_f32.cu", "mra_noalloc.cu"]
 HEADERS = ["mra_internal.h", "mra_kernels.cuh", "mra_launch.cuh", "ff_math.h", "ff_tables.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

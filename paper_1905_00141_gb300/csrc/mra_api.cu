@@ -717,6 +717,14 @@ mra_status ensure_stage(mra_ctx *c, int batch)
 
 } // namespace
 
+// Reason of the calling thread's last failure that has no context to hold it
+// (mra_build, mra_dense_loglik_noalloc); read through mra_last_error(NULL).
+static thread_local std::string g_build_err = "no context";
+
+namespace mra {
+void set_thread_error(const std::string &msg) { g_build_err = msg; }
+} // namespace mra
+
 // ---------------------------------------------------------------- C ABI --
 extern "C" {
 
@@ -731,7 +739,6 @@ void mra_default_opts(mra_opts *opt)
     opt->hbm_budget = 0;
 }
 
-static thread_local std::string g_build_err = "no context";
 
 static mra_status build_ctx(const double *lon, const double *lat, const double *z, int64_t n, int M, int J, int r,
                             const mra_opts *opt_in, mra_ctx **out);

@@ -23,7 +23,7 @@ _STATUS = {0: "MRA_OK", 1: "MRA_EINVAL", 2: "MRA_ENOMEM", 3: "MRA_ENOTPD", 4: "M
 
 EXPORTED = ["mra_default_opts", "mra_build", "mra_loglik", "mra_loglik_device", "mra_set_precision",
             "mra_stats", "mra_tree_export", "mra_region_terms", "mra_profile", "mra_profile_read",
-            "mra_last_error", "mra_free"]
+            "mra_dense_loglik_noalloc", "mra_last_error", "mra_free"]
 
 
 class MRAError(RuntimeError):
@@ -86,6 +86,8 @@ def lib():
         L.mra_profile.argtypes = [vp, ctypes.c_int]
         L.mra_profile_read.restype = ctypes.c_int
         L.mra_profile_read.argtypes = [vp, ctypes.POINTER(KernelTime), ctypes.c_int]
+        L.mra_dense_loglik_noalloc.restype = ctypes.c_int
+        L.mra_dense_loglik_noalloc.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp]
         L.mra_last_error.restype = ctypes.c_char_p
         L.mra_last_error.argtypes = [vp]
         L.mra_free.argtypes = [vp]
@@ -235,6 +237,21 @@ class MRA:
         d, u, lw, ll = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(1)
         st = lib().mra_region_terms(self._h, _dp(th), _dp(d), _dp(u), _dp(lw), _dp(ll))
         return dict(d=d, u=u, logdetW=lw, loglik=float(ll[0]), status=int(st))
+
+
+NOALLOC_MAX_N = 1024
+
+
+def dense_loglik_noalloc(x_ptr: int, y_ptr: int, z_ptr: int, n: int, theta_ptr: int, out_ptr: int,
+                         status_ptr: int = 0, stream: int = 0) -> None:
+    """mra_dense_loglik_noalloc through the C ABI (raw device pointers); raises
+    MRAError with the library's message on a call-level failure."""
+    L = lib()
+    st = L.mra_dense_loglik_noalloc(ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), ctypes.c_void_p(z_ptr),
+                                    int(n), ctypes.c_void_p(theta_ptr), ctypes.c_void_p(out_ptr),
+                                    ctypes.c_void_p(status_ptr or None), ctypes.c_void_p(stream or None))
+    if st != OK:
+        raise MRAError(st, L.mra_last_error(None).decode())
 
 
 def _prec(p):
