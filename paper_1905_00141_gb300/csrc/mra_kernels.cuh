@@ -105,6 +105,29 @@ __device__ __forceinline__ void copy_g2s(T *s, const T *g, int n)
     for (int e = threadIdx.x; e < nv; e += NT) dst[e] = src[e];
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only); each
+// thread waits for its own groups, a barrier then publishes them.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// n elements (a multiple of 16 bytes, 16-byte aligned on both sides)
+template <typename T>
+__device__ __forceinline__ void copy_g2s_async(T *s, const T *g, int n)
+{
+    const int nv = n * (int)sizeof(T) / 16;
+    const char *src = reinterpret_cast<const char *>(g);
+    char *dst = reinterpret_cast<char *>(s);
+    for (int e = threadIdx.x; e < nv; e += NT) cp_async16(dst + 16 * e, src + 16 * e);
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -282,32 +305,41 @@ __device__ __forceinline__ ff f_shfl_xor(ff v, int m)
     return ff{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
 }
 
-// Pair table of chol_small: the lower-triangle positions (i, k), k <= i < n,
-// ordered by decreasing k, so the trailing update of column j (pairs with
-// k > j) is a prefix.
-static __device__ void build_pairs(uint16_t *tab, int n)
-{
-    const int P = tri_count(n);
-    for (int e = threadIdx.x; e < P; e += NT) {
-        int w = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f) + 1;
-        while (tri_count(w) <= e) w++;
-        while (w > 1 && tri_count(w - 1) > e) w--;
-        const int k = n - w, i = k + (e - tri_count(w - 1));
-        tab[e] = (uint16_t)(i | (k << 8));
-    }
-}
-
+// Lower-triangle positions (i, k), k <= i < n, are ordered by decreasing k
+// (e = 0 is (n-1, n-1)), so the positions still updated at column j are the
+// first tri(n-1-j) of the order.
 // Cholesky of a small (n <= 64) symmetric matrix in shared memory by the
 // whole CTA, one barrier per column.  Input: the lower triangle of A.  Output:
 // the factor L in the UPPER triangle, transposed (A[j][i] = L[i][j], i >= j,
 // diagonal included), and rs[j] = 1 / L_jj; the lower triangle is left as
-// scratch.  The owner of the next diagonal entry also forms its reciprocal
-// square root, so each pivot is ready at the barrier.  A pivot at or below
-// `rel` times the largest diagonal entry is singular: it sets *fail and is
-// replaced by 1.  rs: n + 1 entries of shared scratch.
-template <typename F>
-static __device__ void chol_small(F *A, int lda, int n, const uint16_t *tab, F *rs, int *fail, double rel)
+// scratch.  Thread t owns the lower-triangle positions t, t + NT, ... of the
+// pair order of build_pairs and keeps their values in registers through all
+// column steps; only an entry that becomes part of the next pivot column is
+// written back to shared memory.  The owner of the next diagonal entry also
+// forms its reciprocal square root (and its square), so each pivot is ready at
+// the barrier.  A pivot at or below `rel` times the largest diagonal entry is
+// singular: it sets *fail and is replaced by 1.  rs, r2s: n + 1 entries of
+// shared scratch.  S = pairs per thread (ceil(n(n+1)/2 / NT)).
+template <typename F, int S>
+static __device__ void chol_small(F *A, int lda, int n, F *rs, F *r2s, int *fail, double rel)
 {
+    int pi[S], pk[S];
+    F val[S];
+    const int P = tri_count(n);
+#pragma unroll
+    for (int s = 0; s < S; s++) {
+        const int e = threadIdx.x + s * NT;
+        pi[s] = -1;
+        pk[s] = -1;
+        if (e < P) {
+            int w = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f) + 1;
+            while (tri_count(w) <= e) w++;
+            while (w > 1 && tri_count(w - 1) > e) w--;
+            pk[s] = n - w;
+            pi[s] = pk[s] + (e - tri_count(w - 1));
+            val[s] = A[pi[s] * lda + pk[s]];
+        }
+    }
     if (threadIdx.x < 32) {
         double sc = 0.0;
         for (int j = threadIdx.x; j < n; j += 32) sc = fmax(sc, (double)f_hi(A[j * lda + j]));
@@ -321,26 +353,43 @@ static __device__ void chol_small(F *A, int lda, int n, const uint16_t *tab, F *
                 A[0] = d;
             }
             rs[0] = f_rsqrt(d);
+            r2s[0] = f_sqr(rs[0]);
             rs[n] = f_of<F>(tol);
         }
     }
     __syncthreads();
     const double tol = (double)f_hi(rs[n]);
     for (int j = 0; j < n; j++) {
-        const F r = rs[j], r2 = f_sqr(r);
-        for (int i = j + threadIdx.x; i < n; i += NT) A[j * lda + i] = f_mul(A[i * lda + j], r);
-        const int P = tri_count(n - 1 - j);
-        for (int e = threadIdx.x; e < P; e += NT) {
-            const int p = tab[e], i = p & 0xff, k = p >> 8;
-            F v = f_sub(A[i * lda + k], f_mul(f_mul(A[i * lda + j], A[k * lda + j]), r2));
-            if (i == k && k == j + 1) {
-                if (!((double)f_hi(v) > tol)) {
-                    *fail = 1;
-                    v = f_of<F>(1.0);
-                }
-                rs[k] = f_rsqrt(v);
+        const F r = rs[j], r2 = r2s[j];
+        // loads of the pivot column first, so the pairs' chains run in parallel
+        F ai[S], ak[S];
+#pragma unroll
+        for (int s = 0; s < S; s++)
+            if (pk[s] > j) {
+                ai[s] = A[pi[s] * lda + j];
+                ak[s] = A[pk[s] * lda + j];
             }
-            A[i * lda + k] = v;
+        const int ic = j + (int)threadIdx.x;
+        const F colv = ic < n ? A[ic * lda + j] : f_of<F>(0.0);
+#pragma unroll
+        for (int s = 0; s < S; s++)
+            if (pk[s] > j) val[s] = f_sub(val[s], f_mul(f_mul(ai[s], ak[s]), r2));
+        if (ic < n) A[j * lda + ic] = f_mul(colv, r);
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            const int i = pi[s], k = pk[s];
+            if (k == j + 1) {
+                if (i == k) {
+                    if (!((double)f_hi(val[s]) > tol)) {
+                        *fail = 1;
+                        val[s] = f_of<F>(1.0);
+                    }
+                    const F rk = f_rsqrt(val[s]);
+                    rs[k] = rk;
+                    r2s[k] = f_sqr(rk);
+                }
+                A[i * lda + k] = val[s];
+            }
         }
         __syncthreads();
     }
@@ -398,19 +447,6 @@ __device__ __forceinline__ double logdet_small(const ff *A, int lda, int n, doub
     return v;
 }
 
-// The factor of chol_small as a lower-triangular T matrix LT (ld ldt, zeros
-// above) and the reciprocals of its diagonal (from rs).
-template <typename F, typename T>
-__device__ void factor_to_T(const F *A, int lda, const F *rs, int n, T *LT, int ldt, T *dinv)
-{
-    for (int e = threadIdx.x; e < n * n; e += NT) {
-        const int i = e / n, j = e % n;
-        LT[i * ldt + j] = j <= i ? (T)f_hi(A[j * lda + i]) : T(0);
-    }
-    for (int j = threadIdx.x; j < n; j += NT) dinv[j] = (T)f_hi(rs[j]);
-    __syncthreads();
-}
-
 // y <- L^{-1} y with the chol_small factor (L[a][q] = A[q][a]) and rs = 1/L_jj,
 // by warp 0, right-looking: lane a (and a + 32) owns y[a]; after y[q] is
 // final it is broadcast and every later row subtracts its share.
@@ -445,64 +481,101 @@ __device__ __forceinline__ F warp_sum_f(F v)
     return v;
 }
 
-// In-place forward solve X <- L^{-1} X for ncol columns and n <= 64 rows, in
-// two register blocks of 32 rows: solve rows 0..31, subtract their share from
-// rows 32..63, solve those.  One thread per column.
-template <typename T, int MAXN>
-__device__ void fwd_solve_reg2(const T *LT, int ldt, const T *dinv, T *X, int ldx, int ncol, int n)
+// In-place forward solve X <- L^{-1} X for ncol columns of X (row-major, ld
+// ldx), L the chol_small factor (L[k][i] = A[i][k], read as T), rs = 1/L_jj.
+// One thread per column, right-looking: after x_i is final, every later row
+// of the column takes its share (independent updates, so they overlap).
+template <typename T, typename F>
+__device__ void fwd_solve_cols_f(const F *A, int lda, const F *rs, T *X, int ldx, int ncol, int n)
 {
-    static_assert(MAXN == 32 || MAXN == 64, "rows");
     for (int col = threadIdx.x; col < ncol; col += NT) {
-        T x[32];
-#pragma unroll
-        for (int i = 0; i < 32; i++) x[i] = i < n ? X[(size_t)i * ldx + col] : T(0);
-#pragma unroll
-        for (int i = 0; i < 32; i++) {
-            if (i < n) {
-                const T xi = x[i] * dinv[i];
-                x[i] = xi;
-#pragma unroll
-                for (int k = i + 1; k < 32; k++) x[k] = fma(-LT[k * ldt + i], xi, x[k]);
-            }
+        for (int i = 0; i < n; i++) {
+            const T xi = X[(size_t)i * ldx + col] * (T)f_hi(rs[i]);
+            X[(size_t)i * ldx + col] = xi;
+            const F *Li = A + i * lda; // L[k][i] = Li[k]
+#pragma unroll 4
+            for (int k = i + 1; k < n; k++) X[(size_t)k * ldx + col] = fma(-(T)f_hi(Li[k]), xi, X[(size_t)k * ldx + col]);
         }
+    }
+    __syncthreads();
+}
+
+// L^{-1} of the chol_small factor (L[k][i] = A[i][k], n <= NMAX <= 64),
+// written column-major into out (ld ldo: out[col * ldo + i] = (L^{-1})[i][col],
+// zeros above the diagonal), which is also the k-major layout of L^{-1} as a
+// left GEMM operand; out may be global or shared memory, not aliasing A.
+// Warps own columns (col = warp + 8c), lanes own rows (lane, lane + 32): at
+// step i row i of every column is final, one shuffle broadcasts it and each
+// lane updates its later rows with L[k][i], read once per step for all the
+// warp's columns.  Reads of A and writes of out are lane-contiguous.
+template <typename T, int NMAX, typename F>
+__device__ void trinv_warp(const F *A, int lda, const F *rs, T *out, int ldo, int n)
+{
+    constexpr int NW = NT / 32, RPL = NMAX > 32 ? 2 : 1, CPW = (NMAX + NW - 1) / NW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T x[CPW][RPL];
 #pragma unroll
-        for (int i = 0; i < 32; i++)
-            if (i < n) X[(size_t)i * ldx + col] = x[i];
-        if (MAXN > 32 && n > 32) {
-            T y[32];
+    for (int c = 0; c < CPW; c++)
 #pragma unroll
-            for (int i = 0; i < 32; i++) y[i] = 32 + i < n ? X[(size_t)(32 + i) * ldx + col] : T(0);
+        for (int r = 0; r < RPL; r++) x[c][r] = (lane + 32 * r == warp + NW * c) ? T(1) : T(0);
+    for (int i = warp; i < n; i++) {
+        T l[RPL];
 #pragma unroll
-            for (int q = 0; q < 32; q++)
-#pragma unroll
-                for (int k = 0; k < 32; k++) y[k] = fma(-LT[(32 + k) * ldt + q], x[q], y[k]);
-#pragma unroll
-            for (int i = 0; i < 32; i++) {
-                if (32 + i < n) {
-                    const T yi = y[i] * dinv[32 + i];
-                    y[i] = yi;
-#pragma unroll
-                    for (int k = i + 1; k < 32; k++) y[k] = fma(-LT[(32 + k) * ldt + 32 + i], yi, y[k]);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 32; i++)
-                if (32 + i < n) X[(size_t)(32 + i) * ldx + col] = y[i];
+        for (int r = 0; r < RPL; r++) {
+            const int k = lane + 32 * r;
+            l[r] = (k > i && k < n) ? (T)f_hi(A[i * lda + k]) : T(0);
         }
+        const T ri = (T)f_hi(rs[i]);
+#pragma unroll
+        for (int c = 0; c < CPW; c++) {
+            const T own = (RPL == 1 || i < 32) ? x[c][0] : x[c][RPL - 1];
+            const T xi = __shfl_sync(0xffffffffu, own, i & 31) * ri;
+#pragma unroll
+            for (int r = 0; r < RPL; r++) x[c][r] = (lane + 32 * r == i) ? xi : fma(-l[r], xi, x[c][r]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CPW; c++) {
+        const int col = warp + NW * c;
+        if (col < n)
+#pragma unroll
+            for (int r = 0; r < RPL; r++)
+                if (lane + 32 * r < n) out[(size_t)col * ldo + lane + 32 * r] = x[c][r];
+    }
+    __syncthreads();
+}
+
+// x <- L^{-T} x with the chol_small factor (L[q][a] = A[a][q]), by warp 0,
+// right-looking from the last row: lane a (and a + 32) owns x[a].
+template <typename F>
+__device__ void bwd_solve_vec(const F *A, int lda, const F *rs, int n, F *xv)
+{
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        F x0 = lane < n ? xv[lane] : f_of<F>(0.0);
+        F x1 = lane + 32 < n ? xv[lane + 32] : f_of<F>(0.0);
+        for (int q = n - 1; q >= 0; q--) {
+            if (q == lane) x0 = f_mul(x0, rs[q]);
+            if (q == lane + 32) x1 = f_mul(x1, rs[q]);
+            const F xq = q < 32 ? f_shfl(x0, q) : f_shfl(x1, q - 32);
+            if (lane < q) x0 = f_sub(x0, f_mul(A[lane * lda + q], xq));
+            if (lane + 32 < q) x1 = f_sub(x1, f_mul(A[(lane + 32) * lda + q], xq));
+        }
+        if (lane < n) xv[lane] = x0;
+        if (lane + 32 < n) xv[lane + 32] = x1;
     }
     __syncthreads();
 }
 
 // ------------------------------------------------------------------ prior --
 // Region i of level m (1 <= m <= M-1): What^1..What^{m-1} against its
-// ancestors, then W^m = C(Q,Q) - sum_k What^k What^k', its Cholesky factor L
-// (FP64), log|W^m| and Linv = L^{-1}.
+// ancestors, then W^m = C(Q,Q) - sum_k What^k What^k', its Cholesky factor L,
+// log|W^m| and Linv = L^{-1}.
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_prior_bytes(int m)
 {
-    return (size_t)RP * (RP + 1) * sizeof(double) + (RP + 2) * sizeof(double) + 8 * sizeof(double) +
-           (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 + 4 * RP * sizeof(T) +
-           (size_t)(2 * m + 2) * RP * RP * sizeof(T) + RP * sizeof(T) + 64;
+    return (size_t)RP * (RP + 1) * 8 + (RP + 2) * 8 + 8 * 8 + (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 +
+           4 * RP * sizeof(T) + (size_t)(2 * m + 2) * RP * RP * sizeof(T) + RP * sizeof(T) + 64;
 }
 
 template <typename T, int RP>
@@ -518,20 +591,18 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     F *sL = (F *)smem_raw;                  // RP x (RP+1)
     F *srs = sL + RP * (RP + 1);            // RP + 2
     double *red = (double *)(srs + RP + 2); // 8
-    uint16_t *tab = (uint16_t *)(red + 8);  // tri(RP)
-    int *flag = (int *)((unsigned char *)tab + ((tri_count(RP) * 2 + 15) & ~15));
+    F *sr2 = (F *)(red + 8);                // RP + 1 (squared reciprocal pivots)
+    int *flag = (int *)((unsigned char *)sr2 + ((tri_count(RP) * 2 + 15) & ~15));
     T *sq = (T *)(flag + 16);               // own knots relative to the current origin: 2 RP
     T *sa = sq + 2 * RP;                    // ancestor knots: 2 RP
     T *sU = sa + 2 * RP;                    // (m-1) blocks k-major [t][row]
     T *sB = sU + (size_t)(m - 1) * RP * RP; // up to m blocks of the ancestor (column-major)
     T *sW = sB + (size_t)m * RP * RP;       // RP x RP k-major
-    T *sX = sW + RP * RP;                   // RP x RP scratch (inverse)
-    T *sdi = sX + RP * RP;                  // RP
+    T *sX = sW + RP * RP;                   // RP x RP scratch
 
     const int R = t.R;
     const int64_t g = t.lvl_off[m] + i;
     if (tid == 0) flag[0] = 0;
-    build_pairs(tab, RP);
     T *pb = w.prior + (size_t)b * w.prior_stride;
     const int r0 = TL::r0(), c0 = TL::c0();
     for (int l = 1; l < m; l++) {
@@ -594,19 +665,12 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     __syncthreads();
     // W^m assembled in FP32 cannot resolve pivots below its own rounding: the
     // mixed mode calls such a factor singular at 1e-6 of the largest diagonal.
-    chol_small(sL, RP + 1, RP, tab, srs, flag, sizeof(T) == 4 ? 1e-6 : MRA_SINGULAR);
+    chol_small<F, (tri_count(RP) + NT - 1) / NT>(sL, RP + 1, RP, srs, sr2, flag, sizeof(T) == 4 ? 1e-6 : MRA_SINGULAR);
     const double ld = logdet_small(sL, RP + 1, RP, red);
-    factor_to_T(sL, RP + 1, srs, RP, sW, RP, sdi);
-    for (int e = tid; e < RP * RP; e += NT) sX[e] = (e / RP == e % RP) ? T(1) : T(0);
-    __syncthreads();
-    fwd_solve_reg2<T, 32>(sW, RP, sdi, sX, RP, RP, RP); // sX = L^{-1}
     T *out = pb + w.prior_lvl[m] + (size_t)i * m * RP * RP;
     for (int e = tid; e < (m - 1) * RP * RP; e += NT) out[e] = sU[e];
     // Linv stored column-major: element (a, j) at j*RP + a
-    for (int e = tid; e < RP * RP; e += NT) {
-        const int j = e / RP, a = e % RP;
-        out[(size_t)(m - 1) * RP * RP + e] = sX[a * RP + j];
-    }
+    trinv_warp<T, RP>(sL, RP + 1, srs, out + (size_t)(m - 1) * RP * RP, RP, RP);
     if (tid == 0) {
         if (flag[0]) w.status[b] = ST_ENOTPD;
         if (w.reg_lw) w.reg_lw[(size_t)b * w.reglw_stride + g] = ld;
@@ -619,14 +683,15 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_leafbasis_bytes(int M)
 {
-    return (size_t)(2 * chunk_rows<T>() + 2 * RP) * sizeof(T) + (size_t)(M - 1) * RP * chunk_rows<T>() * sizeof(T) +
-           (size_t)(M - 1) * RP * RP * sizeof(T) + (size_t)RP * chunk_rows<T>() * sizeof(T) + 64;
+    return (size_t)(2 * chunk_rows<T>() + 2 * RP) * sizeof(T) + (size_t)(M - 1) * RP * (chunk_rows<T>() + 2) * sizeof(T) +
+           (size_t)(M - 1) * RP * RP * sizeof(T) + (size_t)RP * (chunk_rows<T>() + 2) * sizeof(T) + 64;
 }
 
 template <typename T, int RP>
 __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Chunk *chunks)
 {
     constexpr int CH = chunk_rows<T>();
+    constexpr int LDC = CH + 2; // k-major row stride (keeps the transposed write-out conflict-light)
     using TL = Tile<CH, RP>;
     const Chunk ch = chunks[blockIdx.x];
     const int b = blockIdx.y, tid = threadIdx.x;
@@ -637,9 +702,9 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
     const int M = t.M, R = t.R, P = ch.parent, nr = ch.n;
     T *sp = (T *)smem_raw;                  // 2 CH rows relative to the ancestor corner
     T *sa = sp + 2 * CH;                    // 2 RP
-    T *sU = sa + 2 * RP;                    // (M-1) blocks k-major [t][row], CH rows
-    T *sB = sU + (size_t)(M - 1) * RP * CH; // up to M-1 ancestor blocks
-    T *sW = sB + (size_t)(M - 1) * RP * RP; // RP x CH k-major
+    T *sU = sa + 2 * RP;                     // (M-1) blocks k-major [t][row], stride LDC
+    T *sB = sU + (size_t)(M - 1) * RP * LDC; // up to M-1 ancestor blocks
+    T *sW = sB + (size_t)(M - 1) * RP * RP;  // RP x LDC k-major
     const T *pb = w.prior + (size_t)b * w.prior_stride;
     const int r0 = TL::r0(), c0 = TL::c0();
     for (int l = 1; l <= M - 1; l++) {
@@ -658,30 +723,30 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
         __syncthreads();
         T acc[TL::RT][TL::CT];
         tile_zero(acc);
-        tile_fma<T, CH, RP>(acc, sU, CH, sB, RP, (l - 1) * RP);
+        tile_fma<T, CH, RP>(acc, sU, LDC, sB, RP, (l - 1) * RP);
 #pragma unroll
         for (int r = 0; r < TL::RT; r++)
 #pragma unroll
             for (int c = 0; c < TL::CT; c++) {
                 const int a = r0 + r, j = c0 + c;
                 const T cv = (a < nr && j < R) ? cov_d(cp, sp[a] - sa[j], sp[CH + a] - sa[RP + j]) : T(0);
-                sW[j * CH + a] = cv - acc[r][c];
+                sW[j * LDC + a] = cv - acc[r][c];
             }
         __syncthreads();
         tile_zero(acc);
-        tile_fma<T, CH, RP>(acc, sW, CH, sB + (size_t)(l - 1) * RP * RP, RP, RP);
-        T *out = sU + (size_t)(l - 1) * RP * CH;
+        tile_fma<T, CH, RP>(acc, sW, LDC, sB + (size_t)(l - 1) * RP * RP, RP, RP);
+        T *out = sU + (size_t)(l - 1) * RP * LDC;
 #pragma unroll
         for (int r = 0; r < TL::RT; r++)
 #pragma unroll
-            for (int c = 0; c < TL::CT; c++) out[(c0 + c) * CH + r0 + r] = acc[r][c];
+            for (int c = 0; c < TL::CT; c++) out[(c0 + c) * LDC + r0 + r] = acc[r][c];
         __syncthreads();
     }
     const int UC = (M - 1) * RP;
     T *Ub = w.U + (size_t)b * w.U_stride + (size_t)ch.row0 * UC;
     for (int e = tid; e < nr * UC; e += NT) {
         const int a = e / UC, col = e % UC;
-        Ub[e] = sU[(size_t)col * CH + a];
+        Ub[e] = sU[(size_t)col * LDC + a];
     }
 }
 
@@ -693,10 +758,9 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_leafpost_bytes(int M, int nmax)
 {
-    return (size_t)nmax * (nmax + 1) * sizeof(double) + (size_t)(2 * nmax + 2 + 8) * sizeof(double) +
-           (size_t)((tri_count(nmax) * 2 + 15) & ~15) + 64 + (size_t)nmax * ((M - 1) * RP + 1) * sizeof(T) +
-           (size_t)nmax * (nmax + 1) * sizeof(T) + (size_t)(nmax + 4) * sizeof(T) + 2 * (size_t)nmax * sizeof(double) +
-           80;
+    return (size_t)nmax * (nmax + 1) * 8 + (size_t)(2 * nmax + 2) * 8 + 8 * 8 +
+           (size_t)((tri_count(nmax) * 2 + 15) & ~15) + 64 + (size_t)nmax * ((M - 1) * RP + 4) * sizeof(T) +
+           (size_t)nmax * nmax * sizeof(T) + 2 * (size_t)nmax * 8 + 80;
 }
 
 // Forward solve of UC columns of U (ld ldu, type T) with the lower T factor
@@ -736,6 +800,7 @@ template <typename T, int RP, int NMAX>
 __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, const int64_t *leaves)
 {
     constexpr int nmax = NMAX;
+    using F = typename FacT<T>::type;
     const int64_t c = leaves[blockIdx.x];
     const int b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
@@ -744,23 +809,29 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
     const int M = t.M;
     const int64_t o0 = t.leaf_off[c];
     const int n = (int)(t.leaf_off[c + 1] - o0);
-    using F = typename FacT<T>::type;
-    const int UC = (M - 1) * RP, LDU = UC + 1, LDV = nmax + 1;
+    const int UC = (M - 1) * RP, LDU = UC + 4, LDV = nmax + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    F *sV = (F *)smem_raw;                   // nmax x (nmax+1)
-    F *sy = sV + (size_t)nmax * LDV;         // nmax
-    F *srs = sy + nmax;                      // nmax + 2
-    double *red = (double *)(srs + nmax + 2); // 8
-    uint16_t *tab = (uint16_t *)(red + 8);
-    int *flag = (int *)((unsigned char *)tab + ((tri_count(nmax) * 2 + 15) & ~15));
-    T *sU = (T *)(flag + 16);                // nmax x LDU
-    T *sLT = sU + (size_t)nmax * LDU;        // nmax x (nmax+1)
-    T *sdi = sLT + (size_t)nmax * (nmax + 1); // nmax
-    // local coordinates: 2 nmax doubles (FP64 mode) or 4 nmax floats (x, y as float pairs)
-    double *sp = (double *)(((uintptr_t)(sdi + nmax) + 15) & ~(uintptr_t)15);
+    F *sV = (F *)smem_raw;                      // nmax x (nmax+1): V, then its factor
+    F *sy = sV + (size_t)nmax * LDV;            // nmax: z, then y = L^{-1} z, then V^{-1} z
+    F *srs = sy + nmax;                         // nmax + 2
+    double *red = (double *)(srs + nmax + 2);   // 8
+    F *sr2 = (F *)(red + 8);                    // nmax + 1
+    int *flag = (int *)((unsigned char *)sr2 + ((tri_count(nmax) * 2 + 15) & ~15));
+    T *sU = (T *)(flag + 16);                   // nmax x LDU (rows 16-byte aligned)
+    T *sLi = sU + (size_t)nmax * LDU;           // nmax x nmax: L^{-1}, column-major
+    double *sp = (double *)(((uintptr_t)(sLi + (size_t)nmax * nmax) + 15) & ~(uintptr_t)15); // 2 nmax coordinates
     ff *spf = (ff *)sp;
     __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
     T *Ub = w.U + (size_t)b * w.U_stride + (size_t)o0 * UC;
+    // U rows -> shared (asynchronous 16-byte copies)
+    {
+        const int cpr = UC * (int)sizeof(T) / 16;
+        for (int e = tid; e < n * cpr; e += NT) {
+            const int a = e / cpr, q = e % cpr;
+            cp_async16((char *)(sU + (size_t)a * LDU) + 16 * q, (const char *)(Ub + (size_t)a * UC) + 16 * q);
+        }
+        cp_async_commit();
+    }
     // coordinates relative to the parent region's corner (level M-1)
     const int64_t gp = M > 1 ? t.lvl_off[M - 1] + (c >> t.lgJ) : -1;
     const double ox = gp >= 0 ? t.cx[gp] : t.sx[o0], oy = gp >= 0 ? t.cy[gp] : t.sy[o0];
@@ -774,15 +845,16 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
         }
         sy[a] = f_of<F>(t.sz[o0 + a]);
     }
+    for (int e = tid; e < nmax * nmax; e += NT) sLi[e] = T(0);
     if (tid == 0) {
         flag[0] = 0;
         s_par[0] = ff_from_double(th[0]);
         s_par[1] = ff_from_double(ib64);
     }
     const ff tau2f = ff_from_double(tau2);
-    build_pairs(tab, n);
-    for (int e = tid; e < n * UC; e += NT) sU[(e / UC) * LDU + e % UC] = Ub[e];
+    cp_async_wait<0>();
     __syncthreads();
+    // V = C(S,S) + tau2 I - U U' (lower triangle)
     for (int e = tid; e < n * n; e += NT) {
         const int a = e / n, q = e % n;
         if (q <= a) {
@@ -800,10 +872,24 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
         }
     }
     __syncthreads();
-    chol_small(sV, LDV, n, tab, srs, flag, MRA_SINGULAR);
+    chol_small<F, (tri_count(NMAX) + NT - 1) / NT>(sV, LDV, n, srs, sr2, flag, MRA_SINGULAR);
     const double dv = logdet_small(sV, LDV, n, red);
-    factor_to_T(sV, LDV, srs, n, sLT, nmax + 1, sdi);
-    fwd_solve_reg2<T, NMAX>(sLT, nmax + 1, sdi, sU, LDU, UC, n);
+    trinv_warp<T, NMAX>(sV, LDV, srs, sLi, nmax, n);
+    // Y = L^{-1} U, block column by block column, straight to global
+    {
+        using TL = Tile<NMAX, RP>;
+        const int r0 = TL::r0(), c0 = TL::c0();
+        for (int cb = 0; cb < UC; cb += RP) {
+            T acc[TL::RT][TL::CT];
+            tile_zero(acc);
+            tile_fma<T, NMAX, RP>(acc, sLi, nmax, sU + cb, LDU, n);
+#pragma unroll
+            for (int r = 0; r < TL::RT; r++)
+                if (r0 + r < n)
+#pragma unroll
+                    for (int cc = 0; cc < TL::CT; cc++) Ub[(size_t)(r0 + r) * UC + cb + c0 + cc] = acc[r][cc];
+        }
+    }
     fwd_solve_vec(sV, LDV, srs, n, sy);
     if (tid < 32) {
         F q = f_of<F>(0.0);
@@ -813,8 +899,9 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
     }
     __syncthreads();
     const double uv = red[0];
+    // w_c = Y'y = U' V^{-1} z
+    bwd_solve_vec(sV, LDV, srs, n, sy);
     gram_vec(sU, LDU, UC, sy, n, w.leaf_w + (size_t)b * w.leafw_stride + (size_t)c * UC);
-    for (int e = tid; e < n * UC; e += NT) Ub[e] = sU[(e / UC) * LDU + e % UC];
     if (tid == 0) {
         double *du = w.leaf_du + (size_t)b * w.leafdu_stride + 2 * c;
         du[0] = dv;
@@ -969,93 +1056,112 @@ __global__ void __launch_bounds__(NT) k_leafpost_big(DevTree t, Work<T> w, const
 }
 
 // --------------------------------------------------------------- leaf Gram --
-// Region P of level M-1 and block column l: A^{k,l} = sum over the rows below
-// P of Y^k' Y^l for k = 1..l, accumulated in T within a chunk of 32 rows and
-// as an unevaluated pair across chunks in the mixed mode.  The l = 1 CTA also
-// sums the leaves' w and (d, u).
+// Region P of level M-1: A = Y'Y over the rows below P, as 64 x 64 output
+// tiles of the D x D matrix (D = (M-1) RP, blockIdx.y = upper-triangle tile);
+// every 32 x 32 sub-block (k <= l) is written to the packed layout.  Rows are
+// staged in chunks of 32 (double-buffered with cp.async), accumulated in T
+// within a chunk and as an unevaluated pair across chunks in the mixed mode.
+// Tile (0, 0) also sums the leaves' w and (d, u).
+constexpr int kGramTile = 64, kGramRows = 32;
+
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_leafgram_bytes(int M)
 {
-    return (size_t)32 * (M - 1) * RP * sizeof(T) + 64;
+    return (size_t)2 * 2 * kGramRows * kGramTile * sizeof(T) + 64;
 }
 
-template <typename T, int RP, int LMAX>
+template <typename T, int RP>
 __global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w)
 {
-    using TL = Tile<RP, RP>;
-    constexpr int RW = 32;
+    constexpr int TS = kGramTile, RW = kGramRows;
+    using TL = Tile<TS, TS>;
     constexpr int RT = TL::RT, CT = TL::CT;
-    const int P = blockIdx.x, l = blockIdx.y + 1, b = blockIdx.z, tid = threadIdx.x;
+    const int P = blockIdx.x, b = blockIdx.z, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const int M = t.M, J = t.J, D = M - 1, UC = D * RP, W = l * RP;
+    const int M = t.M, J = t.J, D = M - 1, UC = D * RP;
     const int np = npairs(D);
+    // upper-triangle tile (ti <= tj) from the linear index
+    const int nt = (UC + TS - 1) / TS;
+    int ti = 0, rem = blockIdx.y;
+    while (rem >= nt - ti) {
+        rem -= nt - ti;
+        ti++;
+    }
+    const int tj = ti + rem;
+    const int ca = ti * TS, cb = tj * TS; // first column of the A and B operands
+    const int wa = min(TS, UC - ca), wb = min(TS, UC - cb);
     const int64_t r0 = t.leaf_off[(int64_t)P * J], r1 = t.leaf_off[(int64_t)P * J + J];
     const T *Ub = w.U + (size_t)b * w.U_stride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sY = (T *)smem_raw; // RW x W: the first l blocks of each row
+    T *sbuf = (T *)smem_raw; // 2 stages x (A: RW x TS, B: RW x TS)
     const int i0 = TL::r0(), j0 = TL::c0();
-    T hi[LMAX][RT][CT], lo[LMAX][RT][CT];
-#pragma unroll
-    for (int k = 0; k < LMAX; k++) {
-        tile_zero(hi[k]);
-        tile_zero(lo[k]);
-    }
-    for (int64_t rb = r0; rb < r1; rb += RW) {
+    T hi[RT][CT], lo[RT][CT];
+    tile_zero(hi);
+    tile_zero(lo);
+    // stage a chunk of rows [rb, rb + RW) into buffer st (zero past the end)
+    auto stage = [&](int64_t rb, int st) {
+        T *sA = sbuf + (size_t)st * 2 * RW * TS, *sB = sA + RW * TS;
         const int nr = (int)min((int64_t)RW, r1 - rb);
-        for (int e = tid; e < RW * W; e += NT) {
-            const int a = e / W, cc = e % W;
-            sY[e] = a < nr ? Ub[(size_t)(rb + a) * UC + cc] : T(0);
+        constexpr int VPR = TS * (int)sizeof(T) / 16; // 16-byte vectors per staged row
+        for (int e = tid; e < 2 * RW * VPR; e += NT) {
+            const int which = e / (RW * VPR), a = (e / VPR) % RW, v = e % VPR;
+            const int col0 = (which ? cb : ca) + v * (16 / (int)sizeof(T));
+            const int wdt = which ? wb : wa;
+            T *dst = (which ? sB : sA) + a * TS + v * (16 / (int)sizeof(T));
+            if (a < nr && col0 - (which ? cb : ca) < wdt)
+                cp_async16(dst, Ub + (size_t)(rb + a) * UC + col0);
+            else
+                *reinterpret_cast<int4 *>(dst) = make_int4(0, 0, 0, 0);
+        }
+        cp_async_commit();
+    };
+    int st = 0;
+    if (r0 < r1) stage(r0, 0);
+    for (int64_t rb = r0; rb < r1; rb += RW, st ^= 1) {
+        const int nr = (int)min((int64_t)RW, r1 - rb);
+        if (rb + RW < r1) {
+            stage(rb + RW, st ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-        T acc[LMAX][RT][CT];
+        const T *sA = sbuf + (size_t)st * 2 * RW * TS, *sB = sA + RW * TS;
+        T acc[RT][CT];
+        tile_zero(acc);
+        tile_fma<T, TS, TS>(acc, sA, TS, sB, TS, nr);
 #pragma unroll
-        for (int k = 0; k < LMAX; k++) tile_zero(acc[k]);
-        for (int a = 0; a < nr; a++) {
-            const T *row = sY + a * W;
-            T bv[CT];
-            ldv<T, CT>(bv, row + (l - 1) * RP + j0);
+        for (int r = 0; r < RT; r++)
 #pragma unroll
-            for (int k = 0; k < LMAX; k++) {
-                if (k < l) {
-                    T av[RT];
-                    ldv<T, RT>(av, row + k * RP + i0);
-#pragma unroll
-                    for (int r = 0; r < RT; r++)
-#pragma unroll
-                        for (int c = 0; c < CT; c++) acc[k][r][c] = fma(av[r], bv[c], acc[k][r][c]);
+            for (int c = 0; c < CT; c++) {
+                if constexpr (sizeof(T) == 4) {
+                    FF s{hi[r][c], lo[r][c]};
+                    ff_add(s, acc[r][c]);
+                    hi[r][c] = s.hi;
+                    lo[r][c] = s.lo;
+                } else {
+                    hi[r][c] += acc[r][c];
                 }
             }
-        }
-#pragma unroll
-        for (int k = 0; k < LMAX; k++)
-#pragma unroll
-            for (int r = 0; r < RT; r++)
-#pragma unroll
-                for (int c = 0; c < CT; c++) {
-                    if constexpr (sizeof(T) == 4) {
-                        FF s{hi[k][r][c], lo[k][r][c]};
-                        ff_add(s, acc[k][r][c]);
-                        hi[k][r][c] = s.hi;
-                        lo[k][r][c] = s.lo;
-                    } else {
-                        hi[k][r][c] += acc[k][r][c];
-                    }
-                }
         __syncthreads();
     }
+    // scatter into the packed 32 x 32 (RP x RP) blocks with k <= l
     T *out = w.Ain + (size_t)b * w.Ain_stride + (size_t)P * np * RP * RP;
 #pragma unroll
-    for (int k = 0; k < LMAX; k++) {
-        if (k < l) {
-            T *blk = out + (size_t)pidx(k + 1, l) * RP * RP;
+    for (int r = 0; r < RT; r++) {
+        const int gr = ca + i0 + r;
+        if (i0 + r >= wa) continue;
+        const int k = gr / RP, ii = gr % RP;
 #pragma unroll
-            for (int r = 0; r < RT; r++)
-#pragma unroll
-                for (int c = 0; c < CT; c++) blk[(i0 + r) * RP + j0 + c] = hi[k][r][c] + lo[k][r][c];
+        for (int c = 0; c < CT; c++) {
+            const int gc = cb + j0 + c;
+            if (j0 + c >= wb) continue;
+            const int l = gc / RP, jj = gc % RP;
+            if (k <= l) out[(size_t)pidx(k + 1, l + 1) * RP * RP + ii * RP + jj] = hi[r][c] + lo[r][c];
         }
     }
-    if (l == 1) {
+    if (blockIdx.y == 0) {
         const T *lw = w.leaf_w + (size_t)b * w.leafw_stride;
         const double *ldu = w.leaf_du + (size_t)b * w.leafdu_stride;
         double *wo = w.Ain_w + (size_t)b * w.Ainw_stride + (size_t)P * UC;
@@ -1092,15 +1198,17 @@ __global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w)
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_up_bytes(int m)
 {
-    return (size_t)RP * (RP + 1) * sizeof(double) + (size_t)(m * RP + RP + RP + 2 + 8) * sizeof(double) +
-           (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 + (size_t)(2 * m + 1) * RP * RP * sizeof(T) +
-           RP * sizeof(T) + 64;
+    return (size_t)RP * (RP + 1) * 8 + (size_t)(m * RP) * 8 + (size_t)(RP + RP + 2 + 8) * 8 +
+           (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 + (size_t)(2 * m - 1) * RP * RP * sizeof(T) +
+           (size_t)2 * 4 * RP * RP * sizeof(T) + 64;
 }
 
 template <typename T, int RP>
 __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
 {
     using TL = Tile<RP, RP>;
+    using F = typename FacT<T>::type;
+    constexpr int B2 = RP * RP;
     const int i = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) {
@@ -1113,43 +1221,50 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
     const int M = t.M, J = t.J;
     const bool direct = (m == M - 1);
     const int nsrc = direct ? 1 : J;
-    const int np = npairs(m);
-    using F = typename FacT<T>::type;
+    const int np = npairs(m), npo = npairs(m - 1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    F *sL = (F *)smem_raw;                  // RP x (RP+1)
+    F *sL = (F *)smem_raw;                       // RP x (RP+1)
     double *sw = (double *)(sL + RP * (RP + 1)); // m RP
-    F *sz = (F *)(sw + m * RP);             // RP
-    F *srs = sz + RP;                       // RP + 2
-    double *red = (double *)(srs + RP + 2); // 8
-    uint16_t *tab = (uint16_t *)(red + 8);
-    int *flag = (int *)((unsigned char *)tab + ((tri_count(RP) * 2 + 15) & ~15));
-    T *sC = (T *)(flag + 16);                // m blocks A^{k,m}, row-major
-    T *sZ = sC + (size_t)m * RP * RP;        // (m-1) blocks, row-major [a][bc] = k-major
-    T *sLT = sZ + (size_t)(m - 1) * RP * RP; // RP x RP
-    T *sdi = sLT + RP * RP;                  // RP
+    F *sz = (F *)(sw + m * RP);                  // RP
+    F *srs = sz + RP;                            // RP + 2
+    double *red = (double *)(srs + RP + 2);      // 8
+    F *sr2 = (F *)(red + 8);                     // RP + 1
+    int *flag = (int *)((unsigned char *)sr2 + ((tri_count(RP) * 2 + 15) & ~15));
+    T *sC = (T *)(flag + 16);                    // m blocks A^{k,m}, row-major
+    T *sZ = sC + (size_t)m * B2;                 // RP x (m-1) RP
+    T *sSrc = sZ + (size_t)(m - 1) * B2;         // 2 stages x nsrc blocks of the Schur sources
     const T *blk[4];
     const double *wv[4], *dus[4];
     for (int s = 0; s < nsrc; s++) {
         if (direct) {
-            blk[s] = w.Ain + (size_t)b * w.Ain_stride + (size_t)i * np * RP * RP;
+            blk[s] = w.Ain + (size_t)b * w.Ain_stride + (size_t)i * np * B2;
             wv[s] = w.Ain_w + (size_t)b * w.Ainw_stride + (size_t)i * m * RP;
             dus[s] = w.Ain_du + (size_t)b * w.Aindu_stride + 2 * (size_t)i;
         } else {
             const int64_t ch = (int64_t)i * J + s;
-            blk[s] = w.Atil[m + 1] + (size_t)b * w.Atil_stride[m + 1] + (size_t)ch * np * RP * RP;
+            blk[s] = w.Atil[m + 1] + (size_t)b * w.Atil_stride[m + 1] + (size_t)ch * np * B2;
             wv[s] = w.Atil_w[m + 1] + (size_t)b * w.Atilw_stride[m + 1] + (size_t)ch * m * RP;
             dus[s] = w.Atil_du[m + 1] + (size_t)b * w.Atildu_stride[m + 1] + 2 * (size_t)ch;
         }
     }
     if (tid == 0) flag[0] = 0;
-    build_pairs(tab, RP);
-    for (int k = 1; k <= m; k++) {
-        const size_t off = (size_t)pidx(k, m) * RP * RP;
-        for (int e = tid; e < RP * RP; e += NT) {
-            T v = blk[0][off + e];
-            for (int s = 1; s < nsrc; s++) v += blk[s][off + e];
-            sC[(size_t)(k - 1) * RP * RP + e] = v;
+    // column m: A^{k,m}, k = 1..m, contiguous blocks pidx(1,m) .. pidx(m,m)
+    const size_t c0off = (size_t)pidx(1, m) * B2;
+    if (direct) {
+        copy_g2s_async(sC, blk[0] + c0off, m * B2);
+        cp_async_commit();
+    } else {
+#pragma unroll 4
+        for (int e = tid; e < m * B2; e += NT) {
+            T v = blk[0][c0off + e];
+            for (int s = 1; s < nsrc; s++) v += blk[s][c0off + e];
+            sC[e] = v;
         }
+    }
+    // the first Schur source (pair 0) is fetched while the factor is formed
+    if (m > 1) {
+        for (int s = 0; s < nsrc; s++) copy_g2s_async(sSrc + (size_t)s * B2, blk[s], B2);
+        cp_async_commit();
     }
     for (int e = tid; e < m * RP; e += NT) {
         double v = wv[0][e];
@@ -1161,9 +1276,13 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
         dsum += dus[s][0];
         usum += dus[s][1];
     }
+    if (direct && m > 1)
+        cp_async_wait<1>();
+    else if (direct)
+        cp_async_wait<0>();
     __syncthreads();
-    const T *Cm = sC + (size_t)(m - 1) * RP * RP;
-    for (int e = tid; e < RP * RP; e += NT) {
+    const T *Cm = sC + (size_t)(m - 1) * B2;
+    for (int e = tid; e < B2; e += NT) {
         const int a = e / RP, c = e % RP;
         if (c <= a) {
             F v = f_of_T(Cm[e]);
@@ -1172,19 +1291,18 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
         }
     }
     __syncthreads();
-    chol_small(sL, RP + 1, RP, tab, srs, flag, MRA_SINGULAR);
+    chol_small<F, (tri_count(RP) + NT - 1) / NT>(sL, RP + 1, RP, srs, sr2, flag, MRA_SINGULAR);
     const double ld = logdet_small(sL, RP + 1, RP, red);
-    factor_to_T(sL, RP + 1, srs, RP, sLT, RP, sdi);
     // Z = Lt^{-1} [A^{m,1} .. A^{m,m-1}], stored row-major [a][(k-1) RP + bc] with
     // A^{m,k}[a][bc] = A^{k,m}[bc][a]
     const int ncol = (m - 1) * RP;
     for (int e = tid; e < RP * ncol; e += NT) {
         const int a = e / ncol, col = e % ncol, k = col / RP, bc = col % RP;
-        sZ[e] = sC[(size_t)k * RP * RP + bc * RP + a];
+        sZ[e] = sC[(size_t)k * B2 + bc * RP + a];
     }
     for (int a = tid; a < RP; a += NT) sz[a] = f_of<F>(sw[(m - 1) * RP + a]);
     __syncthreads();
-    fwd_solve_reg2<T, 32>(sLT, RP, sdi, sZ, ncol, ncol, RP);
+    fwd_solve_cols_f<T>(sL, RP + 1, srs, sZ, ncol, ncol, RP);
     fwd_solve_vec(sL, RP + 1, srs, RP, sz);
     if (tid < 32) {
         F q = tid < RP ? f_sqr(sz[tid]) : f_of<F>(0.0);
@@ -1196,24 +1314,36 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
     const double dR = dsum + ld, uR = usum - q2;
     const int64_t g = t.lvl_off[m] + i;
     if (m > 1) {
-        const int npo = npairs(m - 1);
-        T *out = w.Atil[m] + (size_t)b * w.Atil_stride[m] + (size_t)i * npo * RP * RP;
+        T *out = w.Atil[m] + (size_t)b * w.Atil_stride[m] + (size_t)i * npo * B2;
         const int i0 = TL::r0(), j0 = TL::c0();
+        // pair p = pidx(k, l), l = 1..m-1, k = 1..l, in order; sources double-buffered
+        int p = 0;
         for (int l = 1; l <= m - 1; l++) {
-            for (int k = 1; k <= l; k++) {
+            for (int k = 1; k <= l; k++, p++) {
+                if (p + 1 < npo) {
+                    T *dst = sSrc + (size_t)((p + 1) & 1) * 4 * B2;
+                    for (int s = 0; s < nsrc; s++)
+                        copy_g2s_async(dst + (size_t)s * B2, blk[s] + (size_t)(p + 1) * B2, B2);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();
+                const T *src = sSrc + (size_t)(p & 1) * 4 * B2;
                 T acc[TL::RT][TL::CT];
                 tile_zero(acc);
                 tile_fma<T, RP, RP>(acc, sZ + (k - 1) * RP, ncol, sZ + (l - 1) * RP, ncol, RP);
-                const size_t off = (size_t)pidx(k, l) * RP * RP;
 #pragma unroll
                 for (int r = 0; r < TL::RT; r++)
 #pragma unroll
                     for (int c = 0; c < TL::CT; c++) {
                         const int e = (i0 + r) * RP + j0 + c;
-                        T v = blk[0][off + e];
-                        for (int s = 1; s < nsrc; s++) v += blk[s][off + e];
-                        out[off + e] = v - acc[r][c];
+                        T v = src[e];
+                        for (int s = 1; s < nsrc; s++) v += src[(size_t)s * B2 + e];
+                        out[(size_t)p * B2 + e] = v - acc[r][c];
                     }
+                __syncthreads();
             }
         }
         double *wo = w.Atil_w[m] + (size_t)b * w.Atilw_stride[m] + (size_t)i * (m - 1) * RP;

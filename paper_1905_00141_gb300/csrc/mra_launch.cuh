@@ -77,23 +77,16 @@ int launch_leafpost_big(const DevTree &t, const Work<T> &w, const BigLeaf *leave
     return (int)cudaGetLastError();
 }
 
-template <typename T, int RP, int LMAX>
-static int launch_leafgram_l(const DevTree &t, const Work<T> &w, int nP, int B, void *stream)
-{
-    static size_t done = 0;
-    const size_t sm = smem_leafgram_bytes<T, RP>(t.M);
-    if (int e = set_smem(k_leafgram<T, RP, LMAX>, sm, &done)) return e;
-    dim3 grid((unsigned)nP, (unsigned)(t.M - 1), (unsigned)B);
-    k_leafgram<T, RP, LMAX><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w);
-    return (int)cudaGetLastError();
-}
-
 template <typename T, int RP>
 int launch_leafgram(const DevTree &t, const Work<T> &w, int nP, int B, void *stream)
 {
-    if (t.M - 1 <= 4) return launch_leafgram_l<T, RP, 4>(t, w, nP, B, stream);
-    if (t.M - 1 <= 8) return launch_leafgram_l<T, RP, 8>(t, w, nP, B, stream);
-    return launch_leafgram_l<T, RP, 12>(t, w, nP, B, stream);
+    static size_t done = 0;
+    const size_t sm = smem_leafgram_bytes<T, RP>(t.M);
+    if (int e = set_smem(k_leafgram<T, RP>, sm, &done)) return e;
+    const int nt = ((t.M - 1) * RP + kGramTile - 1) / kGramTile;
+    dim3 grid((unsigned)nP, (unsigned)(nt * (nt + 1) / 2), (unsigned)B);
+    k_leafgram<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w);
+    return (int)cudaGetLastError();
 }
 
 template <typename T, int RP>
