@@ -259,8 +259,11 @@ struct mra_ctx {
     int64_t *d_leaf_off = nullptr;
     Chunk *d_chunks32 = nullptr, *d_chunks64 = nullptr; // leaf-basis chunks of 32 (FP64) / 64 (FP32) rows
     int nchunks32 = 0, nchunks64 = 0;
-    int64_t *d_leaves32 = nullptr, *d_leaves64 = nullptr;
-    int nl32 = 0, nl64 = 0, nmax64 = 64;
+    // leaves with 1..kLeafCap[k] observations (and more than the previous cap),
+    // one CTA each; larger leaves take the global-memory path
+    int64_t *d_leaves[kLeafBuckets] = {nullptr, nullptr, nullptr};
+    int nl[kLeafBuckets] = {0, 0, 0};
+    int nmax_small = 64; // largest bucket cap whose shared memory fits
     BigLeaf *d_big = nullptr;
     int nbig = 0;
     int64_t vbig_elems = 0;
@@ -499,15 +502,12 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
         if ((e = timed_launch(c, K_LEAFBASIS, s,
                               [&] { return launch_leafbasis<T, RP>(t, w, chunks, nchunks, B, s); })))
             return e;
-    if (c->nl32 > 0)
-        if ((e = timed_launch(c, K_LEAFPOST, s,
-                              [&] { return launch_leafpost_small<T, RP>(t, w, c->d_leaves32, c->nl32, 32, B, s); })))
-            return e;
-    if (c->nl64 > 0)
-        if ((e = timed_launch(c, K_LEAFPOST, s, [&] {
-                 return launch_leafpost_small<T, RP>(t, w, c->d_leaves64, c->nl64, c->nmax64, B, s);
-             })))
-            return e;
+    for (int k = 0; k < kLeafBuckets; k++)
+        if (c->nl[k] > 0)
+            if ((e = timed_launch(c, K_LEAFPOST, s, [&] {
+                     return launch_leafpost_small<T, RP>(t, w, c->d_leaves[k], c->nl[k], kLeafCap[k], B, s);
+                 })))
+                return e;
     if (c->nbig > 0)
         if ((e = timed_launch(c, K_LEAFPOST_BIG, s,
                               [&] { return launch_leafpost_big<T, RP>(t, w, c->d_big, c->nbig, B, s); })))
@@ -530,7 +530,7 @@ int dispatch_rp(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     return run_pass<T, 32>(c, w, B, s);
 }
 
-size_t max_smem_needed(const mra_ctx *c, int nmax64)
+size_t max_smem_needed(const mra_ctx *c, int nmax)
 {
     const int M = c->P.M;
     size_t mx = 0;
@@ -548,12 +548,12 @@ size_t max_smem_needed(const mra_ctx *c, int nmax64)
         upd(smem_leafgram<double, 16>(M));
         upd(smem_leafbasis<double, 16>(M));
         upd(smem_leafpost_small<double, 16>(M, 32));
-        if (nmax64 > 0) upd(smem_leafpost_small<double, 16>(M, nmax64));
+        if (nmax > 0) upd(smem_leafpost_small<double, 16>(M, nmax));
     } else {
         upd(smem_leafgram<double, 32>(M));
         upd(smem_leafbasis<double, 32>(M));
         upd(smem_leafpost_small<double, 32>(M, 32));
-        if (nmax64 > 0) upd(smem_leafpost_small<double, 32>(M, nmax64));
+        if (nmax > 0) upd(smem_leafpost_small<double, 32>(M, nmax));
     }
     return mx;
 }
@@ -592,7 +592,7 @@ void count_work(mra_ctx *c)
     for (int64_t l = 0; l < P.nleaf(); l++) {
         const double n = (double)(P.leaf_off[(size_t)l + 1] - P.leaf_off[(size_t)l]);
         const double fl = (M - 1) * R * n * (n + 1) + n * n * n / 3.0 + (M - 1) * R * n * n + n * n;
-        if (n <= c->nmax64 || c->d_sx == nullptr)
+        if (n <= c->nmax_small || c->d_sx == nullptr)
             f[K_LEAFPOST] += fl;
         else
             f[K_LEAFPOST_BIG] += fl;
@@ -816,15 +816,15 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
             }
         }
     }
-    int nmax64 = 64;
-    while (nmax64 > 32 && max_smem_needed(c, nmax64) > 227 * 1024) nmax64 -= 8;
-    if (max_smem_needed(c, nmax64 > 32 ? nmax64 : 0) > 227 * 1024) {
+    int nmax_small = kLeafCap[kLeafBuckets - 1];
+    while (nmax_small > kLeafCap[0] && max_smem_needed(c, nmax_small) > 227 * 1024) nmax_small -= 16;
+    if (max_smem_needed(c, nmax_small) > 227 * 1024) {
         c->err = "M too large for the shared-memory kernels at this r";
         *out = c;
         return MRA_EINVAL;
     }
-    c->nmax64 = nmax64;
-    std::vector<int64_t> l32, l64;
+    c->nmax_small = nmax_small;
+    std::vector<int64_t> lb[kLeafBuckets];
     std::vector<BigLeaf> big;
     int64_t voff = 0;
     for (int64_t l = 0; l < P.nleaf(); l++) {
@@ -832,10 +832,10 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         c->max_leaf = std::max(c->max_leaf, nl);
         if (nl == 0) {
             c->empty_leaves++;
-        } else if (nl <= 32) {
-            l32.push_back(l);
-        } else if (nl <= nmax64) {
-            l64.push_back(l);
+        } else if (nl <= nmax_small) {
+            int k = 0;
+            while (nl > kLeafCap[k]) k++;
+            lb[k].push_back(l);
         } else {
             big.push_back(BigLeaf{l, voff});
             voff += big_leaf_scratch(nl);
@@ -861,15 +861,16 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         (st = dev_upload(c, &c->d_leaf_off, P.leaf_off.data(), P.leaf_off.size())) ||
         (st = dev_upload(c, &c->d_chunks32, chunks32.data(), chunks32.size())) ||
         (st = dev_upload(c, &c->d_chunks64, chunks64.data(), chunks64.size())) ||
-        (st = dev_upload(c, &c->d_leaves32, l32.data(), l32.size())) ||
-        (st = dev_upload(c, &c->d_leaves64, l64.data(), l64.size())) || (st = dev_upload(c, &c->d_big, big.data(), big.size()))) {
+        (st = dev_upload(c, &c->d_leaves[0], lb[0].data(), lb[0].size())) ||
+        (st = dev_upload(c, &c->d_leaves[1], lb[1].data(), lb[1].size())) ||
+        (st = dev_upload(c, &c->d_leaves[2], lb[2].data(), lb[2].size())) ||
+        (st = dev_upload(c, &c->d_big, big.data(), big.size()))) {
         *out = c;
         return st;
     }
     c->nchunks32 = (int)chunks32.size();
     c->nchunks64 = (int)chunks64.size();
-    c->nl32 = (int)l32.size();
-    c->nl64 = (int)l64.size();
+    for (int k = 0; k < kLeafBuckets; k++) c->nl[k] = (int)lb[k].size();
     c->nbig = (int)big.size();
     count_work(c);
     const int mb = max_batch_for(c, opt.hbm_budget);
@@ -1082,8 +1083,7 @@ void mra_free(mra_ctx *c)
     if (!c) return;
     if (c->device >= 0 && c->d_sx) cudaSetDevice(c->device);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
-                    c->d_chunks64, c->d_leaves32,
-                    c->d_leaves64, c->d_big, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
+                    c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_big, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
                     c->d_reg_du, c->d_reg_lw};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -72,6 +72,11 @@ struct Work {
     size_t regdu_stride, reglw_stride;
 };
 
+// Leaf-posterior buckets: a leaf with n observations runs in the kernel of the
+// smallest cap >= n (shared-memory footprint grows as cap^2).
+constexpr int kLeafBuckets = 3;
+constexpr int kLeafCap[kLeafBuckets] = {32, 48, 64};
+
 struct Chunk {
     int32_t parent; // level M-1 region index
     int32_t n;      // rows in this chunk (<= chunk rows of the precision)

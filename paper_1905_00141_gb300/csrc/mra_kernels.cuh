@@ -155,7 +155,7 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 template <int ROWS, int COLS>
 struct Tile {
     static constexpr int OUT = ROWS * COLS / NT;
-    static constexpr int CT = OUT >= 4 ? 4 : OUT;
+    static constexpr int CT = OUT % 4 == 0 ? 4 : (OUT % 2 == 0 ? 2 : 1);
     static constexpr int RT = OUT / CT;
     static constexpr int TX = COLS / CT;
     static_assert(OUT >= 1 && RT * CT == OUT && (ROWS / RT) * TX == NT, "tile shape");
@@ -245,6 +245,70 @@ __device__ __forceinline__ void dot2(const double *a, const double *b, int K, do
     for (int k = 0; k < K; k++) s = fma(a[k], b[k], s);
     hi = s;
     lo = 0.0;
+}
+
+// The four sums a_i . q_j (i, j in {0, 1}) over K terms (K a multiple of 8,
+// rows 16-byte aligned).  FP32: each group of 8 products is summed by an FMA
+// chain in FP32 and the group sums are accumulated as float pairs (TwoSum), so
+// the rounding is that of an 8-term FP32 sum per group -- the order of the
+// error already carried by the FP32 operands -- while the 2x2 block reuses
+// every loaded element twice.  FP64: plain FMA chains.
+__device__ __forceinline__ void dot2x2(const float *a0, const float *a1, const float *q0, const float *q1, int K,
+                                       float (&hi)[2][2], float (&lo)[2][2])
+{
+    FF s[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) s[i][j] = FF{0.f, 0.f};
+    for (int k0 = 0; k0 < K; k0 += 8) {
+        float p[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+        for (int k = k0; k < k0 + 8; k += 4) {
+            const float4 x[2] = {*(const float4 *)(a0 + k), *(const float4 *)(a1 + k)};
+            const float4 y[2] = {*(const float4 *)(q0 + k), *(const float4 *)(q1 + k)};
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    p[i][j] = __fmaf_rn(x[i].x, y[j].x, p[i][j]);
+                    p[i][j] = __fmaf_rn(x[i].y, y[j].y, p[i][j]);
+                    p[i][j] = __fmaf_rn(x[i].z, y[j].z, p[i][j]);
+                    p[i][j] = __fmaf_rn(x[i].w, y[j].w, p[i][j]);
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) ff_add(s[i][j], p[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const float t = __fadd_rn(s[i][j].hi, s[i][j].lo);
+            hi[i][j] = t;
+            lo[i][j] = __fsub_rn(s[i][j].lo, __fsub_rn(t, s[i][j].hi));
+        }
+}
+__device__ __forceinline__ void dot2x2(const double *a0, const double *a1, const double *q0, const double *q1, int K,
+                                       double (&hi)[2][2], double (&lo)[2][2])
+{
+    double p[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int k = 0; k < K; k++) {
+        const double x[2] = {a0[k], a1[k]}, y[2] = {q0[k], q1[k]};
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) p[i][j] = fma(x[i], y[j], p[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            hi[i][j] = p[i][j];
+            lo[i][j] = 0.0;
+        }
 }
 
 // C - (hi + lo) with the leading subtraction done first: when C and hi agree
@@ -361,34 +425,25 @@ static __device__ void chol_small(F *A, int lda, int n, F *rs, F *r2s, int *fail
     const double tol = (double)f_hi(rs[n]);
     for (int j = 0; j < n; j++) {
         const F r = rs[j], r2 = r2s[j];
-        // loads of the pivot column first, so the pairs' chains run in parallel
-        F ai[S], ak[S];
-#pragma unroll
-        for (int s = 0; s < S; s++)
-            if (pk[s] > j) {
-                ai[s] = A[pi[s] * lda + j];
-                ak[s] = A[pk[s] * lda + j];
-            }
-        const int ic = j + (int)threadIdx.x;
-        const F colv = ic < n ? A[ic * lda + j] : f_of<F>(0.0);
-#pragma unroll
-        for (int s = 0; s < S; s++)
-            if (pk[s] > j) val[s] = f_sub(val[s], f_mul(f_mul(ai[s], ak[s]), r2));
-        if (ic < n) A[j * lda + ic] = f_mul(colv, r);
+        for (int i = j + threadIdx.x; i < n; i += NT) A[j * lda + i] = f_mul(A[i * lda + j], r);
 #pragma unroll
         for (int s = 0; s < S; s++) {
             const int i = pi[s], k = pk[s];
-            if (k == j + 1) {
-                if (i == k) {
-                    if (!((double)f_hi(val[s]) > tol)) {
-                        *fail = 1;
-                        val[s] = f_of<F>(1.0);
+            if (k > j) {
+                F v = f_sub(val[s], f_mul(f_mul(A[i * lda + j], A[k * lda + j]), r2));
+                if (k == j + 1) {
+                    if (i == k) {
+                        if (!((double)f_hi(v) > tol)) {
+                            *fail = 1;
+                            v = f_of<F>(1.0);
+                        }
+                        const F rk = f_rsqrt(v);
+                        rs[k] = rk;
+                        r2s[k] = f_sqr(rk);
                     }
-                    const F rk = f_rsqrt(val[s]);
-                    rs[k] = rk;
-                    r2s[k] = f_sqr(rk);
+                    A[i * lda + k] = v;
                 }
-                A[i * lda + k] = val[s];
+                val[s] = v;
             }
         }
         __syncthreads();
@@ -481,25 +536,6 @@ __device__ __forceinline__ F warp_sum_f(F v)
     return v;
 }
 
-// In-place forward solve X <- L^{-1} X for ncol columns of X (row-major, ld
-// ldx), L the chol_small factor (L[k][i] = A[i][k], read as T), rs = 1/L_jj.
-// One thread per column, right-looking: after x_i is final, every later row
-// of the column takes its share (independent updates, so they overlap).
-template <typename T, typename F>
-__device__ void fwd_solve_cols_f(const F *A, int lda, const F *rs, T *X, int ldx, int ncol, int n)
-{
-    for (int col = threadIdx.x; col < ncol; col += NT) {
-        for (int i = 0; i < n; i++) {
-            const T xi = X[(size_t)i * ldx + col] * (T)f_hi(rs[i]);
-            X[(size_t)i * ldx + col] = xi;
-            const F *Li = A + i * lda; // L[k][i] = Li[k]
-#pragma unroll 4
-            for (int k = i + 1; k < n; k++) X[(size_t)k * ldx + col] = fma(-(T)f_hi(Li[k]), xi, X[(size_t)k * ldx + col]);
-        }
-    }
-    __syncthreads();
-}
-
 // L^{-1} of the chol_small factor (L[k][i] = A[i][k], n <= NMAX <= 64),
 // written column-major into out (ld ldo: out[col * ldo + i] = (L^{-1})[i][col],
 // zeros above the diagonal), which is also the k-major layout of L^{-1} as a
@@ -541,6 +577,45 @@ __device__ void trinv_warp(const F *A, int lda, const F *rs, T *out, int ldo, in
 #pragma unroll
             for (int r = 0; r < RPL; r++)
                 if (lane + 32 * r < n) out[(size_t)col * ldo + lane + 32 * r] = x[c][r];
+    }
+    __syncthreads();
+}
+
+// X = L^{-1} B for ncol right-hand sides, L the chol_small factor of order
+// N <= 32 (L[k][i] = A[i][k]).  Column col of B is read at src + col * lds
+// (lane-contiguous), column col of X is written to X[a * ldx + col].  Warps
+// own columns (col = warp + 8j, four at a time), lanes own rows; each lane
+// keeps its row of L and its reciprocal pivot in registers, and at step i the
+// owner of row i scales x_i and one shuffle broadcasts it.
+template <typename T, int N, typename F>
+__device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, int lds, T *X, int ldx, int ncol)
+{
+    static_assert(N <= 32, "one row per lane");
+    constexpr int NW = NT / 32, CB = 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T Lr[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) Lr[i] = (lane > i && lane < N) ? (T)f_hi(A[i * lda + lane]) : T(0);
+    const T rl = lane < N ? (T)f_hi(rs[lane]) : T(0);
+    for (int j0 = 0; warp + NW * j0 < ncol; j0 += CB) {
+        T x[CB];
+#pragma unroll
+        for (int cc = 0; cc < CB; cc++) {
+            const int col = warp + NW * (j0 + cc);
+            x[cc] = (col < ncol && lane < N) ? src[(size_t)col * lds + lane] : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+            for (int cc = 0; cc < CB; cc++) {
+                const T xi = __shfl_sync(0xffffffffu, x[cc] * rl, i);
+                x[cc] = lane == i ? xi : fma(-Lr[i], xi, x[cc]);
+            }
+#pragma unroll
+        for (int cc = 0; cc < CB; cc++) {
+            const int col = warp + NW * (j0 + cc);
+            if (col < ncol && lane < N) X[(size_t)lane * ldx + col] = x[cc];
+        }
     }
     __syncthreads();
 }
@@ -854,21 +929,34 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
     const ff tau2f = ff_from_double(tau2);
     cp_async_wait<0>();
     __syncthreads();
-    // V = C(S,S) + tau2 I - U U' (lower triangle)
-    for (int e = tid; e < n * n; e += NT) {
-        const int a = e / n, q = e % n;
-        if (q <= a) {
-            T hi, lo;
-            dot2(sU + a * LDU, sU + q * LDU, UC, hi, lo);
-            if constexpr (sizeof(T) == 4) {
-                const ff cv = ff_cov_exp(s_par[0], s_par[1], spf[a], spf[nmax + a], spf[q], spf[nmax + q]);
-                ff v = ff_sub(cv, ff{(float)hi, (float)lo});
-                if (a == q) v = ff_add(v, tau2f);
-                sV[a * LDV + q] = v;
-            } else {
-                const double cv = cov64(th[0], ib64, sp[a] - sp[q], sp[nmax + a] - sp[nmax + q]);
-                sV[a * LDV + q] = cancel_sub(cv, hi, lo) + (a == q ? tau2 : 0.0);
-            }
+    // V = C(S,S) + tau2 I - U U' (lower triangle), in 2x2 blocks (A, Q), Q <= A
+    {
+        const int nb = (n + 1) >> 1;
+        for (int e = tid; e < tri_count(nb); e += NT) {
+            int A = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while (tri_count(A + 1) <= e) A++;
+            while (A > 0 && tri_count(A) > e) A--;
+            const int Q = e - tri_count(A);
+            const int a0 = 2 * A, q0 = 2 * Q;
+            T hi[2][2], lo[2][2];
+            dot2x2(sU + a0 * LDU, sU + min(a0 + 1, n - 1) * LDU, sU + q0 * LDU, sU + min(q0 + 1, n - 1) * LDU, UC,
+                   hi, lo);
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const int a = a0 + i, q = q0 + j;
+                    if (a >= n || q > a) continue;
+                    if constexpr (sizeof(T) == 4) {
+                        const ff cv = ff_cov_exp(s_par[0], s_par[1], spf[a], spf[nmax + a], spf[q], spf[nmax + q]);
+                        ff v = ff_sub(cv, ff{(float)hi[i][j], (float)lo[i][j]});
+                        if (a == q) v = ff_add(v, tau2f);
+                        sV[a * LDV + q] = v;
+                    } else {
+                        const double cv = cov64(th[0], ib64, sp[a] - sp[q], sp[nmax + a] - sp[nmax + q]);
+                        sV[a * LDV + q] = cancel_sub(cv, hi[i][j], lo[i][j]) + (a == q ? tau2 : 0.0);
+                    }
+                }
         }
     }
     __syncthreads();
@@ -1200,7 +1288,7 @@ __host__ __device__ constexpr size_t smem_up_bytes(int m)
 {
     return (size_t)RP * (RP + 1) * 8 + (size_t)(m * RP) * 8 + (size_t)(RP + RP + 2 + 8) * 8 +
            (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 + (size_t)(2 * m - 1) * RP * RP * sizeof(T) +
-           (size_t)2 * 4 * RP * RP * sizeof(T) + 64;
+           (size_t)4 * RP * sizeof(T) + 64;
 }
 
 template <typename T, int RP>
@@ -1231,8 +1319,7 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
     F *sr2 = (F *)(red + 8);                     // RP + 1
     int *flag = (int *)((unsigned char *)sr2 + ((tri_count(RP) * 2 + 15) & ~15));
     T *sC = (T *)(flag + 16);                    // m blocks A^{k,m}, row-major
-    T *sZ = sC + (size_t)m * B2;                 // RP x (m-1) RP
-    T *sSrc = sZ + (size_t)(m - 1) * B2;         // 2 stages x nsrc blocks of the Schur sources
+    T *sZ = sC + (size_t)m * B2;                 // RP x ((m-1) RP + 4)
     const T *blk[4];
     const double *wv[4], *dus[4];
     for (int s = 0; s < nsrc; s++) {
@@ -1261,11 +1348,6 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
             sC[e] = v;
         }
     }
-    // the first Schur source (pair 0) is fetched while the factor is formed
-    if (m > 1) {
-        for (int s = 0; s < nsrc; s++) copy_g2s_async(sSrc + (size_t)s * B2, blk[s], B2);
-        cp_async_commit();
-    }
     for (int e = tid; e < m * RP; e += NT) {
         double v = wv[0][e];
         for (int s = 1; s < nsrc; s++) v += wv[s][e];
@@ -1276,10 +1358,7 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
         dsum += dus[s][0];
         usum += dus[s][1];
     }
-    if (direct && m > 1)
-        cp_async_wait<1>();
-    else if (direct)
-        cp_async_wait<0>();
+    if (direct) cp_async_wait<0>();
     __syncthreads();
     const T *Cm = sC + (size_t)(m - 1) * B2;
     for (int e = tid; e < B2; e += NT) {
@@ -1293,16 +1372,11 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
     __syncthreads();
     chol_small<F, (tri_count(RP) + NT - 1) / NT>(sL, RP + 1, RP, srs, sr2, flag, MRA_SINGULAR);
     const double ld = logdet_small(sL, RP + 1, RP, red);
-    // Z = Lt^{-1} [A^{m,1} .. A^{m,m-1}], stored row-major [a][(k-1) RP + bc] with
-    // A^{m,k}[a][bc] = A^{k,m}[bc][a]
-    const int ncol = (m - 1) * RP;
-    for (int e = tid; e < RP * ncol; e += NT) {
-        const int a = e / ncol, col = e % ncol, k = col / RP, bc = col % RP;
-        sZ[e] = sC[(size_t)k * B2 + bc * RP + a];
-    }
+    // Z = Lt^{-1} [A^{m,1} .. A^{m,m-1}], stored row-major [a][(k-1) RP + bc] (ld ldz);
+    // right-hand column (k, bc) is A^{m,k}[.][bc] = A^{k,m}[bc][.], contiguous in sC
+    const int ncol = (m - 1) * RP, ldz = ncol + 4;
     for (int a = tid; a < RP; a += NT) sz[a] = f_of<F>(sw[(m - 1) * RP + a]);
-    __syncthreads();
-    fwd_solve_cols_f<T>(sL, RP + 1, srs, sZ, ncol, ncol, RP);
+    fwd_solve_warp<T, RP>(sL, RP + 1, srs, sC, RP, sZ, ldz, ncol);
     fwd_solve_vec(sL, RP + 1, srs, RP, sz);
     if (tid < 32) {
         F q = tid < RP ? f_sqr(sz[tid]) : f_of<F>(0.0);
@@ -1316,40 +1390,37 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
     if (m > 1) {
         T *out = w.Atil[m] + (size_t)b * w.Atil_stride[m] + (size_t)i * npo * B2;
         const int i0 = TL::r0(), j0 = TL::c0();
-        // pair p = pidx(k, l), l = 1..m-1, k = 1..l, in order; sources double-buffered
+        // pair p = pidx(k, l), l = 1..m-1, k = 1..l, in order; each thread's source
+        // elements are loaded before its product so the loads overlap the FMAs
         int p = 0;
         for (int l = 1; l <= m - 1; l++) {
             for (int k = 1; k <= l; k++, p++) {
-                if (p + 1 < npo) {
-                    T *dst = sSrc + (size_t)((p + 1) & 1) * 4 * B2;
-                    for (int s = 0; s < nsrc; s++)
-                        copy_g2s_async(dst + (size_t)s * B2, blk[s] + (size_t)(p + 1) * B2, B2);
-                    cp_async_commit();
-                    cp_async_wait<1>();
-                } else {
-                    cp_async_wait<0>();
+                T v[TL::RT][TL::CT];
+#pragma unroll
+                for (int r = 0; r < TL::RT; r++) {
+                    const size_t e = (size_t)p * B2 + (i0 + r) * RP + j0;
+                    ldv<T, TL::CT>(v[r], blk[0] + e);
+                    for (int s = 1; s < nsrc; s++) {
+                        T u[TL::CT];
+                        ldv<T, TL::CT>(u, blk[s] + e);
+#pragma unroll
+                        for (int c = 0; c < TL::CT; c++) v[r][c] += u[c];
+                    }
                 }
-                __syncthreads();
-                const T *src = sSrc + (size_t)(p & 1) * 4 * B2;
                 T acc[TL::RT][TL::CT];
                 tile_zero(acc);
-                tile_fma<T, RP, RP>(acc, sZ + (k - 1) * RP, ncol, sZ + (l - 1) * RP, ncol, RP);
+                tile_fma<T, RP, RP>(acc, sZ + (k - 1) * RP, ldz, sZ + (l - 1) * RP, ldz, RP);
 #pragma unroll
                 for (int r = 0; r < TL::RT; r++)
 #pragma unroll
-                    for (int c = 0; c < TL::CT; c++) {
-                        const int e = (i0 + r) * RP + j0 + c;
-                        T v = src[e];
-                        for (int s = 1; s < nsrc; s++) v += src[(size_t)s * B2 + e];
-                        out[(size_t)p * B2 + e] = v - acc[r][c];
-                    }
-                __syncthreads();
+                    for (int c = 0; c < TL::CT; c++)
+                        out[(size_t)p * B2 + (i0 + r) * RP + j0 + c] = v[r][c] - acc[r][c];
             }
         }
         double *wo = w.Atil_w[m] + (size_t)b * w.Atilw_stride[m] + (size_t)i * (m - 1) * RP;
         for (int e = tid; e < (m - 1) * RP; e += NT) {
             F acc = f_of<F>(0.0);
-            for (int q = 0; q < RP; q++) acc = f_add(acc, f_mul(f_of_T(sZ[q * ncol + e]), sz[q]));
+            for (int q = 0; q < RP; q++) acc = f_add(acc, f_mul(f_of_T(sZ[q * ldz + e]), sz[q]));
             wo[e] = sw[e] - f_dbl(acc);
         }
         if (tid == 0) {

@@ -57,13 +57,14 @@ static int launch_leafpost_n(const DevTree &t, const Work<T> &w, const int64_t *
     return (int)cudaGetLastError();
 }
 
-// nmax: 32 or 64 (the leaves of the list have at most nmax observations)
+// nmax: a bucket cap (32, 48 or 64); the leaves of the list have at most nmax observations
 template <typename T, int RP>
 int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves, int nmax,
                           int B, void *stream)
 {
     if (nleaves == 0) return 0;
     if (nmax <= 32) return launch_leafpost_n<T, RP, 32>(t, w, leaves, nleaves, B, stream);
+    if (nmax <= 48) return launch_leafpost_n<T, RP, 48>(t, w, leaves, nleaves, B, stream);
     return launch_leafpost_n<T, RP, 64>(t, w, leaves, nleaves, B, stream);
 }
 
