@@ -12,6 +12,10 @@ Two independent references live here:
 * ``dense.py``: a brute-force dense Sigma_MRA built pair by pair from the
   C_m recursion of Sec. 1.1, then the textbook Gaussian log-density.  It has
   its own tree code and is only meant for tiny inputs.
+* ``mlp.py``: the surrogate network (an addition to the paper's method: a
+  3 -> 64 -> 64 -> 1 SiLU perceptron of loglik/n over log theta) in FP64
+  numpy -- BF16 rounding of the parameters, forward pass, hand-derived
+  gradient of the squared-error loss, and the Adam update.
 """
 from __future__ import annotations
 

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmra.so")
-SOURCES = ["mra_api.cu", "k_f64.cu", "k_f32.cu", "mra_noalloc.cu"]
+SOURCES = ["mra_api.cu", "k_f64.cu", "k_f32.cu", "mra_noalloc.cu", "mra_mlp.cu"]
 HEADERS = ["mra_internal.h", "mra_kernels.cuh", "mra_launch.cuh", "ff_math.h", "ff_tables.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -27,7 +27,7 @@ def _stale(out, deps):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "mra.h")]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", h) for h in ("mra.h", "mra_mlp.h")]
     procs = []
     objs = []
     for s in SOURCES:

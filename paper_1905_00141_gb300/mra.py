@@ -26,6 +26,12 @@ EXPORTED = ["mra_default_opts", "mra_build", "mra_loglik", "mra_loglik_device", 
             "mra_dense_loglik_noalloc", "mra_last_error", "mra_free"]
 
 
+def last_error() -> str:
+    """Reason of the last failure on the calling thread (mra_last_error(NULL))."""
+    m = lib().mra_last_error(None)
+    return m.decode() if m else ""
+
+
 class MRAError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))

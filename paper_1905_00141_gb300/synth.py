@@ -105,6 +105,33 @@ def theta_grid_4x4x4():
     return np.stack([S.ravel(), B.ravel(), T.ravel()], axis=1)
 
 
+# theta box of the surrogate and of the batched workload: sigma2, beta, tau2
+THETA_BOX = (np.array([0.5, 0.02, 0.005]), np.array([2.0, 0.2, 0.05]))
+
+
+def theta_sobol(n: int, seed: int = SEED_BASE + 4, box=THETA_BOX):
+    """n theta log-uniform over the box from a scrambled Sobol sequence."""
+    from scipy.stats import qmc
+    u = qmc.Sobol(d=3, scramble=True, seed=seed).random_base2(max(0, math.ceil(math.log2(max(n, 1)))))[:n]
+    lo, hi = np.log(box[0]), np.log(box[1])
+    return np.exp(lo + u * (hi - lo))
+
+
+def mlp_init(seed: int = SEED_BASE + 5, hidden: int = 64):
+    """Initial FP32 parameters of the 3 -> hidden -> hidden -> 1 network
+    (W1, b1, W2, b2, w3, b3 flattened in that order): weights uniform in
+    +-sqrt(6 / (fan_in + fan_out)) (Glorot), biases zero."""
+    rng = np.random.default_rng(seed)
+
+    def glorot(fo, fi):
+        a = math.sqrt(6.0 / (fi + fo))
+        return rng.uniform(-a, a, size=(fo, fi))
+
+    parts = [glorot(hidden, 3), np.zeros(hidden), glorot(hidden, hidden), np.zeros(hidden), glorot(1, hidden),
+             np.zeros(1)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
 def clustered(seed: int = SEED_BASE + 3, n: int = 2097152, grid_n: int = 1024):
     rng = np.random.default_rng(seed)
     nc = int(round(0.7 * n))

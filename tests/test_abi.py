@@ -36,6 +36,8 @@ def test_library_exports_every_declared_symbol():
     for n in names:
         assert hasattr(L, n), n
     assert set(mra.EXPORTED) <= set(names)
+    from paper_1905_00141_gb300 import mlp
+    assert set(mlp.EXPORTED) <= set(names)
 
 
 def _same_tree(x, y, z, M, J, r, offset=np.e / 100, dedup=False):
