@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "../../include/mra.h"
@@ -266,6 +267,11 @@ struct mra_ctx {
     int nmax_small = 64; // largest bucket cap whose shared memory fits
     BigLeaf *d_big = nullptr;
     int nbig = 0;
+    // work items of the tiled large-leaf kernels: [0, n_assemble) assembly
+    // tiles, then per step k the potrf, trsm and update items at big_off[k]
+    BigTile *d_bigitems = nullptr;
+    int big_nassemble = 0;
+    std::vector<std::array<int, 6>> big_steps; // (potrf off, cnt, trsm off, cnt, update off, cnt)
     int64_t vbig_elems = 0;
     // per-theta scratch: one allocation for `cap` theta, sized for FP64
     int cap = 0;     // theta the scratch currently holds
@@ -508,10 +514,24 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
                      return launch_leafpost_small<T, RP>(t, w, c->d_leaves[k], c->nl[k], kLeafCap[k], B, s);
                  })))
                 return e;
-    if (c->nbig > 0)
-        if ((e = timed_launch(c, K_LEAFPOST_BIG, s,
-                              [&] { return launch_leafpost_big<T, RP>(t, w, c->d_big, c->nbig, B, s); })))
+    if (c->nbig > 0) {
+        auto big = [&](int phase, int off, int cnt, int k) {
+            return timed_launch(c, K_LEAFPOST_BIG, s, [&] {
+                return launch_big<T, RP>(t, w, phase, c->d_big, c->d_bigitems + off, cnt, k, B, s);
+            });
+        };
+        if ((e = big(BIG_ASSEMBLE, 0, c->big_nassemble, 0))) return e;
+        for (int k = 0; k < (int)c->big_steps.size(); k++) {
+            const auto &st = c->big_steps[(size_t)k];
+            if ((e = big(BIG_POTRF, st[0], st[1], k))) return e;
+            if (st[3] > 0 && (e = big(BIG_TRSM, st[2], st[3], k))) return e;
+            if (st[5] > 0 && (e = big(BIG_UPDATE, st[4], st[5], k))) return e;
+        }
+        if ((e = timed_launch(c, K_LEAFPOST_BIG, s, [&] {
+                 return launch_big<T, RP>(t, w, BIG_FINISH, c->d_big, nullptr, c->nbig, 0, B, s);
+             })))
             return e;
+    }
     if (M > 1) {
         const int nP = (int)(c->P.lvl_off[(size_t)M] - c->P.lvl_off[(size_t)M - 1]);
         if ((e = timed_launch(c, K_LEAFGRAM, s, [&] { return launch_leafgram<T, RP>(t, w, nP, B, s); }))) return e;
@@ -545,11 +565,13 @@ size_t max_smem_needed(const mra_ctx *c, int nmax)
         }
     }
     if (c->RP == 16) {
+        upd(smem_big<double, 16>(M));
         upd(smem_leafgram<double, 16>(M));
         upd(smem_leafbasis<double, 16>(M));
         upd(smem_leafpost_small<double, 16>(M, 32));
         if (nmax > 0) upd(smem_leafpost_small<double, 16>(M, nmax));
     } else {
+        upd(smem_big<double, 32>(M));
         upd(smem_leafgram<double, 32>(M));
         upd(smem_leafbasis<double, 32>(M));
         upd(smem_leafpost_small<double, 32>(M, 32));
@@ -842,6 +864,41 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         }
     }
     c->vbig_elems = voff;
+    // tiled large-leaf work lists
+    std::vector<BigTile> items;
+    {
+        int ntmax = 0;
+        for (const BigLeaf &bl : big) {
+            const int64_t nl = P.leaf_off[(size_t)bl.leaf + 1] - P.leaf_off[(size_t)bl.leaf];
+            ntmax = std::max(ntmax, (int)((nl + kBigTile - 1) / kBigTile));
+        }
+        auto ntiles = [&](size_t q) {
+            const int64_t nl = P.leaf_off[(size_t)big[q].leaf + 1] - P.leaf_off[(size_t)big[q].leaf];
+            return (int)((nl + kBigTile - 1) / kBigTile);
+        };
+        for (size_t q = 0; q < big.size(); q++)
+            for (int i = 0; i < ntiles(q); i++)
+                for (int j = 0; j <= i; j++) items.push_back(BigTile{(int32_t)q, i, j, 0});
+        c->big_nassemble = (int)items.size();
+        c->big_steps.clear();
+        for (int k = 0; k < ntmax; k++) {
+            std::array<int, 6> st{};
+            st[0] = (int)items.size();
+            for (size_t q = 0; q < big.size(); q++)
+                if (ntiles(q) > k) items.push_back(BigTile{(int32_t)q, k, k, 0});
+            st[1] = (int)items.size() - st[0];
+            st[2] = (int)items.size();
+            for (size_t q = 0; q < big.size(); q++)
+                for (int i = k + 1; i < ntiles(q); i++) items.push_back(BigTile{(int32_t)q, i, k, 0});
+            st[3] = (int)items.size() - st[2];
+            st[4] = (int)items.size();
+            for (size_t q = 0; q < big.size(); q++)
+                for (int i = k + 1; i < ntiles(q); i++)
+                    for (int j = k + 1; j <= i; j++) items.push_back(BigTile{(int32_t)q, i, j, 0});
+            st[5] = (int)items.size() - st[4];
+            c->big_steps.push_back(st);
+        }
+    }
     // device tree, knots padded to RP
     std::vector<double> kxp((size_t)(P.nnonleaf() * c->RP), 0.0), kyp((size_t)(P.nnonleaf() * c->RP), 0.0);
     for (int64_t g = 0; g < P.nnonleaf(); g++)
@@ -864,7 +921,8 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         (st = dev_upload(c, &c->d_leaves[0], lb[0].data(), lb[0].size())) ||
         (st = dev_upload(c, &c->d_leaves[1], lb[1].data(), lb[1].size())) ||
         (st = dev_upload(c, &c->d_leaves[2], lb[2].data(), lb[2].size())) ||
-        (st = dev_upload(c, &c->d_big, big.data(), big.size()))) {
+        (st = dev_upload(c, &c->d_big, big.data(), big.size())) ||
+        (st = dev_upload(c, &c->d_bigitems, items.data(), items.size()))) {
         *out = c;
         return st;
     }
@@ -1083,7 +1141,7 @@ void mra_free(mra_ctx *c)
     if (!c) return;
     if (c->device >= 0 && c->d_sx) cudaSetDevice(c->device);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
-                    c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_big, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
+                    c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
                     c->d_reg_du, c->d_reg_lw};
     for (void *p : ptrs)
         if (p) cudaFree(p);

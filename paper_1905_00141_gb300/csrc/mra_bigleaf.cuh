@@ -1,0 +1,422 @@
+// mra_bigleaf.cuh -- leaf posterior of the large leaves (more observations
+// than the largest shared-memory bucket), blocked in 32 x 32 tiles and
+// batched over all such leaves and all theta of a pass.
+//
+// For a leaf with n observations (Sec. 1.1, finest level): V = C(S,S) -
+// U U' + tau2 I with U the whitened basis of its observations (n x UC),
+// V = L L', d = log|V|, y = L^{-1} z, u = y'y, Y = L^{-1} U and w = Y'y.
+// With nt = ceil(n / 32) tile rows the work is the right-looking blocked
+// Cholesky, carried along with the two right-hand sides:
+//   assemble   every lower tile (I, J) of V                         (1 launch)
+//   for k = 0 .. nt-1:
+//     potrf    tile (k,k) = L_kk L_kk', d += log|L_kk L_kk'|,
+//              y_k = L_kk^{-1} z_k, u += |y_k|^2, Y_k = L_kk^{-1} U_k
+//     trsm     L_ik = V_ik L_kk^{-T} (i > k); z_i -= L_ik y_k;
+//              U_i -= L_ik Y_k
+//     update   V_ij -= L_ik L_jk' (k < j <= i)
+//   finish     w = Y'y; (d, u) and the status to the leaf's outputs
+// One launch covers the tiles of every large leaf that has them at step k
+// (host-built item lists), so the launches per pass grow with the largest
+// leaf's tile count, not with the number of leaves.
+//
+// Precision: the factor and the right-hand side z are carried in the factor
+// type F (float pairs in the mixed mode, FP64 otherwise); the products of
+// the trailing update are exact in the mixed mode (TwoProd of the leading
+// parts, FP32 cross terms of a leading and a trailing part), so the factor
+// keeps double-float accuracy.  U and Y are in the storage type T.
+//
+// Scratch of one large leaf (8-byte slots at BigLeaf::voff): V [n][n] (F,
+// row-major; lower tiles hold V and then L, the upper triangle of each
+// diagonal tile holds that tile's factor transposed as chol_small leaves
+// it), z/y [n] (F), 1/L_jj [n] (F), (d, u) [2] (FP64).
+#pragma once
+
+namespace mra {
+
+constexpr int TB = kBigTile;
+
+template <typename F>
+struct BigView {
+    F *V, *y, *rs;
+    double *du;
+    int n;
+    int64_t o0, c;
+};
+
+template <typename T>
+__device__ __forceinline__ BigView<typename FacT<T>::type> big_view(const DevTree &t, const Work<T> &w,
+                                                                    const BigLeaf &bl, int b)
+{
+    using F = typename FacT<T>::type;
+    BigView<F> v;
+    v.c = bl.leaf;
+    v.o0 = t.leaf_off[bl.leaf];
+    v.n = (int)(t.leaf_off[bl.leaf + 1] - v.o0);
+    double *base = w.Vbig + (size_t)b * w.V_stride + bl.voff;
+    v.V = (F *)base;
+    v.y = (F *)(base + (size_t)v.n * v.n);
+    v.rs = v.y + v.n;
+    v.du = base + (size_t)v.n * v.n + 2 * (size_t)v.n;
+    return v;
+}
+
+// Exact products of float pairs for the trailing update: sum_m a_m b_m with
+// a = ah + al, b = bh + bl, as TwoProd/TwoSum of ah bh plus FP32 sums of
+// ah bl + al bh (the al bl terms are below double-float precision).
+struct FFAcc {
+    FF s;
+    float cross;
+};
+__device__ __forceinline__ void ffacc_zero(FFAcc &a)
+{
+    a.s = FF{0.f, 0.f};
+    a.cross = 0.f;
+}
+__device__ __forceinline__ void ffacc_add(FFAcc &a, ff x, ff y)
+{
+    ff_add_prod(a.s, x.hi, y.hi);
+    a.cross = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, a.cross));
+}
+__device__ __forceinline__ ff ffacc_value(const FFAcc &a)
+{
+    return fast_two_sum(a.s.hi, __fadd_rn(a.s.lo, a.cross));
+}
+
+template <typename T, int RP>
+__host__ __device__ constexpr size_t smem_big_assemble_bytes(int M)
+{
+    return (size_t)2 * TB * ((M - 1) * RP + 4) * sizeof(T) + (size_t)4 * TB * 8 + 64;
+}
+
+// V tile (I, J), I >= J, of a large leaf: C(S_I, S_J) - U_I U_J' (+ tau2 on
+// the diagonal), lower part only for I == J.  U U' is the exact float-float
+// product sum: large leaves are the dense clusters, where C and U U' agree
+// to many digits.
+template <typename T, int RP>
+__global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const BigLeaf *leaves, const BigTile *items)
+{
+    using F = typename FacT<T>::type;
+    const BigTile it = items[blockIdx.x];
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const double *th = w.theta + 3 * b;
+    if (!theta_ok(th)) return;
+    const BigView<F> v = big_view(t, w, leaves[it.bl], b);
+    const int M = t.M, n = v.n, UC = (M - 1) * RP, LDU = UC + 4;
+    const int rI = it.i * TB, rJ = it.j * TB;
+    const int nI = min(TB, n - rI), nJ = min(TB, n - rJ);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sUI = (T *)smem_raw;
+    T *sUJ = sUI + (size_t)TB * LDU;
+    double *sc = (double *)(sUJ + (size_t)TB * LDU); // x_I, y_I, x_J, y_J relative to the parent corner
+    const T *Ub = w.U + (size_t)b * w.U_stride + (size_t)v.o0 * UC;
+    {
+        const int cpr = UC * (int)sizeof(T) / 16;
+        for (int e = tid; e < nI * cpr; e += NT) {
+            const int a = e / cpr, q = e % cpr;
+            cp_async16((char *)(sUI + (size_t)a * LDU) + 16 * q, (const char *)(Ub + (size_t)(rI + a) * UC) + 16 * q);
+        }
+        for (int e = tid; e < nJ * cpr; e += NT) {
+            const int a = e / cpr, q = e % cpr;
+            cp_async16((char *)(sUJ + (size_t)a * LDU) + 16 * q, (const char *)(Ub + (size_t)(rJ + a) * UC) + 16 * q);
+        }
+        cp_async_commit();
+    }
+    const int64_t gp = M > 1 ? t.lvl_off[M - 1] + (v.c >> t.lgJ) : -1;
+    const double ox = gp >= 0 ? t.cx[gp] : t.sx[v.o0], oy = gp >= 0 ? t.cy[gp] : t.sy[v.o0];
+    for (int a = tid; a < TB; a += NT) {
+        sc[a] = a < nI ? t.sx[v.o0 + rI + a] - ox : 0.0;
+        sc[TB + a] = a < nI ? t.sy[v.o0 + rI + a] - oy : 0.0;
+        sc[2 * TB + a] = a < nJ ? t.sx[v.o0 + rJ + a] - ox : 0.0;
+        sc[3 * TB + a] = a < nJ ? t.sy[v.o0 + rJ + a] - oy : 0.0;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    const double tau2 = th[2], ib64 = 1.0 / th[1];
+    const int a0 = 2 * (tid / (TB / 2)), q0 = 2 * (tid % (TB / 2));
+    T hi[2][2], lo[2][2];
+    dot2x2_exact(sUI + a0 * LDU, sUI + min(a0 + 1, TB - 1) * LDU, sUJ + q0 * LDU, sUJ + min(q0 + 1, TB - 1) * LDU, UC,
+                 hi, lo);
+    const ff s2f = ff_from_double(th[0]), ibf = ff_from_double(ib64), tau2f = ff_from_double(tau2);
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const int a = a0 + i, q = q0 + j;
+            if (a >= nI || q >= nJ || (it.i == it.j && q > a)) continue;
+            const bool diag = it.i == it.j && a == q;
+            F val;
+            if constexpr (sizeof(T) == 4) {
+                const ff cv = ff_cov_exp(s2f, ibf, ff_from_double(sc[a]), ff_from_double(sc[TB + a]),
+                                         ff_from_double(sc[2 * TB + q]), ff_from_double(sc[3 * TB + q]));
+                val = ff_sub(cv, ff{(float)hi[i][j], (float)lo[i][j]});
+                if (diag) val = ff_add(val, tau2f);
+            } else {
+                const double cv = cov64(th[0], ib64, sc[a] - sc[2 * TB + q], sc[TB + a] - sc[3 * TB + q]);
+                val = cancel_sub(cv, hi[i][j], lo[i][j]) + (diag ? tau2 : 0.0);
+            }
+            v.V[(size_t)(rI + a) * n + rJ + q] = val;
+        }
+}
+
+template <typename T, int RP>
+__host__ __device__ constexpr size_t smem_big_potrf_bytes(int M)
+{
+    return (size_t)TB * (TB + 1) * 8 + (size_t)(3 * TB + 4) * 8 + 8 * 8 + (size_t)((tri_count(TB) * 2 + 15) & ~15) +
+           64 + (size_t)TB * ((M - 1) * RP + 4) * sizeof(T) + 64;
+}
+
+// Step k, diagonal tile: factor, log-determinant, and the diagonal solves of
+// the two right-hand sides.
+template <typename T, int RP>
+__global__ void __launch_bounds__(NT) k_big_potrf(DevTree t, Work<T> w, const BigLeaf *leaves, const BigTile *items,
+                                                  int k)
+{
+    using F = typename FacT<T>::type;
+    const BigTile it = items[blockIdx.x];
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const double *th = w.theta + 3 * b;
+    if (!theta_ok(th)) return;
+    const BigView<F> v = big_view(t, w, leaves[it.bl], b);
+    const int M = t.M, n = v.n, UC = (M - 1) * RP, LDU = UC + 4;
+    const int r0 = k * TB, nk = min(TB, n - r0);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    F *sL = (F *)smem_raw;                    // TB x (TB+1)
+    F *sy = sL + TB * (TB + 1);               // TB
+    F *srs = sy + TB;                         // TB + 2
+    F *sr2 = srs + TB + 2;                    // TB + 2
+    double *red = (double *)(sr2 + TB + 2);   // 8
+    int *flag = (int *)((unsigned char *)(red + 8) + ((tri_count(TB) * 2 + 15) & ~15));
+    T *sU = (T *)(flag + 16);                 // TB x LDU
+    T *Ub = w.U + (size_t)b * w.U_stride + (size_t)(v.o0 + r0) * UC;
+    {
+        const int cpr = UC * (int)sizeof(T) / 16;
+        for (int e = tid; e < nk * cpr; e += NT) {
+            const int a = e / cpr, q = e % cpr;
+            cp_async16((char *)(sU + (size_t)a * LDU) + 16 * q, (const char *)(Ub + (size_t)a * UC) + 16 * q);
+        }
+        cp_async_commit();
+    }
+    if (tid == 0) flag[0] = 0;
+    for (int e = tid; e < nk * nk; e += NT) {
+        const int a = e / nk, q = e % nk;
+        if (q <= a) sL[a * (TB + 1) + q] = v.V[(size_t)(r0 + a) * n + r0 + q];
+    }
+    for (int a = tid; a < nk; a += NT) sy[a] = k == 0 ? f_of<F>(t.sz[v.o0 + a]) : v.y[r0 + a];
+    __syncthreads();
+    chol_small<F, (tri_count(TB) + NT - 1) / NT>(sL, TB + 1, nk, srs, sr2, flag, MRA_SINGULAR);
+    const double ld = logdet_small(sL, TB + 1, nk, red);
+    // factor (transposed, upper triangle of the tile) and 1/L_jj to the scratch
+    for (int e = tid; e < nk * nk; e += NT) {
+        const int j = e / nk, i = e % nk;
+        if (i >= j) v.V[(size_t)(r0 + j) * n + r0 + i] = sL[j * (TB + 1) + i];
+    }
+    for (int j = tid; j < nk; j += NT) v.rs[r0 + j] = srs[j];
+    fwd_solve_vec(sL, TB + 1, srs, nk, sy);
+    if (tid < 32) {
+        F q = tid < nk ? f_sqr(sy[tid]) : f_of<F>(0.0);
+        q = warp_sum_f(q);
+        if (tid == 0) red[0] = f_dbl(q);
+    }
+    for (int a = tid; a < nk; a += NT) v.y[r0 + a] = sy[a];
+    cp_async_wait<0>();
+    __syncthreads();
+    const double uk = red[0];
+    fwd_solve_warp<T, TB>(sL, TB + 1, srs, sU, 1, LDU, sU, LDU, UC, nk);
+    {
+        const int cpr = UC * (int)sizeof(T) / 16;
+        for (int e = tid; e < nk * cpr; e += NT) {
+            const int a = e / cpr, q = e % cpr;
+            reinterpret_cast<int4 *>(Ub + (size_t)a * UC)[q] = reinterpret_cast<const int4 *>(sU + (size_t)a * LDU)[q];
+        }
+    }
+    if (tid == 0) {
+        v.du[0] = (k == 0 ? 0.0 : v.du[0]) + ld;
+        v.du[1] = (k == 0 ? 0.0 : v.du[1]) + uk;
+        if (flag[0]) w.status[b] = ST_ENOTPD;
+    }
+}
+
+constexpr int kBigUcChunk = 64;
+
+template <typename T, int RP>
+__host__ __device__ constexpr size_t smem_big_trsm_bytes()
+{
+    return (size_t)2 * TB * (TB + 1) * 8 + (size_t)2 * TB * 8 + (size_t)TB * kBigUcChunk * sizeof(T) + 64;
+}
+
+// Step k, tile column below the diagonal: L_ik = V_ik L_kk^{-T}, then the
+// right-hand sides of row block i take their share of block k.
+template <typename T, int RP>
+__global__ void __launch_bounds__(NT) k_big_trsm(DevTree t, Work<T> w, const BigLeaf *leaves, const BigTile *items,
+                                                 int k)
+{
+    using F = typename FacT<T>::type;
+    const BigTile it = items[blockIdx.x];
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const double *th = w.theta + 3 * b;
+    if (!theta_ok(th)) return;
+    const BigView<F> v = big_view(t, w, leaves[it.bl], b);
+    const int M = t.M, n = v.n, UC = (M - 1) * RP;
+    const int rk = k * TB, nk = min(TB, n - rk), ri = it.i * TB, ni = min(TB, n - ri);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    F *sK = (F *)smem_raw;          // factor of tile (k,k), transposed: sK[m][c] = L_cm (c >= m)
+    F *sA = sK + TB * (TB + 1);     // tile (i,k), then L_ik
+    F *srs = sA + TB * (TB + 1);    // TB
+    F *syk = srs + TB;              // TB
+    T *sY = (T *)(syk + TB);        // TB x kBigUcChunk
+    for (int e = tid; e < nk * nk; e += NT) {
+        const int m = e / nk, c = e % nk;
+        if (c >= m) sK[m * (TB + 1) + c] = v.V[(size_t)(rk + m) * n + rk + c];
+    }
+    for (int e = tid; e < ni * nk; e += NT) {
+        const int r = e / nk, c = e % nk;
+        sA[r * (TB + 1) + c] = v.V[(size_t)(ri + r) * n + rk + c];
+    }
+    for (int m = tid; m < nk; m += NT) {
+        srs[m] = v.rs[rk + m];
+        syk[m] = v.y[rk + m];
+    }
+    __syncthreads();
+    // rows r = warp + 8q; lanes own columns; x_m final at step m, broadcast
+    {
+        const int warp = tid >> 5, lane = tid & 31;
+        constexpr int RPW = TB / (NT / 32);
+        F a[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; q++) {
+            const int r = warp + (NT / 32) * q;
+            a[q] = (r < ni && lane < nk) ? sA[r * (TB + 1) + lane] : f_of<F>(0.0);
+        }
+        for (int m = 0; m < nk; m++) {
+            const F lcm = lane > m && lane < nk ? sK[m * (TB + 1) + lane] : f_of<F>(0.0);
+            const F rm = srs[m];
+#pragma unroll
+            for (int q = 0; q < RPW; q++) {
+                const F xm = f_shfl(f_mul(a[q], rm), m);
+                a[q] = lane == m ? xm : f_sub(a[q], f_mul(lcm, xm));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; q++) {
+            const int r = warp + (NT / 32) * q;
+            if (r < ni && lane < nk) {
+                sA[r * (TB + 1) + lane] = a[q];
+                v.V[(size_t)(ri + r) * n + rk + lane] = a[q];
+            }
+        }
+        __syncthreads();
+        // z_i -= L_ik y_k
+#pragma unroll
+        for (int q = 0; q < RPW; q++) {
+            const int r = warp + (NT / 32) * q;
+            F p = lane < nk && r < ni ? f_mul(sA[r * (TB + 1) + lane], syk[lane]) : f_of<F>(0.0);
+            p = warp_sum_f(p);
+            if (lane == 0 && r < ni) v.y[ri + r] = f_sub(k == 0 ? f_of<F>(t.sz[v.o0 + ri + r]) : v.y[ri + r], p);
+        }
+    }
+    // U_i -= L_ik Y_k, kBigUcChunk columns at a time
+    T *Ui = w.U + (size_t)b * w.U_stride + (size_t)(v.o0 + ri) * UC;
+    const T *Yk = w.U + (size_t)b * w.U_stride + (size_t)(v.o0 + rk) * UC;
+    constexpr int CPT = TB * kBigUcChunk / NT; // outputs per thread (8)
+    const int r = tid / (kBigUcChunk / CPT), c0 = (tid % (kBigUcChunk / CPT)) * CPT;
+    for (int cb = 0; cb < UC; cb += kBigUcChunk) {
+        __syncthreads();
+        for (int e = tid; e < TB * kBigUcChunk; e += NT) {
+            const int m = e / kBigUcChunk, cc = e % kBigUcChunk;
+            sY[e] = (m < nk && cb + cc < UC) ? Yk[(size_t)m * UC + cb + cc] : T(0);
+        }
+        __syncthreads();
+        if (r < ni) {
+            T acc[CPT];
+#pragma unroll
+            for (int cc = 0; cc < CPT; cc++) acc[cc] = T(0);
+            for (int m = 0; m < nk; m++) {
+                const T l = (T)f_hi(sA[r * (TB + 1) + m]);
+#pragma unroll
+                for (int cc = 0; cc < CPT; cc++) acc[cc] = fma(l, sY[m * kBigUcChunk + c0 + cc], acc[cc]);
+            }
+#pragma unroll
+            for (int cc = 0; cc < CPT; cc++)
+                if (cb + c0 + cc < UC) Ui[(size_t)r * UC + cb + c0 + cc] -= acc[cc];
+        }
+    }
+}
+
+template <typename T, int RP>
+__host__ __device__ constexpr size_t smem_big_update_bytes()
+{
+    return (size_t)2 * TB * (TB + 1) * 8 + 64;
+}
+
+// Step k, trailing tile (i, j), k < j <= i: V_ij -= L_ik L_jk'.
+template <typename T, int RP>
+__global__ void __launch_bounds__(NT) k_big_update(DevTree t, Work<T> w, const BigLeaf *leaves, const BigTile *items,
+                                                   int k)
+{
+    using F = typename FacT<T>::type;
+    const BigTile it = items[blockIdx.x];
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const double *th = w.theta + 3 * b;
+    if (!theta_ok(th)) return;
+    const BigView<F> v = big_view(t, w, leaves[it.bl], b);
+    const int n = v.n;
+    const int rk = k * TB, nk = min(TB, n - rk);
+    const int ri = it.i * TB, ni = min(TB, n - ri), rj = it.j * TB, nj = min(TB, n - rj);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    F *sLi = (F *)smem_raw;
+    F *sLj = sLi + TB * (TB + 1);
+    for (int e = tid; e < TB * TB; e += NT) {
+        const int r = e / TB, m = e % TB;
+        sLi[r * (TB + 1) + m] = (r < ni && m < nk) ? v.V[(size_t)(ri + r) * n + rk + m] : f_of<F>(0.0);
+        sLj[r * (TB + 1) + m] = (r < nj && m < nk) ? v.V[(size_t)(rj + r) * n + rk + m] : f_of<F>(0.0);
+    }
+    __syncthreads();
+    const int a0 = 2 * (tid / (TB / 2)), q0 = 2 * (tid % (TB / 2));
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const int a = a0 + i, q = q0 + j;
+            F sum;
+            if constexpr (sizeof(T) == 4) {
+                FFAcc acc;
+                ffacc_zero(acc);
+                for (int m = 0; m < nk; m++) ffacc_add(acc, sLi[a * (TB + 1) + m], sLj[q * (TB + 1) + m]);
+                sum = ffacc_value(acc);
+            } else {
+                double acc = 0.0;
+                for (int m = 0; m < nk; m++) acc = fma(sLi[a * (TB + 1) + m], sLj[q * (TB + 1) + m], acc);
+                sum = acc;
+            }
+            if (a < ni && q < nj && (it.i != it.j || q <= a)) {
+                F *p = v.V + (size_t)(ri + a) * n + rj + q;
+                *p = f_sub(*p, sum);
+            }
+        }
+}
+
+// Per leaf after the last step: w = Y'y and the (d, u) terms.
+template <typename T, int RP>
+__global__ void __launch_bounds__(NT) k_big_finish(DevTree t, Work<T> w, const BigLeaf *leaves)
+{
+    using F = typename FacT<T>::type;
+    const int b = blockIdx.y;
+    const double *th = w.theta + 3 * b;
+    if (!theta_ok(th)) return;
+    const BigView<F> v = big_view(t, w, leaves[blockIdx.x], b);
+    const int M = t.M, UC = (M - 1) * RP;
+    const T *Y = w.U + (size_t)b * w.U_stride + (size_t)v.o0 * UC;
+    gram_vec(Y, UC, UC, v.y, v.n, w.leaf_w + (size_t)b * w.leafw_stride + (size_t)v.c * UC);
+    if (threadIdx.x == 0) {
+        double *du = w.leaf_du + (size_t)b * w.leafdu_stride + 2 * v.c;
+        du[0] = v.du[0];
+        du[1] = v.du[1];
+        if (w.reg_du) {
+            double *r = w.reg_du + (size_t)b * w.regdu_stride + 2 * (t.lvl_off[M] + v.c);
+            r[0] = v.du[0];
+            r[1] = v.du[1];
+        }
+    }
+}
+
+} // namespace mra

@@ -88,10 +88,18 @@ struct BigLeaf {
     int64_t voff; // element offset (doubles) of its scratch in Vbig
 };
 
-// Scratch of one large leaf in Vbig, in 8-byte slots: V (n^2), its factor in
-// the storage type (n^2), y (n), reciprocal pivots (n), 1/diag in the storage
-// type (n).
-inline int64_t big_leaf_scratch(int64_t n) { return 2 * n * n + 3 * n; }
+// Large leaves are factored in square tiles of kBigTile rows.
+constexpr int kBigTile = 32;
+
+// One work item of the tiled large-leaf kernels: leaf bl (index into the
+// BigLeaf list), tile row i, tile column j.
+struct BigTile {
+    int32_t bl, i, j, pad;
+};
+
+// Scratch of one large leaf in Vbig, in 8-byte slots: V and its factor
+// (n^2), z then y (n), reciprocal pivots (n), (log-det, quadratic form) (2).
+inline int64_t big_leaf_scratch(int64_t n) { return n * n + 2 * n + 2; }
 
 // Observation rows per leaf-basis chunk: 64 in FP32, 32 in FP64 (shared memory).
 template <typename T> __host__ __device__ constexpr int chunk_rows() { return sizeof(T) == 4 ? 64 : 32; }
@@ -105,9 +113,11 @@ int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, in
 template <typename T, int RP>
 int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves,
                           int nmax, int B, void *stream);
+// Tiled large-leaf posterior: one launch per phase; items of that phase.
+enum BigPhase { BIG_ASSEMBLE = 0, BIG_POTRF = 1, BIG_TRSM = 2, BIG_UPDATE = 3, BIG_FINISH = 4 };
 template <typename T, int RP>
-int launch_leafpost_big(const DevTree &t, const Work<T> &w, const BigLeaf *leaves, int nleaves,
-                        int B, void *stream);
+int launch_big(const DevTree &t, const Work<T> &w, int phase, const BigLeaf *leaves, const BigTile *items,
+               int nitems, int k, int B, void *stream);
 template <typename T, int RP>
 int launch_leafgram(const DevTree &t, const Work<T> &w, int nP, int B, void *stream);
 template <typename T, int RP>
@@ -121,5 +131,6 @@ template <typename T, int RP> size_t smem_leafbasis(int M);
 template <typename T, int RP> size_t smem_leafpost_small(int M, int nmax);
 template <typename T, int RP> size_t smem_up(int m);
 template <typename T, int RP> size_t smem_leafgram(int M);
+template <typename T, int RP> size_t smem_big(int M);
 
 } // namespace mra

@@ -291,6 +291,40 @@ __device__ __forceinline__ void dot2x2(const float *a0, const float *a1, const f
             lo[i][j] = __fsub_rn(s[i][j].lo, __fsub_rn(t, s[i][j].hi));
         }
 }
+// As dot2x2 with every product exact (TwoProd) and the running sums kept as
+// float pairs (TwoSum): the float-float product sum of the FP32 operands,
+// for leaves whose covariance loses many digits to cancellation (tight
+// clusters of observations).
+__device__ __forceinline__ void dot2x2_exact(const float *a0, const float *a1, const float *q0, const float *q1,
+                                             int K, float (&hi)[2][2], float (&lo)[2][2])
+{
+    FF s[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) s[i][j] = FF{0.f, 0.f};
+    for (int k = 0; k < K; k += 4) {
+        const float4 x[2] = {*(const float4 *)(a0 + k), *(const float4 *)(a1 + k)};
+        const float4 y[2] = {*(const float4 *)(q0 + k), *(const float4 *)(q1 + k)};
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                ff_add_prod(s[i][j], x[i].x, y[j].x);
+                ff_add_prod(s[i][j], x[i].y, y[j].y);
+                ff_add_prod(s[i][j], x[i].z, y[j].z);
+                ff_add_prod(s[i][j], x[i].w, y[j].w);
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const float t = __fadd_rn(s[i][j].hi, s[i][j].lo);
+            hi[i][j] = t;
+            lo[i][j] = __fsub_rn(s[i][j].lo, __fsub_rn(t, s[i][j].hi));
+        }
+}
 __device__ __forceinline__ void dot2x2(const double *a0, const double *a1, const double *q0, const double *q1, int K,
                                        double (&hi)[2][2], double (&lo)[2][2])
 {
@@ -309,6 +343,11 @@ __device__ __forceinline__ void dot2x2(const double *a0, const double *a1, const
             hi[i][j] = p[i][j];
             lo[i][j] = 0.0;
         }
+}
+__device__ __forceinline__ void dot2x2_exact(const double *a0, const double *a1, const double *q0, const double *q1,
+                                             int K, double (&hi)[2][2], double (&lo)[2][2])
+{
+    dot2x2(a0, a1, q0, q1, K, hi, lo);
 }
 
 // C - (hi + lo) with the leading subtraction done first: when C and hi agree
@@ -582,13 +621,16 @@ __device__ void trinv_warp(const F *A, int lda, const F *rs, T *out, int ldo, in
 }
 
 // X = L^{-1} B for ncol right-hand sides, L the chol_small factor of order
-// N <= 32 (L[k][i] = A[i][k]).  Column col of B is read at src + col * lds
-// (lane-contiguous), column col of X is written to X[a * ldx + col].  Warps
+// N <= 32 (L[k][i] = A[i][k]).  Element a of column col of B is read at
+// src[col * cs + a * ls], element a of column col of X is written to
+// X[a * ldx + col] (X may be B itself when B is stored that way).  Only the
+// leading nrow <= N rows take part (rows beyond are left as garbage).  Warps
 // own columns (col = warp + 8j, four at a time), lanes own rows; each lane
 // keeps its row of L and its reciprocal pivot in registers, and at step i the
 // owner of row i scales x_i and one shuffle broadcasts it.
 template <typename T, int N, typename F>
-__device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, int lds, T *X, int ldx, int ncol)
+__device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, int cs, int ls, T *X, int ldx,
+                               int ncol, int nrow = N)
 {
     static_assert(N <= 32, "one row per lane");
     constexpr int NW = NT / 32, CB = 4;
@@ -602,15 +644,16 @@ __device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, i
 #pragma unroll
         for (int cc = 0; cc < CB; cc++) {
             const int col = warp + NW * (j0 + cc);
-            x[cc] = (col < ncol && lane < N) ? src[(size_t)col * lds + lane] : T(0);
+            x[cc] = (col < ncol && lane < N) ? src[(size_t)col * cs + (size_t)lane * ls] : T(0);
         }
 #pragma unroll
         for (int i = 0; i < N; i++)
+            if (i < nrow)
 #pragma unroll
-            for (int cc = 0; cc < CB; cc++) {
-                const T xi = __shfl_sync(0xffffffffu, x[cc] * rl, i);
-                x[cc] = lane == i ? xi : fma(-Lr[i], xi, x[cc]);
-            }
+                for (int cc = 0; cc < CB; cc++) {
+                    const T xi = __shfl_sync(0xffffffffu, x[cc] * rl, i);
+                    x[cc] = lane == i ? xi : fma(-Lr[i], xi, x[cc]);
+                }
 #pragma unroll
         for (int cc = 0; cc < CB; cc++) {
             const int col = warp + NW * (j0 + cc);
@@ -838,21 +881,6 @@ __host__ __device__ constexpr size_t smem_leafpost_bytes(int M, int nmax)
            (size_t)nmax * nmax * sizeof(T) + 2 * (size_t)nmax * 8 + 80;
 }
 
-// Forward solve of UC columns of U (ld ldu, type T) with the lower T factor
-// LT (ld ldt) and the reciprocals of its diagonal, one column per thread.
-template <typename T>
-__device__ void fwd_solve_cols(const T *LT, int ldt, const T *dinv, T *U, int ldu, int UC, int n)
-{
-    for (int col = threadIdx.x; col < UC; col += NT) {
-        for (int a = 0; a < n; a++) {
-            T s = U[(size_t)a * ldu + col];
-            for (int q = 0; q < a; q++) s = fma(-LT[(size_t)a * ldt + q], U[(size_t)q * ldu + col], s);
-            U[(size_t)a * ldu + col] = s * dinv[a];
-        }
-    }
-    __syncthreads();
-}
-
 // w[col] = sum_a Y[a][col] y[a] for UC columns (exact FP32 products of Y and
 // the leading part of y in the mixed mode).
 template <typename T, typename F>
@@ -1063,84 +1091,6 @@ static __device__ void fwd_solve_vec_big(const F *A, int lda, const F *rs, int n
         }
     }
     __syncthreads();
-}
-
-template <typename T, int RP>
-__global__ void __launch_bounds__(NT) k_leafpost_big(DevTree t, Work<T> w, const BigLeaf *leaves)
-{
-    using F = typename FacT<T>::type;
-    const BigLeaf bl = leaves[blockIdx.x];
-    const int64_t c = bl.leaf;
-    const int b = blockIdx.y, tid = threadIdx.x;
-    const double *th = w.theta + 3 * b;
-    if (!theta_ok(th)) return;
-    const double tau2 = th[2], ib64 = 1.0 / th[1];
-    const int M = t.M;
-    const int64_t o0 = t.leaf_off[c];
-    const int n = (int)(t.leaf_off[c + 1] - o0);
-    const int UC = (M - 1) * RP;
-    __shared__ double red[32];
-    __shared__ double sc[2];
-    __shared__ F sr;
-    __shared__ int flag[4];
-    // scratch: V (n^2 F), its factor as T (n^2 slots), y (n F), rs (n F), 1/diag (n T)
-    double *base = w.Vbig + (size_t)b * w.V_stride + bl.voff;
-    F *V = (F *)base;
-    T *LT = (T *)(base + (size_t)n * n);
-    F *yb = (F *)(base + 2 * (size_t)n * n);
-    F *rs = yb + n;
-    T *dinv = (T *)(rs + n);
-    T *Ub = w.U + (size_t)b * w.U_stride + (size_t)o0 * UC;
-    const double *px = t.sx + o0, *py = t.sy + o0, *pz = t.sz + o0;
-    const int64_t gp = M > 1 ? t.lvl_off[M - 1] + (c >> t.lgJ) : -1;
-    const double ox = gp >= 0 ? t.cx[gp] : px[0], oy = gp >= 0 ? t.cy[gp] : py[0];
-    if (tid == 0) flag[0] = 0;
-    for (int a = tid; a < n; a += NT) yb[a] = f_of<F>(pz[a]);
-    const ff tau2f = ff_from_double(tau2);
-    for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
-        const int a = (int)(e / n), q = (int)(e % n);
-        if (q <= a) {
-            T hi, lo;
-            dot2(Ub + (size_t)a * UC, Ub + (size_t)q * UC, UC, hi, lo);
-            if constexpr (sizeof(T) == 4) {
-                const ff cv = ff_cov_exp(ff_from_double(th[0]), ff_from_double(ib64), ff_from_double(px[a] - ox),
-                                         ff_from_double(py[a] - oy), ff_from_double(px[q] - ox),
-                                         ff_from_double(py[q] - oy));
-                ff v = ff_sub(cv, ff{(float)hi, (float)lo});
-                if (a == q) v = ff_add(v, tau2f);
-                V[(size_t)a * n + q] = v;
-            } else {
-                const double cv = cov64(th[0], ib64, (px[a] - ox) - (px[q] - ox), (py[a] - oy) - (py[q] - oy));
-                V[(size_t)a * n + q] = cancel_sub(cv, hi, lo) + (a == q ? tau2 : 0.0);
-            }
-        }
-    }
-    __syncthreads();
-    chol_global(V, n, n, rs, flag, sc, &sr);
-    for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
-        const int a = (int)(e / n), q = (int)(e % n);
-        LT[e] = q <= a ? (T)f_hi(V[(size_t)a * n + q]) : T(0);
-    }
-    for (int a = tid; a < n; a += NT) dinv[a] = (T)f_hi(rs[a]);
-    __syncthreads();
-    fwd_solve_cols(LT, n, dinv, Ub, UC, UC, n);
-    fwd_solve_vec_big(V, n, rs, n, yb);
-    double uv = 0.0;
-    for (int a = tid; a < n; a += NT) uv += f_dbl(f_sqr(yb[a]));
-    uv = block_sum(uv, red);
-    const double dv = logdet_small(V, n, n, red);
-    gram_vec(Ub, UC, UC, yb, n, w.leaf_w + (size_t)b * w.leafw_stride + (size_t)c * UC);
-    if (tid == 0) {
-        double *du = w.leaf_du + (size_t)b * w.leafdu_stride + 2 * c;
-        du[0] = dv;
-        du[1] = uv;
-        if (w.reg_du) {
-            double *r = w.reg_du + (size_t)b * w.regdu_stride + 2 * (t.lvl_off[M] + c);
-            r[0] = dv;
-            r[1] = uv;
-        }
-        if (flag[0]) w.status[b] = ST_ENOTPD;
-    }
 }
 
 // --------------------------------------------------------------- leaf Gram --
@@ -1376,7 +1326,7 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
     // right-hand column (k, bc) is A^{m,k}[.][bc] = A^{k,m}[bc][.], contiguous in sC
     const int ncol = (m - 1) * RP, ldz = ncol + 4;
     for (int a = tid; a < RP; a += NT) sz[a] = f_of<F>(sw[(m - 1) * RP + a]);
-    fwd_solve_warp<T, RP>(sL, RP + 1, srs, sC, RP, sZ, ldz, ncol);
+    fwd_solve_warp<T, RP>(sL, RP + 1, srs, sC, RP, 1, sZ, ldz, ncol);
     fwd_solve_vec(sL, RP + 1, srs, RP, sz);
     if (tid < 32) {
         F q = tid < RP ? f_sqr(sz[tid]) : f_of<F>(0.0);
@@ -1461,3 +1411,5 @@ __global__ void k_root_single(DevTree t, Work<T> w)
 }
 
 } // namespace mra
+
+#include "mra_bigleaf.cuh"

@@ -21,6 +21,11 @@ template <typename T, int RP> size_t smem_leafbasis(int M) { return smem_leafbas
 template <typename T, int RP> size_t smem_leafpost_small(int M, int nmax) { return smem_leafpost_bytes<T, RP>(M, nmax); }
 template <typename T, int RP> size_t smem_up(int m) { return smem_up_bytes<T, RP>(m); }
 template <typename T, int RP> size_t smem_leafgram(int M) { return smem_leafgram_bytes<T, RP>(M); }
+template <typename T, int RP> size_t smem_big(int M)
+{
+    size_t a = smem_big_assemble_bytes<T, RP>(M), p = smem_big_potrf_bytes<T, RP>(M);
+    return a > p ? a : p;
+}
 
 template <typename T, int RP>
 int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream)
@@ -69,12 +74,39 @@ int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *lea
 }
 
 template <typename T, int RP>
-int launch_leafpost_big(const DevTree &t, const Work<T> &w, const BigLeaf *leaves, int nleaves, int B,
-                        void *stream)
+int launch_big(const DevTree &t, const Work<T> &w, int phase, const BigLeaf *leaves, const BigTile *items,
+               int nitems, int k, int B, void *stream)
 {
-    if (nleaves == 0) return 0;
-    dim3 grid((unsigned)nleaves, (unsigned)B);
-    k_leafpost_big<T, RP><<<grid, NT, 0, (cudaStream_t)stream>>>(t, w, leaves);
+    static size_t done_a = 0, done_p = 0, done_t = 0, done_u = 0;
+    if (nitems == 0) return 0;
+    dim3 grid((unsigned)nitems, (unsigned)B);
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t sm;
+    switch (phase) {
+    case BIG_ASSEMBLE:
+        sm = smem_big_assemble_bytes<T, RP>(t.M);
+        if (int e = set_smem(k_big_assemble<T, RP>, sm, &done_a)) return e;
+        k_big_assemble<T, RP><<<grid, NT, sm, s>>>(t, w, leaves, items);
+        break;
+    case BIG_POTRF:
+        sm = smem_big_potrf_bytes<T, RP>(t.M);
+        if (int e = set_smem(k_big_potrf<T, RP>, sm, &done_p)) return e;
+        k_big_potrf<T, RP><<<grid, NT, sm, s>>>(t, w, leaves, items, k);
+        break;
+    case BIG_TRSM:
+        sm = smem_big_trsm_bytes<T, RP>();
+        if (int e = set_smem(k_big_trsm<T, RP>, sm, &done_t)) return e;
+        k_big_trsm<T, RP><<<grid, NT, sm, s>>>(t, w, leaves, items, k);
+        break;
+    case BIG_UPDATE:
+        sm = smem_big_update_bytes<T, RP>();
+        if (int e = set_smem(k_big_update<T, RP>, sm, &done_u)) return e;
+        k_big_update<T, RP><<<grid, NT, sm, s>>>(t, w, leaves, items, k);
+        break;
+    default:
+        k_big_finish<T, RP><<<grid, NT, 0, s>>>(t, w, leaves);
+        break;
+    }
     return (int)cudaGetLastError();
 }
 
@@ -118,8 +150,9 @@ int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream)
     template int launch_leafbasis<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, void *); \
     template int launch_leafpost_small<T, RP>(const DevTree &, const Work<T> &, const int64_t *, int, int,   \
                                               int, void *);                                                 \
-    template int launch_leafpost_big<T, RP>(const DevTree &, const Work<T> &, const BigLeaf *, int, int,    \
-                                            void *);                                                        \
+    template size_t smem_big<T, RP>(int);                                                                   \
+    template int launch_big<T, RP>(const DevTree &, const Work<T> &, int, const BigLeaf *, const BigTile *, \
+                                   int, int, int, void *);                                                  \
     template int launch_leafgram<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                \
     template int launch_up<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                      \
     template int launch_root_single<T, RP>(const DevTree &, const Work<T> &, int, void *);
