@@ -276,6 +276,10 @@ struct mra_ctx {
     // per-theta scratch: one allocation for `cap` theta, sized for FP64
     int cap = 0;     // theta the scratch currently holds
     int max_cap = 1; // theta per device pass allowed by the memory budget
+    int user_max_batch = 0;
+    size_t hbm_budget = 0;   // from the options (0 = 60% of free HBM)
+    int ain_chunk = 0;       // level M-1 regions per Ain chunk (0 = the whole level)
+    int status_cap = 0;      // theta the status array holds
     unsigned char *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     size_t per_theta_bytes = 0;
@@ -347,7 +351,8 @@ Plan make_plan(const mra_ctx *c)
     p.leafdu = 2 * (size_t)P.nleaf();
     p.V = (size_t)c->vbig_elems;
     if (M >= 2) {
-        const size_t nP = (size_t)(P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1]);
+        size_t nP = (size_t)(P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1]);
+        if (c->ain_chunk > 0) nP = std::min(nP, (size_t)c->ain_chunk);
         p.Ain = nP * (size_t)(M - 1) * M / 2 * B2;
         p.Ainw = nP * (size_t)(M - 1) * RP;
         p.Aindu = 2 * nP;
@@ -386,14 +391,8 @@ Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
         off = align256(off + elems * (size_t)B * sizeof(double));
         return q;
     };
-    // the layout is computed for sizeof(double) per T element so that both
-    // precisions share one allocation
-    auto takeT8 = [&](size_t elems) {
-        T *q = (T *)(base + off);
-        off = align256(off + elems * (size_t)B * sizeof(double));
-        return q;
-    };
-    (void)takeT;
+    // T arrays in sizeof(T): the allocation is sized for the precision in use
+    auto takeT8 = takeT;
     w.prior = takeT8(p.prior);
     w.prior_stride = p.prior;
     for (int m = 0; m <= MRA_MAXM; m++) w.prior_lvl[m] = p.prior_lvl[m];
@@ -423,22 +422,27 @@ Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
     return w;
 }
 
+// Bytes of the per-theta scratch for B theta; arrays of the storage type
+// take 4 bytes per element in the mixed mode and 8 in the FP64 mode (the
+// layout make_work<T> lays out).
 size_t scratch_bytes_for(const Plan &p, const mra_ctx *c, int B)
 {
+    const size_t ts = c->precision == MRA_MIXED ? sizeof(float) : sizeof(double);
     size_t s = 0;
-    auto add = [&](size_t elems) { s = align256(s + elems * (size_t)B * sizeof(double)); };
-    add(p.prior);
-    add(p.U);
-    add(p.leafw);
-    add(p.leafdu);
-    add(p.V);
-    add(p.Ain);
-    add(p.Ainw);
-    add(p.Aindu);
+    auto addT = [&](size_t elems) { s = align256(s + elems * (size_t)B * ts); };
+    auto addD = [&](size_t elems) { s = align256(s + elems * (size_t)B * sizeof(double)); };
+    addT(p.prior);
+    addT(p.U);
+    addT(p.leafw);
+    addD(p.leafdu);
+    addD(p.V);
+    addT(p.Ain);
+    addD(p.Ainw);
+    addD(p.Aindu);
     for (int m = 2; m <= c->P.M - 1; m++) {
-        add(p.Atil[m]);
-        add(p.Atilw[m]);
-        add(p.Atildu[m]);
+        addT(p.Atil[m]);
+        addD(p.Atilw[m]);
+        addD(p.Atildu[m]);
     }
     return s;
 }
@@ -534,9 +538,17 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     }
     if (M > 1) {
         const int nP = (int)(c->P.lvl_off[(size_t)M] - c->P.lvl_off[(size_t)M - 1]);
-        if ((e = timed_launch(c, K_LEAFGRAM, s, [&] { return launch_leafgram<T, RP>(t, w, nP, B, s); }))) return e;
+        const int chunk = c->ain_chunk > 0 ? c->ain_chunk : nP;
+        for (int p0 = 0; p0 < nP; p0 += chunk) {
+            const int cnt = std::min(chunk, nP - p0);
+            if ((e = timed_launch(c, K_LEAFGRAM, s, [&] { return launch_leafgram<T, RP>(t, w, p0, cnt, B, s); })))
+                return e;
+            if ((e = timed_launch(c, K_UP, s, [&] { return launch_up<T, RP>(t, w, M - 1, p0, cnt, B, s); })))
+                return e;
+        }
         for (int m = M - 1; m >= 1; m--)
-            if ((e = timed_launch(c, K_UP, s, [&] { return launch_up<T, RP>(t, w, m, B, s); }))) return e;
+            if (m < M - 1 && (e = timed_launch(c, K_UP, s, [&] { return launch_up<T, RP>(t, w, m, 0, -1, B, s); })))
+                return e;
     } else {
         if ((e = timed_launch(c, K_ROOT, s, [&] { return launch_root_single<T, RP>(t, w, B, s); }))) return e;
     }
@@ -631,9 +643,12 @@ void count_work(mra_ctx *c)
 
 mra_status ensure_capacity(mra_ctx *c, int B)
 {
-    if (B <= c->cap) return MRA_OK;
     Plan p = make_plan(c);
     const size_t bytes = scratch_bytes_for(p, c, B);
+    if (c->d_scratch && bytes <= c->scratch_bytes && B <= c->status_cap) {
+        c->cap = B;
+        return MRA_OK;
+    }
     if (c->d_scratch) {
         cudaFree(c->d_scratch);
         c->bytes_held -= c->scratch_bytes;
@@ -660,19 +675,38 @@ mra_status ensure_capacity(mra_ctx *c, int B)
     c->scratch_bytes = bytes;
     c->bytes_held += bytes;
     c->cap = B;
+    c->status_cap = B;
     return MRA_OK;
 }
 
+// Theta per device pass for the current precision, and the Ain chunking:
+// the level M-1 Gram blocks (the largest per-theta array on deep trees) are
+// produced and consumed chunk by chunk only when one theta would not fit
+// otherwise.
 int max_batch_for(mra_ctx *c, size_t budget)
 {
-    Plan p = make_plan(c);
-    const size_t per = scratch_bytes_for(p, c, 1) + 4096;
-    c->per_theta_bytes = per;
     if (budget == 0) {
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)8 << 30;
-        budget = (size_t)(0.6 * (double)fr);
+        budget = (size_t)(0.6 * (double)(fr + c->scratch_bytes));
     }
+    c->ain_chunk = 0;
+    Plan p = make_plan(c);
+    size_t per = scratch_bytes_for(p, c, 1) + 4096;
+    const int M = c->P.M;
+    if (per > budget && M >= 2 && p.Ain > 0) {
+        const int64_t nP = c->P.lvl_off[(size_t)M] - c->P.lvl_off[(size_t)M - 1];
+        const size_t full_ain = scratch_bytes_for(p, c, 1);
+        c->ain_chunk = 1;
+        const size_t base = scratch_bytes_for(make_plan(c), c, 1);
+        const double per_region = (double)(full_ain - base) / (double)std::max<int64_t>(nP - 1, 1);
+        const double room = (double)budget - (double)base - 4096.0;
+        int64_t chunk = room > 0 ? (int64_t)(room / std::max(per_region, 1.0)) : 1;
+        chunk = std::max<int64_t>(1, std::min<int64_t>(chunk, nP));
+        c->ain_chunk = (int)chunk;
+        per = scratch_bytes_for(make_plan(c), c, 1) + 4096;
+    }
+    c->per_theta_bytes = per;
     size_t b = budget / per;
     if (b < 1) b = 1;
     if (b > 1024) b = 1024;
@@ -931,6 +965,8 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     for (int k = 0; k < kLeafBuckets; k++) c->nl[k] = (int)lb[k].size();
     c->nbig = (int)big.size();
     count_work(c);
+    c->hbm_budget = opt.hbm_budget;
+    c->user_max_batch = opt.max_batch;
     const int mb = max_batch_for(c, opt.hbm_budget);
     c->max_cap = opt.max_batch > 0 ? std::min(opt.max_batch, 1024) : mb;
     st = ensure_capacity(c, 1);
@@ -949,7 +985,14 @@ mra_status mra_set_precision(mra_ctx *c, int precision)
         c->err = "precision must be MRA_FP64 or MRA_MIXED";
         return MRA_EINVAL;
     }
+    if (precision == c->precision) return MRA_OK;
     c->precision = precision;
+    if (c->d_sx) {
+        // the scratch layout and the theta per pass depend on the storage type
+        const int mb = max_batch_for(c, c->hbm_budget);
+        c->max_cap = c->user_max_batch > 0 ? std::min(c->user_max_batch, 1024) : mb;
+        c->cap = 0;
+    }
     return MRA_OK;
 }
 

@@ -17,6 +17,9 @@
 //   Ain        level M-1 regions: A = sum over the leaf children of Y'Y, packed
 //              upper blocks (k <= l, pair index l(l-1)/2 + k-1), each RP x RP
 //              row-major; Ain_w (FP64) the summed w, Ain_du the summed (d, u).
+//              Holds one chunk of consecutive regions when the whole level
+//              does not fit (the leaf Gram and the level M-1 upward step then
+//              run chunk by chunk).
 //   Atil[m]    level m regions (2 <= m <= M-1): ATilde after the region's
 //              step, blocks (k <= l <= m-1), same packing, plus w (FP64) and (d, u).
 #pragma once
@@ -119,9 +122,9 @@ template <typename T, int RP>
 int launch_big(const DevTree &t, const Work<T> &w, int phase, const BigLeaf *leaves, const BigTile *items,
                int nitems, int k, int B, void *stream);
 template <typename T, int RP>
-int launch_leafgram(const DevTree &t, const Work<T> &w, int nP, int B, void *stream);
+int launch_leafgram(const DevTree &t, const Work<T> &w, int reg0, int nP, int B, void *stream);
 template <typename T, int RP>
-int launch_up(const DevTree &t, const Work<T> &w, int m, int B, void *stream);
+int launch_up(const DevTree &t, const Work<T> &w, int m, int reg0, int nreg, int B, void *stream);
 template <typename T, int RP>
 int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream);
 

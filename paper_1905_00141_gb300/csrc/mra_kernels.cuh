@@ -1109,12 +1109,13 @@ __host__ __device__ constexpr size_t smem_leafgram_bytes(int M)
 }
 
 template <typename T, int RP>
-__global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w)
+__global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w, int reg0)
 {
     constexpr int TS = kGramTile, RW = kGramRows;
     using TL = Tile<TS, TS>;
     constexpr int RT = TL::RT, CT = TL::CT;
-    const int P = blockIdx.x, b = blockIdx.z, tid = threadIdx.x;
+    // region P of level M-1; Ain holds the regions reg0, reg0 + 1, ... of this launch
+    const int P = reg0 + blockIdx.x, Pl = blockIdx.x, b = blockIdx.z, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
     const int M = t.M, J = t.J, D = M - 1, UC = D * RP;
@@ -1185,7 +1186,7 @@ __global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w)
         __syncthreads();
     }
     // scatter into the packed 32 x 32 (RP x RP) blocks with k <= l
-    T *out = w.Ain + (size_t)b * w.Ain_stride + (size_t)P * np * RP * RP;
+    T *out = w.Ain + (size_t)b * w.Ain_stride + (size_t)Pl * np * RP * RP;
 #pragma unroll
     for (int r = 0; r < RT; r++) {
         const int gr = ca + i0 + r;
@@ -1202,7 +1203,7 @@ __global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w)
     if (blockIdx.y == 0) {
         const T *lw = w.leaf_w + (size_t)b * w.leafw_stride;
         const double *ldu = w.leaf_du + (size_t)b * w.leafdu_stride;
-        double *wo = w.Ain_w + (size_t)b * w.Ainw_stride + (size_t)P * UC;
+        double *wo = w.Ain_w + (size_t)b * w.Ainw_stride + (size_t)Pl * UC;
         for (int col = tid; col < UC; col += NT) {
             double s = 0.0;
             for (int j = 0; j < J; j++) {
@@ -1220,7 +1221,7 @@ __global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w)
                     u += ldu[2 * c + 1];
                 }
             }
-            double *du = w.Ain_du + (size_t)b * w.Aindu_stride + 2 * (size_t)P;
+            double *du = w.Ain_du + (size_t)b * w.Aindu_stride + 2 * (size_t)Pl;
             du[0] = d;
             du[1] = u;
         }
@@ -1242,12 +1243,13 @@ __host__ __device__ constexpr size_t smem_up_bytes(int m)
 }
 
 template <typename T, int RP>
-__global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
+__global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0)
 {
     using TL = Tile<RP, RP>;
     using F = typename FacT<T>::type;
     constexpr int B2 = RP * RP;
-    const int i = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+    // region i of level m; at m = M-1 the Ain buffer holds regions reg0, reg0 + 1, ...
+    const int i = reg0 + blockIdx.x, il = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) {
         if (m == 1 && tid == 0) {
@@ -1274,9 +1276,9 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m)
     const double *wv[4], *dus[4];
     for (int s = 0; s < nsrc; s++) {
         if (direct) {
-            blk[s] = w.Ain + (size_t)b * w.Ain_stride + (size_t)i * np * B2;
-            wv[s] = w.Ain_w + (size_t)b * w.Ainw_stride + (size_t)i * m * RP;
-            dus[s] = w.Ain_du + (size_t)b * w.Aindu_stride + 2 * (size_t)i;
+            blk[s] = w.Ain + (size_t)b * w.Ain_stride + (size_t)il * np * B2;
+            wv[s] = w.Ain_w + (size_t)b * w.Ainw_stride + (size_t)il * m * RP;
+            dus[s] = w.Ain_du + (size_t)b * w.Aindu_stride + 2 * (size_t)il;
         } else {
             const int64_t ch = (int64_t)i * J + s;
             blk[s] = w.Atil[m + 1] + (size_t)b * w.Atil_stride[m + 1] + (size_t)ch * np * B2;

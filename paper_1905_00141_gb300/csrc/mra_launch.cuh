@@ -111,25 +111,27 @@ int launch_big(const DevTree &t, const Work<T> &w, int phase, const BigLeaf *lea
 }
 
 template <typename T, int RP>
-int launch_leafgram(const DevTree &t, const Work<T> &w, int nP, int B, void *stream)
+int launch_leafgram(const DevTree &t, const Work<T> &w, int reg0, int nP, int B, void *stream)
 {
     static size_t done = 0;
     const size_t sm = smem_leafgram_bytes<T, RP>(t.M);
     if (int e = set_smem(k_leafgram<T, RP>, sm, &done)) return e;
     const int nt = ((t.M - 1) * RP + kGramTile - 1) / kGramTile;
     dim3 grid((unsigned)nP, (unsigned)(nt * (nt + 1) / 2), (unsigned)B);
-    k_leafgram<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w);
+    k_leafgram<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, reg0);
     return (int)cudaGetLastError();
 }
 
+// regions reg0 .. reg0 + nreg - 1 of level m (nreg < 0: the whole level)
 template <typename T, int RP>
-int launch_up(const DevTree &t, const Work<T> &w, int m, int B, void *stream)
+int launch_up(const DevTree &t, const Work<T> &w, int m, int reg0, int nreg, int B, void *stream)
 {
     static size_t done = 0;
     const size_t sm = smem_up_bytes<T, RP>(m);
     if (int e = set_smem(k_up<T, RP>, sm, &done)) return e;
-    dim3 grid((unsigned)(t.lvl_off[m + 1] - t.lvl_off[m]), (unsigned)B);
-    k_up<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m);
+    if (nreg < 0) nreg = (int)(t.lvl_off[m + 1] - t.lvl_off[m]);
+    dim3 grid((unsigned)nreg, (unsigned)B);
+    k_up<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, reg0);
     return (int)cudaGetLastError();
 }
 
@@ -153,8 +155,8 @@ int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream)
     template size_t smem_big<T, RP>(int);                                                                   \
     template int launch_big<T, RP>(const DevTree &, const Work<T> &, int, const BigLeaf *, const BigTile *, \
                                    int, int, int, void *);                                                  \
-    template int launch_leafgram<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                \
-    template int launch_up<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                      \
+    template int launch_leafgram<T, RP>(const DevTree &, const Work<T> &, int, int, int, void *);           \
+    template int launch_up<T, RP>(const DevTree &, const Work<T> &, int, int, int, int, void *);            \
     template int launch_root_single<T, RP>(const DevTree &, const Work<T> &, int, void *);
 
 } // namespace mra

@@ -155,3 +155,34 @@ def test_mixed_is_not_the_fp64_path():
         g.set_precision("mixed")
         b = g.loglik(d["theta"])
     assert a[0] != b[0] and abs(a[0] - b[0]) / 4096 <= TOLMIX
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_streamed_level_gram_matches_whole_level(precision):
+    # a budget of one byte forces the level M-1 Gram blocks to be produced and
+    # consumed one region at a time; the result must not change at all
+    x, y, z = synth.uniform(3000, 21)
+    ref, st = oracle.loglik(x, y, z, 4, 4, 16, THETAS)
+    assert st == 0
+    with mra.MRA(x, y, z, 4, 4, 16, precision=precision) as g, \
+            mra.MRA(x, y, z, 4, 4, 16, precision=precision, hbm_budget=1) as gs:
+        a = g.loglik(THETAS)
+        b = gs.loglik(THETAS)
+        n = g.stats()["n_used"]
+    assert np.array_equal(a, b)
+    assert np.all(np.abs(b - ref) / n <= (TOL64 if precision == "fp64" else TOLMIX))
+
+
+def test_precision_switch_resizes_scratch():
+    x, y, z = synth.uniform(2000, 22)
+    ref, _ = oracle.loglik(x, y, z, 3, 4, 16, THETAS)
+    with mra.MRA(x, y, z, 3, 4, 16, precision="mixed") as g:
+        n = g.stats()["n_used"]
+        m1 = g.loglik(THETAS)
+        g.set_precision("fp64")
+        d1 = g.loglik(THETAS)
+        g.set_precision("mixed")
+        m2 = g.loglik(THETAS)
+    assert np.array_equal(m1, m2)
+    assert np.all(np.abs(d1 - ref) / n <= TOL64)
+    assert np.all(np.abs(m1 - ref) / n <= TOLMIX)
