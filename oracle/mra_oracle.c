@@ -557,6 +557,30 @@ static int ovisit(const octx *c, int m, int64_t i, onode *const *path, double *A
     int M = t->M, R = t->rhat, J = t->J;
     if (m == M) return oleaf(c, i, path, At, wt, d, u);
 
+    /* A subtree with no observation has A = 0 and w = 0, so T = W^m_R and
+     * every term of the step is exactly zero (Sec. 1.2 eliminations can empty
+     * whole regions): return zeros without forming its prior.  In the region
+     * terms its regions read d = u = 0 and log|W^m| = NaN (not formed). */
+    {
+        int64_t l0 = i, l1 = i + 1;
+        for (int l = m; l < M; l++) { l0 *= J; l1 *= J; }
+        if (t->leaf_off[l1] == t->leaf_off[l0]) {
+            int E0 = (m - 1) * R;
+            memset(At, 0, sizeof(double) * (size_t)E0 * E0);
+            memset(wt, 0, sizeof(double) * (size_t)E0);
+            *d = 0.0;
+            *u = 0.0;
+            if (c->rd) {
+                int64_t a = i, b = i + 1;
+                for (int l = m; l <= M; l++) {
+                    for (int64_t q = a; q < b; q++) { c->rd[t->lvl_off[l] + q] = 0.0; c->ru[t->lvl_off[l] + q] = 0.0; }
+                    a *= J; b *= J;
+                }
+            }
+            return O_OK;
+        }
+    }
+
     int64_t g = t->lvl_off[m] + i;
     onode self;
     self.m = m; self.g = g;
