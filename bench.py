@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the cpu_baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--workload", default="grid", choices=["grid", "clustered", "massive"],
+                   help="grid: n=131,072, 1 theta per call (default); clustered: n=2,097,152 with 64 theta per "
+                        "call; massive: n=47,185,920, 1 theta per call")
     return p.parse_args()
 
 
@@ -63,16 +66,40 @@ def dist_env():
     return rank, world, local
 
 
-def workload():
+WORKLOAD_INFO = {
+    "grid": dict(desc="grid n=131072 M=7 J=4 r=32 (r_hat=30), 1 theta per call", per_call=1, data=DATA),
+    "clustered": dict(desc="clustered n=2097152 M=9 J=4 r=32 (r_hat=30), 64 theta per call (4x4x4 log grid)",
+                      per_call=64,
+                      data="synthetic: 70% of n=2097152 in 8 Gaussian clusters (sd 0.03), 30% uniform; z from an "
+                           "exponential GP (sigma2=1, beta=0.05, tau2=0.01) by circulant embedding, seed 1908"),
+    "massive": dict(desc="massive n=47185920 M=12 J=4 r=16, 1 theta per call", per_call=1,
+                    data="synthetic: n=47185920 uniform on [0,1]^2 minus 200 discs (5% of the area); z from an "
+                         "exponential GP (sigma2=1, beta=0.02, tau2=0.01) by circulant embedding, seed 1911"),
+}
+
+
+def workload(name="grid"):
     from paper_1905_00141_gb300 import synth
-    d = synth.grid()
-    return d
+    return synth.make(name)
 
 
-def config(precision):
-    return {"workload": "grid n=131072 M=7 J=4 r=32 (r_hat=30), 1 theta per call", "n": 131072, "M": 7, "J": 4,
-            "r": 32, "r_hat": 30, "theta_per_call": 1, "precision": precision,
-            "l2": "flushed between steps (256 MB write, outside the timed events)"}
+def step_thetas(name):
+    """theta of each timed call, [calls][per_call][3]"""
+    if name == "clustered":
+        from paper_1905_00141_gb300 import synth
+        return synth.theta_grid_4x4x4()[None, :, :]
+    if name == "massive":
+        return np.array([[1.0, 0.02, 0.01], [1.2, 0.025, 0.012], [0.8, 0.016, 0.008], [1.1, 0.022, 0.009]])[:, None]
+    return THETAS[:, None, :]
+
+
+def config(precision, name="grid", d=None):
+    info = WORKLOAD_INFO[name]
+    c = {"workload": info["desc"], "n": int(len(d["x"])) if d is not None else None,
+         "M": d["M"] if d is not None else None, "J": 4, "r": d["r"] if d is not None else None,
+         "theta_per_call": info["per_call"], "precision": precision,
+         "l2": "flushed between steps (256 MB write, outside the timed events)"}
+    return c
 
 
 # ------------------------------------------------------------------ clocks --
@@ -152,13 +179,14 @@ def clocks_rejected(c):
 
 
 # ---------------------------------------------------------------- oracle arm --
-def oracle_rate(d, seconds, max_evals=30, min_evals=1):
+def oracle_rate(d, seconds, max_evals=30, min_evals=1, name="grid", warm=True):
     """Time the FP64 CPU oracle, as it stands, on full evaluations of the workload."""
     import oracle
     oracle.build()
     t = oracle.Tree(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"])
     cores = oracle.max_threads()
-    t.loglik(THETAS[0])  # warm caches / threads
+    if warm:
+        t.loglik(THETAS[0])  # warm caches / threads
     done = 0
     t0 = time.perf_counter()
     while done < min_evals or (time.perf_counter() - t0 < seconds and done < max_evals):
@@ -168,67 +196,73 @@ def oracle_rate(d, seconds, max_evals=30, min_evals=1):
     n = t.n_used
     t.close()
     return dict(value=n * done / dt, unit=UNIT, cores=cores, kind="oracle",
-                sample="%d full evaluations of the grid workload (n=%d) on %d host threads, %.1f s" %
-                (done, n, cores, dt), seconds=dt, evals=done)
+                sample="%d full evaluations of the %s workload (n=%d) on %d host threads, %.1f s" %
+                (done, name, n, cores, dt), seconds=dt, evals=done)
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    d = workload()
+    if args.workload == "massive":
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 CPU oracle is not run on the 47M-observation "
+                          "tree (about 5 TFLOP and tens of GB of host memory per evaluation)"}), flush=True)
+        return 0
+    d = workload(args.workload)
+    thetas = step_thetas(args.workload).reshape(-1, 3)
     import oracle
     oracle.build()
     t = oracle.Tree(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"])
-    for k in range(args.warmup):
-        t.loglik(THETAS[k % len(THETAS)])
+    for k in range(args.warmup if args.workload == "grid" else 0):
+        t.loglik(thetas[k % len(thetas)])
     t0 = time.perf_counter()
     for k in range(args.steps):
-        t.loglik(THETAS[k % len(THETAS)])
+        t.loglik(thetas[k % len(thetas)])
     dt = time.perf_counter() - t0
     n = t.n_used
     cores = oracle.max_threads()
     value = n * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA,
-            "config": config("fp64"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": WORKLOAD_INFO[args.workload]["data"], "config": config("fp64", args.workload, d),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d full evaluations of the grid workload on %d host threads" %
-                             (args.steps, cores)},
+                             "sample": "%d full evaluations (one theta each) of the %s workload on %d host threads" %
+                             (args.steps, args.workload, cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # --------------------------------------------------------------- GPU arm --
-def timed_steps(g, torch, th_dev, out_dev, flush, stream, K, n):
-    """K device-resident steps, each bracketed by CUDA events on `stream`."""
+def timed_steps(g, torch, th_dev, out_dev, flush, stream, K):
+    """K device-resident calls, each bracketed by CUDA events on `stream`;
+    th_dev[c] holds the theta of call c (cycled), out_dev[c] its loglik."""
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    C = th_dev.shape[0]
     with torch.cuda.stream(stream):
         for k in range(K):
             flush.zero_()
             ev[k][0].record(stream)
-            g.loglik_device(th_dev[k % len(THETAS)].data_ptr(), 1, out_dev[k % len(THETAS)].data_ptr(), 0,
+            g.loglik_device(th_dev[k % C].data_ptr(), th_dev.shape[1], out_dev[k % C].data_ptr(), 0,
                             stream.cuda_stream)
             ev[k][1].record(stream)
     stream.synchronize()
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def measure_precision(g, torch, precision, args, d, stream, flush, local):
+def measure_precision(g, torch, precision, args, thetas, stream, flush, local):
     g.set_precision(precision)
-    th_dev = torch.tensor(THETAS, dtype=torch.float64, device="cuda")
-    out_dev = torch.zeros(len(THETAS), dtype=torch.float64, device="cuda")
-    th_rows = [th_dev[i:i + 1] for i in range(len(THETAS))]
+    th_dev = torch.tensor(thetas, dtype=torch.float64, device="cuda").contiguous()
+    out_dev = torch.zeros(thetas.shape[:2], dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
-        timed_steps(g, torch, th_rows, out_dev, flush, stream, len(THETAS), 0)
+        timed_steps(g, torch, th_dev, out_dev, flush, stream, thetas.shape[0])
     g.profile(True)
     g.profile_read()
     sampler = ClockSampler(local)
     if not args.no_clocks:
         sampler.start()
-    ms = timed_steps(g, torch, th_rows, out_dev, flush, stream, args.steps, 0)
+    ms = timed_steps(g, torch, th_dev, out_dev, flush, stream, args.steps)
     clocks = sampler.stop() if not args.no_clocks else None
     prof = g.profile_read()
     g.profile(False)
@@ -249,70 +283,90 @@ def run_ours(args):
         mbuild.build()
     if world > 1:
         dist.barrier()
-    d = workload()
+    name = args.workload
+    d = workload(name)
+    thetas = step_thetas(name)
+    per_call = thetas.shape[1]
     g = mra.MRA(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], device=local, precision=args.precision)
     st = g.stats()
     n = st["n_used"]
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def one_measure(prec):
+    def one_measure(prec, a):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        ms, clocks, prof, ll = measure_precision(g, torch, prec, args, d, stream, flush, local)
+        ms, clocks, prof, ll = measure_precision(g, torch, prec, a, thetas, stream, flush, local)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         return ms, clocks, prof, ll
 
-    ms, clocks, prof, ll = one_measure(args.precision)
+    ms, clocks, prof, ll = one_measure(args.precision, args)
     if clocks_rejected(clocks):
-        ms, clocks, prof, ll = one_measure(args.precision)
+        ms, clocks, prof, ll = one_measure(args.precision, args)
     t_total = sum(ms) / 1e3
     if world > 1:
         tt = torch.tensor([t_total], dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt[0])
-    value = world * n * args.steps / t_total
+    value = world * n * per_call * args.steps / t_total
 
-    # the other precision on the same steps, for the mixed-vs-FP64 comparison
+    # the other precision on the same theta, for the mixed-vs-FP64 comparison
     other = "fp64" if args.precision == "mixed" else "mixed"
-    ms_o, _, prof_o, ll_o = one_measure(other)
-    g.set_precision(args.precision)
+    other_line, ll_o = None, None
+    if name != "massive":
+        oargs = argparse.Namespace(**vars(args))
+        if name != "grid":
+            oargs.steps, oargs.warmup = min(args.steps, 2), 1
+        ms_o, _, prof_o, ll_o = one_measure(other, oargs)
+        other_line = {"precision": other, "value": world * n * per_call * oargs.steps / (sum(ms_o) / 1e3),
+                      "ms_per_step": sum(ms_o) / oargs.steps, "steps": oargs.steps}
+        g.set_precision(args.precision)
 
     # end to end: host theta (pinned) in, host loglik out, through mra_loglik
-    th_host = torch.tensor(THETAS, dtype=torch.float64).pin_memory().numpy()
+    th_host = torch.tensor(thetas, dtype=torch.float64).pin_memory().numpy()
+    C = th_host.shape[0]
     for k in range(args.warmup):
-        g.loglik(th_host[k % len(THETAS)])
+        g.loglik(th_host[k % C])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        g.loglik(th_host[k % len(THETAS)])
+        g.loglik(th_host[k % C])
     e2e_dt = time.perf_counter() - t0
-    e2e_value = world * n * args.steps / e2e_dt if world == 1 else None
+    e2e_value = world * n * per_call * args.steps / e2e_dt if world == 1 else None
     if world > 1:
         tt = torch.tensor([e2e_dt], dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_value = world * n * args.steps / float(tt[0])
+        e2e_value = world * n * per_call * args.steps / float(tt[0])
 
     if rank != 0:
         if world > 1:
             dist.barrier()
         return 0
 
-    # accuracy of both precisions against the FP64 oracle at the step thetas
+    # accuracy: against the FP64 oracle (grid), against the FP64 GPU path
+    # (clustered); not measured at the 47M size (sampled leaves are in the tests)
     import oracle
     oracle.build()
-    ot = oracle.Tree(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"])
-    ref, _ = ot.loglik(THETAS)
-    ot.close()
-    acc = {args.precision: float(np.max(np.abs(ll - ref)) / n), other: float(np.max(np.abs(ll_o - ref)) / n)}
+    if name == "grid":
+        ot = oracle.Tree(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"])
+        ref, _ = ot.loglik(thetas.reshape(-1, 3))
+        ot.close()
+        ref = ref.reshape(thetas.shape[:2])
+        acc = {"against": "FP64 CPU oracle", args.precision: float(np.max(np.abs(ll - ref)) / n),
+               other: float(np.max(np.abs(ll_o - ref)) / n)}
+    elif ll_o is not None:
+        acc = {"against": "FP64 GPU path", args.precision: float(np.max(np.abs(ll - ll_o)) / n)}
+    else:
+        acc = {"against": None, "note": "FP64 does not fit one theta of this tree; sampled leaves against the "
+                                        "oracle in tests/test_zx_massive_gpu.py"}
 
     # roofline of the dominant kernel family
     fam = max(prof, key=lambda k: prof[k][1])
     launches, fam_ms = prof[fam]
-    fl_per_launch = st["flops_by_kernel"][fam] * args.steps / launches
+    fl_per_launch = st["flops_by_kernel"][fam] * per_call * args.steps / launches
     achieved = fl_per_launch / (fam_ms / launches / 1e3) / 1e12
     if args.precision == "mixed":
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -321,30 +375,38 @@ def run_ours(args):
         peak = FP64_TFLOPS_NOMINAL
         peak_note = "FP64: nominal 1.25 TFLOP/s (recipe)"
     roof = {"bound": "alu", "kernel": fam, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": measured_traffic(fam, args.precision), "peak_source": peak_note,
-            "launch_ms": fam_ms / launches, "flops_per_launch": fl_per_launch}
+            "frac": achieved / peak,
+            "traffic": measured_traffic(fam, args.precision) if name == "grid" else None,
+            "peak_source": peak_note, "launch_ms": fam_ms / launches, "flops_per_launch": fl_per_launch}
 
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = oracle_rate(d, args.cpu_seconds)
-        cpu.pop("seconds", None)
-        cpu.pop("evals", None)
+        if name == "grid":
+            cpu = oracle_rate(d, args.cpu_seconds)
+        elif name == "clustered":
+            cpu = oracle_rate(d, args.cpu_seconds, max_evals=1, name=name, warm=False)
+        else:
+            cpu = {"value": None, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                   "sample": "not run: about 5 TFLOP per evaluation of the 47M tree"}
+        if cpu:
+            cpu.pop("seconds", None)
+            cpu.pop("evals", None)
 
     step_ms = 1e3 * t_total / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": DATA,
-        "config": config(args.precision),
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": WORKLOAD_INFO[name]["data"], "config": config(args.precision, name, d),
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 12},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * per_call,
+                "d2h_bytes_per_step": 12 * per_call},
         "gpu_launches": int(st["launches_per_pass"]) * args.steps if st["launches_per_pass"] else
         int(sum(v[0] for v in prof.values())),
         "clocks": clocks,
         "accuracy_abs_dl_per_n": acc,
-        "other_precision": {"precision": other, "value": world * n * args.steps / (sum(ms_o) / 1e3),
-                            "ms_per_step": sum(ms_o) / args.steps},
+        "other_precision": other_line,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "flops_per_eval": st["flops_per_theta"],
     }

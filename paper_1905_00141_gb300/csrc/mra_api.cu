@@ -398,7 +398,7 @@ Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
     for (int m = 0; m <= MRA_MAXM; m++) w.prior_lvl[m] = p.prior_lvl[m];
     w.U = takeT8(p.U);
     w.U_stride = p.U;
-    w.leaf_w = takeT8(p.leafw);
+    w.leaf_w = takeD(p.leafw);
     w.leafw_stride = p.leafw;
     w.leaf_du = takeD(p.leafdu);
     w.leafdu_stride = p.leafdu;
@@ -433,7 +433,7 @@ size_t scratch_bytes_for(const Plan &p, const mra_ctx *c, int B)
     auto addD = [&](size_t elems) { s = align256(s + elems * (size_t)B * sizeof(double)); };
     addT(p.prior);
     addT(p.U);
-    addT(p.leafw);
+    addD(p.leafw);
     addD(p.leafdu);
     addD(p.V);
     addT(p.Ain);

@@ -12,7 +12,7 @@
 //              Linv = L^{-1}, L the Cholesky factor of W^m = C_m(Q, Q).
 //   U          [n_used][(M-1) RP] row-major: the whitened leaf basis What^l of
 //              every observation, overwritten in place by Y = L_V^{-1} U.
-//   leaf_w     [n_leaf][(M-1) RP]  w_c = Y_c' y_c of each leaf
+//   leaf_w     [n_leaf][(M-1) RP]  w_c = Y_c' y_c of each leaf (FP64)
 //   leaf_du    [n_leaf][2]         (log|V_c|, y_c'y_c)
 //   Ain        level M-1 regions: A = sum over the leaf children of Y'Y, packed
 //              upper blocks (k <= l, pair index l(l-1)/2 + k-1), each RP x RP
@@ -56,7 +56,7 @@ struct Work {
     size_t prior_lvl[MRA_MAXM + 1]; // element offset of level m inside one theta's prior
     T *U;
     size_t U_stride;
-    T *leaf_w;
+    double *leaf_w; // FP64 in both modes (see gram_vec)
     size_t leafw_stride;
     double *leaf_du; // [nleaf][2]
     size_t leafdu_stride;

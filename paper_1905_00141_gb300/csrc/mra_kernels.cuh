@@ -565,6 +565,8 @@ __device__ void fwd_solve_vec(const F *A, int lda, const F *rs, int n, F *y)
     __syncthreads();
 }
 
+__device__ __forceinline__ ff f_of_ff(ff v) { return v; }
+__device__ __forceinline__ ff f_of_ff(double v) { return ff_from_double(v); }
 __device__ __forceinline__ double f_of_T(double v) { return v; }
 __device__ __forceinline__ ff f_of_T(float v) { return ff{v, 0.f}; }
 
@@ -881,16 +883,25 @@ __host__ __device__ constexpr size_t smem_leafpost_bytes(int M, int nmax)
            (size_t)nmax * nmax * sizeof(T) + 2 * (size_t)nmax * 8 + 80;
 }
 
-// w[col] = sum_a Y[a][col] y[a] for UC columns (exact FP32 products of Y and
-// the leading part of y in the mixed mode).
+// w[col] = sum_a Y[a][col] y[a] for UC columns, in FP64.  Mixed mode: y is a
+// float pair; the products with its leading part are exact and summed as a
+// float pair, those with its trailing part are summed in FP32, so w carries
+// the precision of y (the upward pass cancels sum y'y against quadratic
+// forms in w, which must agree to more than FP32).
 template <typename T, typename F>
-__device__ void gram_vec(const T *Y, int ldy, int UC, const F *y, int n, T *wout)
+__device__ void gram_vec(const T *Y, int ldy, int UC, const F *y, int n, double *wout)
 {
     for (int col = threadIdx.x; col < UC; col += NT) {
         if constexpr (sizeof(T) == 4) {
             FF s{0.f, 0.f};
-            for (int a = 0; a < n; a++) ff_add_prod(s, Y[(size_t)a * ldy + col], (float)f_hi(y[a]));
-            wout[col] = s.hi + s.lo;
+            float sl = 0.f;
+            for (int a = 0; a < n; a++) {
+                const float v = Y[(size_t)a * ldy + col];
+                const ff ya = f_of_ff(y[a]);
+                ff_add_prod(s, v, ya.hi);
+                sl = __fmaf_rn(v, ya.lo, sl);
+            }
+            wout[col] = (double)s.hi + ((double)s.lo + (double)sl);
         } else {
             double s = 0.0;
             for (int a = 0; a < n; a++) s = fma(Y[(size_t)a * ldy + col], (double)f_hi(y[a]), s);
@@ -1201,14 +1212,14 @@ __global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w, int reg0)
         }
     }
     if (blockIdx.y == 0) {
-        const T *lw = w.leaf_w + (size_t)b * w.leafw_stride;
+        const double *lw = w.leaf_w + (size_t)b * w.leafw_stride;
         const double *ldu = w.leaf_du + (size_t)b * w.leafdu_stride;
         double *wo = w.Ain_w + (size_t)b * w.Ainw_stride + (size_t)Pl * UC;
         for (int col = tid; col < UC; col += NT) {
             double s = 0.0;
             for (int j = 0; j < J; j++) {
                 const int64_t c = (int64_t)P * J + j;
-                if (t.leaf_off[c + 1] > t.leaf_off[c]) s += (double)lw[(size_t)c * UC + col];
+                if (t.leaf_off[c + 1] > t.leaf_off[c]) s += lw[(size_t)c * UC + col];
             }
             wo[col] = s;
         }

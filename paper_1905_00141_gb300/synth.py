@@ -22,6 +22,10 @@ Workloads (sizes follow the configurations the library is measured on):
                over the bounding box, nearest-cell value; M=9, J=4, r=32; a
                4x4x4 log-spaced theta grid.  Stand-in for the skewed leaf
                counts of the AMSR data.
+* ``massive``  n=47,185,920 uniform on [0,1]^2 minus 200 random discs (5% of
+               the area); GP by circulant embedding on a 4096^2 grid
+               (sigma2=1, beta=0.02, tau2=0.01); M=12, J=4, r=16.  Stand-in
+               for the large MODIS scene (gaps where clouds mask pixels).
 """
 from __future__ import annotations
 
@@ -33,6 +37,7 @@ WORKLOADS = {
     "small": dict(n=4096, M=3, J=4, r=16, theta=(1.0, 0.1, 0.05)),
     "grid": dict(n=131072, M=7, J=4, r=32, theta=(1.0, 0.05, 0.01)),
     "clustered": dict(n=2097152, M=9, J=4, r=32, theta=(1.0, 0.05, 0.01)),
+    "massive": dict(n=47185920, M=12, J=4, r=16, theta=(1.0, 0.02, 0.01)),
 }
 
 SEED_BASE = 1905
@@ -153,6 +158,41 @@ def clustered(seed: int = SEED_BASE + 3, n: int = 2097152, grid_n: int = 1024):
     return dict(x=x, y=y, z=z, M=9, J=4, r=32, theta=theta_grid_4x4x4())
 
 
+def massive(seed: int = SEED_BASE + 6, n: int = 47185920, grid_n: int = 4096, n_discs: int = 200,
+            gap_fraction: float = 0.05):
+    """n points uniform on [0,1]^2 minus n_discs random discs (gaps) whose
+    radius is set so their areas add up to gap_fraction of the square (an
+    oversample is drawn and trimmed to n); z from an exponential GP
+    (sigma2=1, beta=0.02, tau2=0.01) by circulant embedding on a grid_n^2
+    grid, nearest-cell value plus the nugget; M=12, J=4, r=16."""
+    rng = np.random.default_rng(seed)
+    rad = math.sqrt(gap_fraction / (n_discs * math.pi))
+    centres = rng.random((n_discs, 2))
+    m = int(n / (1.0 - gap_fraction) * 1.03) + 1024
+    x = rng.random(m)
+    y = rng.random(m)
+    order = np.argsort(x, kind="stable")
+    x, y = x[order], y[order]
+    keep = np.ones(m, dtype=bool)
+    for cx, cy in centres:
+        a, b = np.searchsorted(x, [cx - rad, cx + rad])
+        keep[a:b] &= (x[a:b] - cx) ** 2 + (y[a:b] - cy) ** 2 > rad * rad
+    idx = np.flatnonzero(keep)
+    if len(idx) < n:
+        raise ValueError("oversample too small")
+    idx = np.sort(rng.permutation(idx)[:n])
+    x, y = x[idx], y[idx]
+    perm = rng.permutation(n)
+    x, y = x[perm], y[perm]
+    s2, b, t2 = WORKLOADS["massive"]["theta"]
+    h = 1.0 / (grid_n - 1)
+    field = gp_grid(grid_n, grid_n, h, h, s2, b, rng)
+    ix = np.clip(np.rint(x / h).astype(np.int64), 0, grid_n - 1)
+    iy = np.clip(np.rint(y / h).astype(np.int64), 0, grid_n - 1)
+    z = field[ix, iy] + math.sqrt(t2) * rng.standard_normal(n)
+    return dict(x=x, y=y, z=z, M=12, J=4, r=16, theta=np.array([[s2, b, t2]]))
+
+
 def uniform(n: int, seed: int, sigma2=1.0, beta=0.1, tau2=0.05, exact=True):
     """Small uniform draw for tests (exact GP values when exact=True)."""
     rng = np.random.default_rng(seed)
@@ -166,4 +206,4 @@ def uniform(n: int, seed: int, sigma2=1.0, beta=0.1, tau2=0.05, exact=True):
 
 
 def make(name: str, **kw):
-    return {"small": small, "grid": grid, "clustered": clustered}[name](**kw)
+    return {"small": small, "grid": grid, "clustered": clustered, "massive": massive}[name](**kw)
