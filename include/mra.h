@@ -57,6 +57,9 @@ typedef struct {
                           (stats and tree queries work, likelihood calls give MRA_EINVAL) */
     int max_batch;     /* theta evaluated per device pass; 0 = choose from hbm_budget */
     size_t hbm_budget; /* bytes of per-theta scratch the context may hold; 0 = 60% of free HBM */
+    int graphs;        /* 1 (default): a device pass seen before is replayed from a captured CUDA graph
+                          (keyed by its theta/loglik/status pointers, batch and precision; recaptured
+                          when the scratch moves); 0: every kernel is launched on each call */
 } mra_opts;
 
 typedef struct {

@@ -280,6 +280,20 @@ struct mra_ctx {
     size_t hbm_budget = 0;   // from the options (0 = 60% of free HBM)
     int ain_chunk = 0;       // level M-1 regions per Ain chunk (0 = the whole level)
     int status_cap = 0;      // theta the status array holds
+    // captured device passes, replayed when the same pass comes again
+    struct GraphEntry {
+        const double *theta;
+        double *loglik;
+        int *status;
+        int B, precision, regions;
+        uint64_t gen, last_use;
+        cudaGraphExec_t exec;
+    };
+    bool graphs = true;
+    uint64_t scratch_gen = 0, use_clock = 0;
+    std::vector<GraphEntry> graph_cache;
+    std::vector<GraphEntry> graph_seen; // passes run once, captured on their next call
+    cudaStream_t cap_stream = nullptr;
     unsigned char *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     size_t per_theta_bytes = 0;
@@ -676,6 +690,7 @@ mra_status ensure_capacity(mra_ctx *c, int B)
     c->bytes_held += bytes;
     c->cap = B;
     c->status_cap = B;
+    c->scratch_gen++;
     return MRA_OK;
 }
 
@@ -713,6 +728,110 @@ int max_batch_for(mra_ctx *c, size_t budget)
     return (int)b;
 }
 
+// One device pass of B theta (theta_dev, loglik_dev, status_dev already
+// offset to the pass) on stream s: clear the status, run the kernels, copy the
+// status out.
+mra_status pass_ops(mra_ctx *c, const double *theta_dev, int B, double *loglik_dev, int *status_dev, cudaStream_t s,
+                    bool with_regions)
+{
+    Plan p = make_plan(c);
+    cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int) * (size_t)B, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+    int rc;
+    if (c->precision == MRA_MIXED) {
+        Work<float> w = make_work<float>(c, p, B);
+        w.theta = theta_dev;
+        w.loglik = loglik_dev;
+        if (with_regions) {
+            w.reg_du = c->d_reg_du;
+            w.reg_lw = c->d_reg_lw;
+        }
+        rc = dispatch_rp<float>(c, w, B, s);
+    } else {
+        Work<double> w = make_work<double>(c, p, B);
+        w.theta = theta_dev;
+        w.loglik = loglik_dev;
+        if (with_regions) {
+            w.reg_du = c->d_reg_du;
+            w.reg_lw = c->d_reg_lw;
+        }
+        rc = dispatch_rp<double>(c, w, B, s);
+    }
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+    if (status_dev) {
+        e = cudaMemcpyAsync(status_dev, c->d_status, sizeof(int) * (size_t)B, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
+    }
+    return MRA_OK;
+}
+
+void drop_graphs(mra_ctx *c)
+{
+    for (auto &g : c->graph_cache) cudaGraphExecDestroy(g.exec);
+    c->graph_cache.clear();
+    c->graph_seen.clear();
+}
+
+// Replay a captured pass, or capture it when it comes for the second time (the
+// first run also sets the kernels' shared-memory limits, which are not stream
+// work); a pass seen for the first time runs without a graph.
+mra_status graph_pass(mra_ctx *c, const double *theta_dev, int B, double *loglik_dev, int *status_dev,
+                      cudaStream_t s, bool with_regions)
+{
+    const int regions = with_regions ? 1 : 0;
+    auto same = [&](const mra_ctx::GraphEntry &g) {
+        return g.theta == theta_dev && g.loglik == loglik_dev && g.status == status_dev && g.B == B &&
+               g.precision == c->precision && g.regions == regions && g.gen == c->scratch_gen;
+    };
+    c->use_clock++;
+    for (auto &g : c->graph_cache)
+        if (same(g)) {
+            g.last_use = c->use_clock;
+            cudaError_t e = cudaGraphLaunch(g.exec, s);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+            return MRA_OK;
+        }
+    bool seen = false;
+    for (auto &g : c->graph_seen)
+        if (same(g)) seen = true;
+    if (!seen) {
+        if (c->graph_seen.size() >= 64) c->graph_seen.erase(c->graph_seen.begin());
+        c->graph_seen.push_back(mra_ctx::GraphEntry{theta_dev, loglik_dev, status_dev, B, c->precision, regions,
+                                                    c->scratch_gen, 0, nullptr});
+        return pass_ops(c, theta_dev, B, loglik_dev, status_dev, s, with_regions);
+    }
+    if (!c->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamCreate");
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+    mra_status st = pass_ops(c, theta_dev, B, loglik_dev, status_dev, c->cap_stream, with_regions);
+    e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (st != MRA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    if (c->graph_cache.size() >= 16) {
+        size_t old = 0;
+        for (size_t k = 1; k < c->graph_cache.size(); k++)
+            if (c->graph_cache[k].last_use < c->graph_cache[old].last_use) old = k;
+        cudaGraphExecDestroy(c->graph_cache[old].exec);
+        c->graph_cache.erase(c->graph_cache.begin() + (long)old);
+    }
+    c->graph_cache.push_back(mra_ctx::GraphEntry{theta_dev, loglik_dev, status_dev, B, c->precision, regions,
+                                                 c->scratch_gen, c->use_clock, exec});
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+    return MRA_OK;
+}
+
 mra_status enqueue(mra_ctx *c, const double *theta_dev, int batch, double *loglik_dev, int *status_dev,
                    cudaStream_t s, bool with_regions)
 {
@@ -720,34 +839,12 @@ mra_status enqueue(mra_ctx *c, const double *theta_dev, int batch, double *logli
     while (done < batch) {
         const int B = std::min(batch - done, std::max(c->max_cap, 1));
         if (mra_status st = ensure_capacity(c, B)) return st;
-        Plan p = make_plan(c);
-        cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int) * (size_t)B, s);
-        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
-        int rc;
-        if (c->precision == MRA_MIXED) {
-            Work<float> w = make_work<float>(c, p, B);
-            w.theta = theta_dev + 3 * (size_t)done;
-            w.loglik = loglik_dev + done;
-            if (with_regions) {
-                w.reg_du = c->d_reg_du;
-                w.reg_lw = c->d_reg_lw;
-            }
-            rc = dispatch_rp<float>(c, w, B, s);
-        } else {
-            Work<double> w = make_work<double>(c, p, B);
-            w.theta = theta_dev + 3 * (size_t)done;
-            w.loglik = loglik_dev + done;
-            if (with_regions) {
-                w.reg_du = c->d_reg_du;
-                w.reg_lw = c->d_reg_lw;
-            }
-            rc = dispatch_rp<double>(c, w, B, s);
-        }
-        if (rc) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
-        if (status_dev) {
-            e = cudaMemcpyAsync(status_dev + done, c->d_status, sizeof(int) * (size_t)B, cudaMemcpyDeviceToDevice, s);
-            if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
-        }
+        const double *th = theta_dev + 3 * (size_t)done;
+        double *ll = loglik_dev + done;
+        int *sd = status_dev ? status_dev + done : nullptr;
+        mra_status st = (c->graphs && !c->prof_on && !with_regions) ? graph_pass(c, th, B, ll, sd, s, false)
+                                                                    : pass_ops(c, th, B, ll, sd, s, with_regions);
+        if (st != MRA_OK) return st;
         done += B;
     }
     return MRA_OK;
@@ -793,6 +890,7 @@ void mra_default_opts(mra_opts *opt)
     opt->device = 0;
     opt->max_batch = 0;
     opt->hbm_budget = 0;
+    opt->graphs = 1;
 }
 
 
@@ -966,6 +1064,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     c->nbig = (int)big.size();
     count_work(c);
     c->hbm_budget = opt.hbm_budget;
+    c->graphs = opt.graphs != 0;
     c->user_max_batch = opt.max_batch;
     const int mb = max_batch_for(c, opt.hbm_budget);
     c->max_cap = opt.max_batch > 0 ? std::min(opt.max_batch, 1024) : mb;
@@ -1183,6 +1282,8 @@ void mra_free(mra_ctx *c)
 {
     if (!c) return;
     if (c->device >= 0 && c->d_sx) cudaSetDevice(c->device);
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
                     c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
                     c->d_reg_du, c->d_reg_lw};

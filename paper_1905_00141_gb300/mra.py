@@ -40,7 +40,8 @@ class MRAError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("offset", ctypes.c_double), ("dedup", ctypes.c_int), ("precision", ctypes.c_int),
-                ("device", ctypes.c_int), ("max_batch", ctypes.c_int), ("hbm_budget", ctypes.c_size_t)]
+                ("device", ctypes.c_int), ("max_batch", ctypes.c_int), ("hbm_budget", ctypes.c_size_t),
+                ("graphs", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -123,7 +124,7 @@ class MRA:
     """
 
     def __init__(self, x, y, z, M, J, r, offset=None, dedup=False, precision="fp64", device=0,
-                 max_batch=0, hbm_budget=0):
+                 max_batch=0, hbm_budget=0, graphs=True):
         L = lib()
         self._x = np.ascontiguousarray(x, dtype=np.float64)
         self._y = np.ascontiguousarray(y, dtype=np.float64)
@@ -136,6 +137,7 @@ class MRA:
         o.device = int(device)
         o.max_batch = int(max_batch)
         o.hbm_budget = int(hbm_budget)
+        o.graphs = int(bool(graphs))
         h = ctypes.c_void_p(0)
         st = L.mra_build(_dp(self._x), _dp(self._y), _dp(self._z), len(self._x), int(M), int(J), int(r),
                          ctypes.byref(o), ctypes.byref(h))

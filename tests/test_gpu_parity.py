@@ -186,3 +186,26 @@ def test_precision_switch_resizes_scratch():
     assert np.array_equal(m1, m2)
     assert np.all(np.abs(d1 - ref) / n <= TOL64)
     assert np.all(np.abs(m1 - ref) / n <= TOLMIX)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_equals_direct_launches(precision):
+    torch = pytest.importorskip("torch")
+    x, y, z = synth.uniform(5000, 23)
+    x = np.concatenate([x, 0.3 + 0.005 * np.random.default_rng(1).standard_normal(300)])
+    y = np.concatenate([y, 0.7 + 0.005 * np.random.default_rng(2).standard_normal(300)])
+    z = np.concatenate([z, np.random.default_rng(3).standard_normal(300)])  # a few large leaves too
+    with mra.MRA(x, y, z, 4, 4, 16, precision=precision, graphs=False) as g0, \
+            mra.MRA(x, y, z, 4, 4, 16, precision=precision) as g1:
+        assert g0.stats()["max_leaf"] > 64
+        ref = g0.loglik(THETAS)
+        for _ in range(4):  # first run direct, second captured, then replayed
+            assert np.array_equal(g1.loglik(THETAS), ref)
+        # device entry point with alternating buffers
+        th = [torch.tensor(THETAS[k:k + 1], dtype=torch.float64, device="cuda") for k in range(3)]
+        out = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in range(3)]
+        for _ in range(3):
+            for k in range(3):
+                g1.loglik_device(th[k].data_ptr(), 1, out[k].data_ptr(), 0, 0)
+        torch.cuda.synchronize()
+        assert np.array_equal(np.array([o.item() for o in out]), ref)
