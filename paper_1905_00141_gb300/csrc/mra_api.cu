@@ -258,7 +258,7 @@ struct mra_ctx {
     double *d_kx = nullptr, *d_ky = nullptr, *d_sx = nullptr, *d_sy = nullptr, *d_sz = nullptr;
     double *d_cx = nullptr, *d_cy = nullptr;
     int64_t *d_leaf_off = nullptr;
-    Chunk *d_chunks32 = nullptr, *d_chunks64 = nullptr; // leaf-basis chunks of 32 (FP64) / 64 (FP32) rows
+    Chunk *d_chunks32 = nullptr, *d_chunks64 = nullptr; // leaf-basis chunks of 32 / 64 rows
     int nchunks32 = 0, nchunks64 = 0;
     // leaves with 1..kLeafCap[k] observations (and more than the previous cap),
     // one CTA each; larger leaves take the global-memory path
@@ -520,8 +520,8 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     c->launches_last = 0;
     for (int m = 1; m < M; m++)
         if ((e = timed_launch(c, K_PRIOR, s, [&] { return launch_prior<T, RP>(t, w, m, B, s); }))) return e;
-    const Chunk *chunks = sizeof(T) == 4 ? c->d_chunks64 : c->d_chunks32;
-    const int nchunks = sizeof(T) == 4 ? c->nchunks64 : c->nchunks32;
+    const Chunk *chunks = chunk_rows<T>() == 64 ? c->d_chunks64 : c->d_chunks32;
+    const int nchunks = chunk_rows<T>() == 64 ? c->nchunks64 : c->nchunks32;
     if (M > 1 && nchunks > 0)
         if ((e = timed_launch(c, K_LEAFBASIS, s,
                               [&] { return launch_leafbasis<T, RP>(t, w, chunks, nchunks, B, s); })))
