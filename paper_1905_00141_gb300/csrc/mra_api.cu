@@ -294,6 +294,11 @@ struct mra_ctx {
     std::vector<GraphEntry> graph_cache;
     std::vector<GraphEntry> graph_seen; // passes run once, captured on their next call
     cudaStream_t cap_stream = nullptr;
+    // independent leaf-posterior launches (size buckets, the large-leaf
+    // pipeline) run side by side on these streams, forked from and joined to
+    // the pass's stream by events
+    cudaStream_t aux[kLeafBuckets] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr, join_ev[kLeafBuckets] = {nullptr, nullptr, nullptr};
     unsigned char *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     size_t per_theta_bytes = 0;
@@ -526,12 +531,39 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
         if ((e = timed_launch(c, K_LEAFBASIS, s,
                               [&] { return launch_leafbasis<T, RP>(t, w, chunks, nchunks, B, s); })))
             return e;
-    for (int k = 0; k < kLeafBuckets; k++)
-        if (c->nl[k] > 0)
-            if ((e = timed_launch(c, K_LEAFPOST, s, [&] {
-                     return launch_leafpost_small<T, RP>(t, w, c->d_leaves[k], c->nl[k], kLeafCap[k], B, s);
+    // leaf posterior: the size buckets and the large-leaf pipeline touch
+    // disjoint leaves, so they run concurrently: the large leaves (or the first
+    // bucket) on s, every other bucket on a side stream forked from s
+    int naux = 0;
+    {
+        int jobs = c->nbig > 0 ? 1 : 0;
+        for (int k = 0; k < kLeafBuckets; k++) jobs += c->nl[k] > 0;
+        const bool fork = jobs > 1;
+        if (fork) {
+            if (!c->fork_ev && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+                return (int)cudaErrorLaunchFailure;
+            cudaEventRecord(c->fork_ev, s);
+        }
+        bool s_taken = c->nbig > 0;
+        for (int k = 0; k < kLeafBuckets; k++) {
+            if (c->nl[k] == 0) continue;
+            cudaStream_t q = s;
+            if (fork && s_taken) {
+                const int a = naux++;
+                if (!c->aux[a] && cudaStreamCreateWithFlags(&c->aux[a], cudaStreamNonBlocking) != cudaSuccess)
+                    return (int)cudaErrorLaunchFailure;
+                if (!c->join_ev[a] && cudaEventCreateWithFlags(&c->join_ev[a], cudaEventDisableTiming) != cudaSuccess)
+                    return (int)cudaErrorLaunchFailure;
+                q = c->aux[a];
+                cudaStreamWaitEvent(q, c->fork_ev, 0);
+            }
+            s_taken = true;
+            if ((e = timed_launch(c, K_LEAFPOST, q, [&] {
+                     return launch_leafpost_small<T, RP>(t, w, c->d_leaves[k], c->nl[k], kLeafCap[k], B, q);
                  })))
                 return e;
+        }
+    }
     if (c->nbig > 0) {
         auto big = [&](int phase, int off, int cnt, int k) {
             return timed_launch(c, K_LEAFPOST_BIG, s, [&] {
@@ -549,6 +581,11 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
                  return launch_big<T, RP>(t, w, BIG_FINISH, c->d_big, nullptr, c->nbig, 0, B, s);
              })))
             return e;
+    }
+    // join the side streams back into s
+    for (int a = 0; a < naux; a++) {
+        cudaEventRecord(c->join_ev[a], c->aux[a]);
+        cudaStreamWaitEvent(s, c->join_ev[a], 0);
     }
     if (M > 1) {
         const int nP = (int)(c->P.lvl_off[(size_t)M] - c->P.lvl_off[(size_t)M - 1]);
@@ -1284,6 +1321,11 @@ void mra_free(mra_ctx *c)
     if (c->device >= 0 && c->d_sx) cudaSetDevice(c->device);
     drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (int k = 0; k < kLeafBuckets; k++) {
+        if (c->aux[k]) cudaStreamDestroy(c->aux[k]);
+        if (c->join_ev[k]) cudaEventDestroy(c->join_ev[k]);
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
                     c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
                     c->d_reg_du, c->d_reg_lw};

@@ -801,10 +801,18 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
 // A chunk of observation rows below one level-(M-1) region: What^l of each
 // row against its M-1 ancestors, written as rows of U.
 template <typename T, int RP>
-__host__ __device__ constexpr size_t smem_leafbasis_bytes(int M)
+__host__ __device__ constexpr size_t smem_leafbasis_bytes(int M, int stages)
 {
     return (size_t)(2 * chunk_rows<T>() + 2 * RP) * sizeof(T) + (size_t)(M - 1) * RP * (chunk_rows<T>() + 2) * sizeof(T) +
-           (size_t)2 * (M - 1) * RP * RP * sizeof(T) + (size_t)RP * (chunk_rows<T>() + 2) * sizeof(T) + 64;
+           (size_t)stages * (M - 1) * RP * RP * sizeof(T) + (size_t)RP * (chunk_rows<T>() + 2) * sizeof(T) + 64;
+}
+
+// Two stages of ancestor blocks (prefetch of the next level) only while two
+// CTAs still fit on an SM; deep trees keep one stage and the occupancy.
+template <typename T, int RP>
+__host__ __device__ constexpr int leafbasis_stages(int M)
+{
+    return smem_leafbasis_bytes<T, RP>(M, 2) <= (size_t)110 * 1024 ? 2 : 1;
 }
 
 template <typename T, int RP>
@@ -823,27 +831,33 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
     T *sp = (T *)smem_raw;                  // 2 CH rows relative to the ancestor corner
     T *sa = sp + 2 * CH;                    // 2 RP
     T *sU = sa + 2 * RP;                     // (M-1) blocks k-major [t][row], stride LDC
-    T *sB0 = sU + (size_t)(M - 1) * RP * LDC; // 2 stages of up to M-1 ancestor blocks
-    T *sW = sB0 + (size_t)2 * (M - 1) * RP * RP; // RP x LDC k-major
+    const int stages = leafbasis_stages<T, RP>(M);
+    T *sB0 = sU + (size_t)(M - 1) * RP * LDC;          // 1 or 2 stages of up to M-1 ancestor blocks
+    T *sW = sB0 + (size_t)stages * (M - 1) * RP * RP; // RP x LDC k-major
     const T *pb = w.prior + (size_t)b * w.prior_stride;
     const int r0 = TL::r0(), c0 = TL::c0();
-    // the ancestor's blocks of level l go to stage l & 1; level l + 1 is fetched
-    // (cp.async) while level l is computed
+    // the ancestor's blocks of level l go to stage l & 1 (two stages: level
+    // l + 1 is fetched with cp.async while level l is computed)
     auto fetch = [&](int l) {
         const int64_t ia = (int64_t)P >> (t.lgJ * (M - 1 - l));
-        copy_g2s_async(sB0 + (size_t)(l & 1) * (M - 1) * RP * RP, pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP,
-                       l * RP * RP);
+        copy_g2s_async(sB0 + (size_t)((l & 1) * (stages - 1)) * (M - 1) * RP * RP,
+                       pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP, l * RP * RP);
         cp_async_commit();
     };
     fetch(1);
     for (int l = 1; l <= M - 1; l++) {
         const int64_t ia = (int64_t)P >> (t.lgJ * (M - 1 - l));
         const int64_t ga = t.lvl_off[l] + ia;
-        T *sB = sB0 + (size_t)(l & 1) * (M - 1) * RP * RP;
-        if (l + 1 <= M - 1) {
-            fetch(l + 1);
-            cp_async_wait<1>();
+        T *sB = sB0 + (size_t)((l & 1) * (stages - 1)) * (M - 1) * RP * RP;
+        if (stages == 2) {
+            if (l + 1 <= M - 1) {
+                fetch(l + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
         } else {
+            if (l > 1) fetch(l); // the single stage is free after the previous level's barrier
             cp_async_wait<0>();
         }
         const double ox = t.cx[ga], oy = t.cy[ga];

@@ -17,7 +17,10 @@ static int set_smem(K kernel, size_t bytes, size_t *done)
 }
 
 template <typename T, int RP> size_t smem_prior(int m) { return smem_prior_bytes<T, RP>(m); }
-template <typename T, int RP> size_t smem_leafbasis(int M) { return smem_leafbasis_bytes<T, RP>(M); }
+template <typename T, int RP> size_t smem_leafbasis(int M)
+{
+    return smem_leafbasis_bytes<T, RP>(M, leafbasis_stages<T, RP>(M));
+}
 template <typename T, int RP> size_t smem_leafpost_small(int M, int nmax) { return smem_leafpost_bytes<T, RP>(M, nmax); }
 template <typename T, int RP> size_t smem_up(int m) { return smem_up_bytes<T, RP>(m); }
 template <typename T, int RP> size_t smem_leafgram(int M) { return smem_leafgram_bytes<T, RP>(M); }
@@ -43,7 +46,7 @@ int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, in
 {
     static size_t done = 0;
     if (nchunks == 0) return 0;
-    const size_t sm = smem_leafbasis_bytes<T, RP>(t.M);
+    const size_t sm = smem_leafbasis_bytes<T, RP>(t.M, leafbasis_stages<T, RP>(t.M));
     if (int e = set_smem(k_leafbasis<T, RP>, sm, &done)) return e;
     dim3 grid((unsigned)nchunks, (unsigned)B);
     k_leafbasis<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, chunks);
