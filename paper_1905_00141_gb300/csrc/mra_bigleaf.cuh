@@ -12,7 +12,9 @@
 //     potrf    tile (k,k) = L_kk L_kk', d += log|L_kk L_kk'|,
 //              y_k = L_kk^{-1} z_k, u += |y_k|^2, Y_k = L_kk^{-1} U_k
 //     trsm     L_ik = V_ik L_kk^{-T} (i > k); z_i -= L_ik y_k;
-//              U_i -= L_ik Y_k
+//              U_i -= L_ik Y_k (the right-hand sides use the leading floats
+//              of L in both modes' storage type, y in float pairs, so y and Y
+//              belong to one operator)
 //     update   V_ij -= L_ik L_jk' (k < j <= i)
 //   finish     w = Y'y; (d, u) and the status to the leaf's outputs
 // One launch covers the tiles of every large leaf that has them at step k
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(NT) k_big_potrf(DevTree t, Work<T> w, const Bi
         if (i >= j) v.V[(size_t)(r0 + j) * n + r0 + i] = sL[j * (TB + 1) + i];
     }
     for (int j = tid; j < nk; j += NT) v.rs[r0 + j] = srs[j];
-    fwd_solve_vec(sL, TB + 1, srs, nk, sy);
+    fwd_solve_vec<F, true>(sL, TB + 1, srs, nk, sy);
     if (tid < 32) {
         F q = tid < nk ? f_sqr(sy[tid]) : f_of<F>(0.0);
         q = warp_sum_f(q);
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(NT) k_big_trsm(DevTree t, Work<T> w, const Big
 #pragma unroll
         for (int q = 0; q < RPW; q++) {
             const int r = warp + (NT / 32) * q;
-            F p = lane < nk && r < ni ? f_mul(sA[r * (TB + 1) + lane], syk[lane]) : f_of<F>(0.0);
+            F p = lane < nk && r < ni ? f_mul(f_lead(sA[r * (TB + 1) + lane]), syk[lane]) : f_of<F>(0.0);
             p = warp_sum_f(p);
             if (lane == 0 && r < ni) v.y[ri + r] = f_sub(k == 0 ? f_of<F>(t.sz[v.o0 + ri + r]) : v.y[ri + r], p);
         }

@@ -541,10 +541,19 @@ __device__ __forceinline__ double logdet_small(const ff *A, int lda, int n, doub
     return v;
 }
 
+// The leading float of a factor entry, as a factor-type value (float pairs:
+// the pair (hi, 0); FP64: the value itself).
+__device__ __forceinline__ ff f_lead(ff a) { return ff{a.hi, 0.f}; }
+__device__ __forceinline__ double f_lead(double a) { return a; }
+
 // y <- L^{-1} y with the chol_small factor (L[a][q] = A[q][a]) and rs = 1/L_jj,
 // by warp 0, right-looking: lane a (and a + 32) owns y[a]; after y[q] is
-// final it is broadcast and every later row subtracts its share.
-template <typename F>
+// final it is broadcast and every later row subtracts its share.  With LEAD,
+// the operator is the leading floats of L and rs (the FP32 factor the solves
+// of the storage-type right-hand sides use), applied in float-pair arithmetic:
+// y then belongs to the same operator as those solves, which keeps the
+// quadratic forms of the upward pass consistent with the Gram blocks.
+template <typename F, bool LEAD = false>
 __device__ void fwd_solve_vec(const F *A, int lda, const F *rs, int n, F *y)
 {
     if (threadIdx.x < 32) {
@@ -553,17 +562,44 @@ __device__ void fwd_solve_vec(const F *A, int lda, const F *rs, int n, F *y)
         F y1 = lane + 32 < n ? y[lane + 32] : f_of<F>(0.0);
         for (int q = 0; q < n; q++) {
             const bool mine0 = (q == lane), mine1 = (q == lane + 32);
-            if (mine0) y0 = f_mul(y0, rs[q]);
-            if (mine1) y1 = f_mul(y1, rs[q]);
+            const F rq = LEAD ? f_lead(rs[q]) : rs[q];
+            if (mine0) y0 = f_mul(y0, rq);
+            if (mine1) y1 = f_mul(y1, rq);
             const F yq = q < 32 ? f_shfl(y0, q) : f_shfl(y1, q - 32);
-            if (lane > q && lane < n) y0 = f_sub(y0, f_mul(A[q * lda + lane], yq));
-            if (lane + 32 > q && lane + 32 < n) y1 = f_sub(y1, f_mul(A[q * lda + lane + 32], yq));
+            if (lane > q && lane < n) {
+                const F l = A[q * lda + lane];
+                y0 = f_sub(y0, f_mul(LEAD ? f_lead(l) : l, yq));
+            }
+            if (lane + 32 > q && lane + 32 < n) {
+                const F l = A[q * lda + lane + 32];
+                y1 = f_sub(y1, f_mul(LEAD ? f_lead(l) : l, yq));
+            }
         }
         if (lane < n) y[lane] = y0;
         if (lane + 32 < n) y[lane + 32] = y1;
     }
     __syncthreads();
 }
+
+// sum_k a_k b_k with a in the storage type and b in the factor type: float x
+// float-pair products exact in their leading part (TwoProd), the trailing
+// part summed in FP32; FP64: plain FMA.
+template <typename T, typename F> struct DotTF;
+template <> struct DotTF<float, ff> {
+    FF s{0.f, 0.f};
+    float side = 0.f;
+    __device__ __forceinline__ void add(float a, ff b)
+    {
+        ff_add_prod(s, a, b.hi);
+        side = __fmaf_rn(a, b.lo, side);
+    }
+    __device__ __forceinline__ ff value() const { return fast_two_sum(s.hi, __fadd_rn(s.lo, side)); }
+};
+template <> struct DotTF<double, double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
 
 __device__ __forceinline__ ff f_of_ff(ff v) { return v; }
 __device__ __forceinline__ ff f_of_ff(double v) { return ff_from_double(v); }
@@ -661,28 +697,6 @@ __device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, i
             const int col = warp + NW * (j0 + cc);
             if (col < ncol && lane < N) X[(size_t)lane * ldx + col] = x[cc];
         }
-    }
-    __syncthreads();
-}
-
-// x <- L^{-T} x with the chol_small factor (L[q][a] = A[a][q]), by warp 0,
-// right-looking from the last row: lane a (and a + 32) owns x[a].
-template <typename F>
-__device__ void bwd_solve_vec(const F *A, int lda, const F *rs, int n, F *xv)
-{
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        F x0 = lane < n ? xv[lane] : f_of<F>(0.0);
-        F x1 = lane + 32 < n ? xv[lane + 32] : f_of<F>(0.0);
-        for (int q = n - 1; q >= 0; q--) {
-            if (q == lane) x0 = f_mul(x0, rs[q]);
-            if (q == lane + 32) x1 = f_mul(x1, rs[q]);
-            const F xq = q < 32 ? f_shfl(x0, q) : f_shfl(x1, q - 32);
-            if (lane < q) x0 = f_sub(x0, f_mul(A[lane * lda + q], xq));
-            if (lane + 32 < q) x1 = f_sub(x1, f_mul(A[(lane + 32) * lda + q], xq));
-        }
-        if (lane < n) xv[lane] = x0;
-        if (lane + 32 < n) xv[lane + 32] = x1;
     }
     __syncthreads();
 }
@@ -1046,17 +1060,30 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
                     for (int cc = 0; cc < TL::CT; cc++) Ub[(size_t)(r0 + r) * UC + cb + c0 + cc] = acc[r][cc];
         }
     }
-    fwd_solve_vec(sV, LDV, srs, n, sy);
+    // y = Linv z, u = y'y and w = Y'y = U' (Linv' y) with the same FP32 Linv
+    // that forms Y = Linv U (exact products, float-pair sums): the leaf's u, w
+    // and Gram blocks then all belong to one operator, so the upward pass
+    // cancels them consistently
+    F *sy2 = sr2; // the Cholesky's scratch is free now
+    for (int r = tid; r < n; r += NT) {
+        DotTF<T, F> acc;
+        for (int k = 0; k <= r; k++) acc.add(sLi[k * nmax + r], sy[k]);
+        sy2[r] = acc.value();
+    }
+    __syncthreads();
     if (tid < 32) {
         F q = f_of<F>(0.0);
-        for (int a = tid; a < n; a += 32) q = f_add(q, f_sqr(sy[a]));
+        for (int a = tid; a < n; a += 32) q = f_add(q, f_sqr(sy2[a]));
         q = warp_sum_f(q);
         if (tid == 0) red[0] = f_dbl(q);
     }
+    for (int k = tid; k < n; k += NT) {
+        DotTF<T, F> acc;
+        for (int r = k; r < n; r++) acc.add(sLi[k * nmax + r], sy2[r]);
+        sy[k] = acc.value();
+    }
     __syncthreads();
     const double uv = red[0];
-    // w_c = Y'y = U' V^{-1} z
-    bwd_solve_vec(sV, LDV, srs, n, sy);
     gram_vec(sU, LDU, UC, sy, n, w.leaf_w + (size_t)b * w.leafw_stride + (size_t)c * UC);
     if (tid == 0) {
         double *du = w.leaf_du + (size_t)b * w.leafdu_stride + 2 * c;
@@ -1369,7 +1396,7 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
     const int ncol = (m - 1) * RP, ldz = ncol + 4;
     for (int a = tid; a < RP; a += NT) sz[a] = f_of<F>(sw[(m - 1) * RP + a]);
     fwd_solve_warp<T, RP>(sL, RP + 1, srs, sC, RP, 1, sZ, ldz, ncol);
-    fwd_solve_vec(sL, RP + 1, srs, RP, sz);
+    fwd_solve_vec<F, true>(sL, RP + 1, srs, RP, sz);
     if (tid < 32) {
         F q = tid < RP ? f_sqr(sz[tid]) : f_of<F>(0.0);
         q = warp_sum_f(q);
