@@ -127,6 +127,36 @@ mra_status mra_loglik(mra_ctx *ctx, const double *theta, int batch, double *logl
 mra_status mra_loglik_device(mra_ctx *ctx, const double *theta_dev, int batch, double *loglik_dev,
                              int *status_dev, void *stream);
 
+/*
+ * mra_autotune -- choose the launch configuration of the context's current
+ * precision by timing it on this tree.  Candidates: observation rows per
+ * leaf-basis CTA (32 or, in the mixed mode, 64), one or two shared-memory
+ * stages of ancestor blocks, the leaf-size buckets of the leaf posterior
+ * ({<=32, <=48, <=64} or {<=32, <=64}), and running those buckets on side
+ * streams or one after another.  Every candidate computes the same loglik,
+ * bit for bit; only the time differs.  Each candidate runs 2 untimed and
+ * `reps` timed passes of one theta (theta: host, 3 doubles) on a stream of
+ * the library; the fastest is kept for later calls (mra_set_precision resets
+ * it).  out (may be NULL) receives the choice and the times.
+ */
+typedef struct {
+    int leafbasis_rows;   /* 32 or 64 */
+    int leafbasis_stages; /* 1 or 2 */
+    int bucket_set;       /* 0: {<=32, <=48, <=64}, 1: {<=32, <=64} */
+    int concurrent;       /* 1: leaf-posterior buckets on side streams */
+    double ms_default;    /* mean pass time with the configuration before the call */
+    double ms_best;       /* mean pass time with the chosen configuration */
+    int tried;            /* candidates timed */
+} mra_tune_t;
+
+mra_status mra_autotune(mra_ctx *ctx, const double *theta, int reps, mra_tune_t *out);
+
+/* Set the launch configuration directly (the four configuration fields of
+ * cfg; the times are ignored).  leafbasis_rows 0 and leafbasis_stages 0 select
+ * the defaults; EINVAL for a value outside the candidates or one whose shared
+ * memory does not fit. */
+mra_status mra_set_launch(mra_ctx *ctx, const mra_tune_t *cfg);
+
 /* Select MRA_FP64 or MRA_MIXED for later calls. */
 mra_status mra_set_precision(mra_ctx *ctx, int precision);
 

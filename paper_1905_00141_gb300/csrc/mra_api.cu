@@ -265,6 +265,14 @@ struct mra_ctx {
     int64_t *d_leaves[kLeafBuckets] = {nullptr, nullptr, nullptr};
     int nl[kLeafBuckets] = {0, 0, 0};
     int nmax_small = 64; // largest bucket cap whose shared memory fits
+    // the 48- and 64-observation buckets as one list (bucket set 1)
+    int64_t *d_leaves_m = nullptr;
+    int nl_m = 0;
+    // launch configuration (mra_autotune): leaf-basis rows per chunk (0 = the
+    // precision's default) and prefetch stages (0 = automatic), bucket set
+    // (0: 32/48/64, 1: 32/64), side streams for the leaf posterior
+    int lb_rows = 0, lb_stages = 0, bucket_set = 0;
+    bool concurrent = true;
     BigLeaf *d_big = nullptr;
     int nbig = 0;
     // work items of the tiled large-leaf kernels: [0, n_assemble) assembly
@@ -525,28 +533,42 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     c->launches_last = 0;
     for (int m = 1; m < M; m++)
         if ((e = timed_launch(c, K_PRIOR, s, [&] { return launch_prior<T, RP>(t, w, m, B, s); }))) return e;
-    const Chunk *chunks = chunk_rows<T>() == 64 ? c->d_chunks64 : c->d_chunks32;
-    const int nchunks = chunk_rows<T>() == 64 ? c->nchunks64 : c->nchunks32;
+    const int rows = (sizeof(T) == 4 && c->lb_rows == 32) ? 32 : chunk_rows<T>();
+    const Chunk *chunks = rows == 64 ? c->d_chunks64 : c->d_chunks32;
+    const int nchunks = rows == 64 ? c->nchunks64 : c->nchunks32;
     if (M > 1 && nchunks > 0)
-        if ((e = timed_launch(c, K_LEAFBASIS, s,
-                              [&] { return launch_leafbasis<T, RP>(t, w, chunks, nchunks, B, s); })))
+        if ((e = timed_launch(c, K_LEAFBASIS, s, [&] {
+                 return launch_leafbasis<T, RP>(t, w, chunks, nchunks, rows, c->lb_stages, B, s);
+             })))
             return e;
     // leaf posterior: the size buckets and the large-leaf pipeline touch
     // disjoint leaves, so they run concurrently: the large leaves (or the first
     // bucket) on s, every other bucket on a side stream forked from s
     int naux = 0;
     {
+        // the launch list of this bucket set: (leaves, count, cap)
+        const int64_t *lists[kLeafBuckets];
+        int counts[kLeafBuckets], caps[kLeafBuckets];
+        int nlist = 0;
+        const bool merged = c->bucket_set == 1 && c->nmax_small >= 64;
+        for (int k = 0; k < kLeafBuckets; k++) {
+            if (merged && kLeafCap[k] == 48) continue;
+            lists[nlist] = (merged && kLeafCap[k] == 64) ? c->d_leaves_m : c->d_leaves[k];
+            counts[nlist] = (merged && kLeafCap[k] == 64) ? c->nl_m : c->nl[k];
+            caps[nlist] = kLeafCap[k];
+            nlist++;
+        }
         int jobs = c->nbig > 0 ? 1 : 0;
-        for (int k = 0; k < kLeafBuckets; k++) jobs += c->nl[k] > 0;
-        const bool fork = jobs > 1;
+        for (int k = 0; k < nlist; k++) jobs += counts[k] > 0;
+        const bool fork = jobs > 1 && c->concurrent;
         if (fork) {
             if (!c->fork_ev && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess)
                 return (int)cudaErrorLaunchFailure;
             cudaEventRecord(c->fork_ev, s);
         }
         bool s_taken = c->nbig > 0;
-        for (int k = 0; k < kLeafBuckets; k++) {
-            if (c->nl[k] == 0) continue;
+        for (int k = 0; k < nlist; k++) {
+            if (counts[k] == 0) continue;
             cudaStream_t q = s;
             if (fork && s_taken) {
                 const int a = naux++;
@@ -559,7 +581,7 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
             }
             s_taken = true;
             if ((e = timed_launch(c, K_LEAFPOST, q, [&] {
-                     return launch_leafpost_small<T, RP>(t, w, c->d_leaves[k], c->nl[k], kLeafCap[k], B, q);
+                     return launch_leafpost_small<T, RP>(t, w, lists[k], counts[k], caps[k], B, q);
                  })))
                 return e;
         }
@@ -1033,6 +1055,12 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         }
     }
     c->vbig_elems = voff;
+    // bucket set 1: the 48- and 64-observation leaves as one list, in leaf order
+    std::vector<int64_t> lbm;
+    for (int64_t l = 0; l < P.nleaf(); l++) {
+        const int64_t nl = P.leaf_off[(size_t)l + 1] - P.leaf_off[(size_t)l];
+        if (nl > kLeafCap[0] && nl <= nmax_small) lbm.push_back(l);
+    }
     // tiled large-leaf work lists
     std::vector<BigTile> items;
     {
@@ -1090,6 +1118,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         (st = dev_upload(c, &c->d_leaves[0], lb[0].data(), lb[0].size())) ||
         (st = dev_upload(c, &c->d_leaves[1], lb[1].data(), lb[1].size())) ||
         (st = dev_upload(c, &c->d_leaves[2], lb[2].data(), lb[2].size())) ||
+        (st = dev_upload(c, &c->d_leaves_m, lbm.data(), lbm.size())) ||
         (st = dev_upload(c, &c->d_big, big.data(), big.size())) ||
         (st = dev_upload(c, &c->d_bigitems, items.data(), items.size()))) {
         *out = c;
@@ -1098,6 +1127,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     c->nchunks32 = (int)chunks32.size();
     c->nchunks64 = (int)chunks64.size();
     for (int k = 0; k < kLeafBuckets; k++) c->nl[k] = (int)lb[k].size();
+    c->nl_m = (int)lbm.size();
     c->nbig = (int)big.size();
     count_work(c);
     c->hbm_budget = opt.hbm_budget;
@@ -1114,6 +1144,137 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     return MRA_OK;
 }
 
+mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *out)
+{
+    if (!c || !theta || reps < 1) return MRA_EINVAL;
+    if (!c->d_sx) {
+        c->err = "context was built without a device";
+        return MRA_EINVAL;
+    }
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    if (mra_status st = ensure_stage(c, 1)) return st;
+    e = cudaMemcpy(c->d_theta_stage, theta, 3 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy theta");
+    struct Cfg {
+        int rows, stages, set;
+        bool conc;
+    };
+    const bool mixed = c->precision == MRA_MIXED;
+    const int RP = c->RP, M = c->P.M;
+    auto smem_ok = [&](int rows, int stages) {
+        size_t b;
+        if (mixed)
+            b = RP == 16 ? smem_leafbasis_cfg<float, 16>(M, rows, stages) : smem_leafbasis_cfg<float, 32>(M, rows, stages);
+        else
+            b = RP == 16 ? smem_leafbasis_cfg<double, 16>(M, rows, stages) : smem_leafbasis_cfg<double, 32>(M, rows, stages);
+        return b <= 227 * 1024;
+    };
+    std::vector<Cfg> cand;
+    const Cfg start{c->lb_rows, c->lb_stages, c->bucket_set, c->concurrent};
+    cand.push_back(start);
+    for (int rows : {64, 32}) {
+        if (rows == 64 && !mixed) continue;
+        for (int stages : {1, 2}) {
+            if (!smem_ok(rows, stages)) continue;
+            for (int set : {0, 1}) {
+                if (set == 1 && c->nmax_small < 64) continue;
+                for (bool conc : {true, false}) cand.push_back(Cfg{rows, stages, set, conc});
+            }
+        }
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        if (st) cudaStreamDestroy(st);
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(c, cudaErrorMemoryAllocation, "autotune stream");
+    }
+    auto apply = [&](const Cfg &g) {
+        c->lb_rows = g.rows;
+        c->lb_stages = g.stages;
+        c->bucket_set = g.set;
+        c->concurrent = g.conc;
+        drop_graphs(c); // the pass changes
+    };
+    double best = 1e300, first = 0.0;
+    Cfg bestc = start;
+    mra_status rs = MRA_OK;
+    for (size_t q = 0; q < cand.size() && rs == MRA_OK; q++) {
+        apply(cand[q]);
+        for (int w = 0; w < 2 && rs == MRA_OK; w++)
+            rs = enqueue(c, c->d_theta_stage, 1, c->d_ll_stage, nullptr, st, false);
+        if (rs != MRA_OK) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && rs == MRA_OK; r++)
+            rs = enqueue(c, c->d_theta_stage, 1, c->d_ll_stage, nullptr, st, false);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rs = cuda_fail(c, cudaGetLastError(), "autotune timing");
+        if (rs != MRA_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = (double)ms / reps;
+        if (q == 0) first = per;
+        if (per < best) {
+            best = per;
+            bestc = cand[q];
+        }
+    }
+    apply(rs == MRA_OK ? bestc : start);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (rs != MRA_OK) return rs;
+    if (out) {
+        out->leafbasis_rows = bestc.rows > 0 ? bestc.rows : (mixed ? 64 : 32);
+        int stages = bestc.stages;
+        if (stages == 0) { // the automatic rule of the launcher
+            const int r = out->leafbasis_rows;
+            const size_t b2 = mixed ? (RP == 16 ? smem_leafbasis_cfg<float, 16>(M, r, 2) : smem_leafbasis_cfg<float, 32>(M, r, 2))
+                                    : (RP == 16 ? smem_leafbasis_cfg<double, 16>(M, r, 2) : smem_leafbasis_cfg<double, 32>(M, r, 2));
+            stages = b2 <= (size_t)110 * 1024 ? 2 : 1;
+        }
+        out->leafbasis_stages = stages;
+        out->bucket_set = bestc.set;
+        out->concurrent = bestc.conc ? 1 : 0;
+        out->ms_default = first;
+        out->ms_best = best;
+        out->tried = (int)cand.size();
+    }
+    return MRA_OK;
+}
+
+mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
+{
+    if (!c || !g) return MRA_EINVAL;
+    const bool mixed = c->precision == MRA_MIXED;
+    const int rows = g->leafbasis_rows, stages = g->leafbasis_stages;
+    if (!(rows == 0 || rows == 32 || (rows == 64 && mixed)) || stages < 0 || stages > 2 || g->bucket_set < 0 ||
+        g->bucket_set > 1 || (g->bucket_set == 1 && c->nmax_small < 64)) {
+        c->err = "launch configuration outside the candidates";
+        return MRA_EINVAL;
+    }
+    if (stages > 0) {
+        const int r = rows > 0 ? rows : (mixed ? 64 : 32), RP = c->RP, M = c->P.M;
+        size_t b;
+        if (mixed)
+            b = RP == 16 ? smem_leafbasis_cfg<float, 16>(M, r, stages) : smem_leafbasis_cfg<float, 32>(M, r, stages);
+        else
+            b = RP == 16 ? smem_leafbasis_cfg<double, 16>(M, r, stages) : smem_leafbasis_cfg<double, 32>(M, r, stages);
+        if (b > 227 * 1024) {
+            c->err = "leaf-basis stages do not fit in shared memory";
+            return MRA_EINVAL;
+        }
+    }
+    c->lb_rows = rows;
+    c->lb_stages = stages;
+    c->bucket_set = g->bucket_set;
+    c->concurrent = g->concurrent != 0;
+    drop_graphs(c);
+    return MRA_OK;
+}
+
 mra_status mra_set_precision(mra_ctx *c, int precision)
 {
     if (!c) return MRA_EINVAL;
@@ -1123,6 +1284,8 @@ mra_status mra_set_precision(mra_ctx *c, int precision)
     }
     if (precision == c->precision) return MRA_OK;
     c->precision = precision;
+    c->lb_rows = c->lb_stages = c->bucket_set = 0; // tuned for the other precision
+    c->concurrent = true;
     if (c->d_sx) {
         // the scratch layout and the theta per pass depend on the storage type
         const int mb = max_batch_for(c, c->hbm_budget);
@@ -1327,7 +1490,7 @@ void mra_free(mra_ctx *c)
     }
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
-                    c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
+                    c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_leaves_m, c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
                     c->d_reg_du, c->d_reg_lw};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -111,8 +111,8 @@ template <typename T> __host__ __device__ constexpr int chunk_rows() { return si
 template <typename T, int RP>
 int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream);
 template <typename T, int RP>
-int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int B,
-                     void *stream);
+int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int rows, int stages,
+                     int B, void *stream);
 template <typename T, int RP>
 int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves,
                           int nmax, int B, void *stream);
@@ -131,6 +131,7 @@ int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream);
 // Dynamic shared memory (bytes) each kernel needs.
 template <typename T, int RP> size_t smem_prior(int m);
 template <typename T, int RP> size_t smem_leafbasis(int M);
+template <typename T, int RP> size_t smem_leafbasis_cfg(int M, int rows, int stages);
 template <typename T, int RP> size_t smem_leafpost_small(int M, int nmax);
 template <typename T, int RP> size_t smem_up(int m);
 template <typename T, int RP> size_t smem_leafgram(int M);

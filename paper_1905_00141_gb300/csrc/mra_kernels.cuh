@@ -815,24 +815,23 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
 // A chunk of observation rows below one level-(M-1) region: What^l of each
 // row against its M-1 ancestors, written as rows of U.
 template <typename T, int RP>
-__host__ __device__ constexpr size_t smem_leafbasis_bytes(int M, int stages)
+__host__ __device__ constexpr size_t smem_leafbasis_bytes(int M, int stages, int CH = chunk_rows<T>())
 {
-    return (size_t)(2 * chunk_rows<T>() + 2 * RP) * sizeof(T) + (size_t)(M - 1) * RP * (chunk_rows<T>() + 2) * sizeof(T) +
-           (size_t)stages * (M - 1) * RP * RP * sizeof(T) + (size_t)RP * (chunk_rows<T>() + 2) * sizeof(T) + 64;
+    return (size_t)(2 * CH + 2 * RP) * sizeof(T) + (size_t)(M - 1) * RP * (CH + 2) * sizeof(T) +
+           (size_t)stages * (M - 1) * RP * RP * sizeof(T) + (size_t)RP * (CH + 2) * sizeof(T) + 64;
 }
 
 // Two stages of ancestor blocks (prefetch of the next level) only while two
 // CTAs still fit on an SM; deep trees keep one stage and the occupancy.
 template <typename T, int RP>
-__host__ __device__ constexpr int leafbasis_stages(int M)
+__host__ __device__ constexpr int leafbasis_stages(int M, int CH = chunk_rows<T>())
 {
-    return smem_leafbasis_bytes<T, RP>(M, 2) <= (size_t)110 * 1024 ? 2 : 1;
+    return smem_leafbasis_bytes<T, RP>(M, 2, CH) <= (size_t)110 * 1024 ? 2 : 1;
 }
 
-template <typename T, int RP>
-__global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Chunk *chunks)
+template <typename T, int RP, int CH>
+__global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Chunk *chunks, int stages)
 {
-    constexpr int CH = chunk_rows<T>();
     constexpr int LDC = CH + 2; // k-major row stride (keeps the transposed write-out conflict-light)
     using TL = Tile<CH, RP>;
     const Chunk ch = chunks[blockIdx.x];
@@ -845,7 +844,6 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
     T *sp = (T *)smem_raw;                  // 2 CH rows relative to the ancestor corner
     T *sa = sp + 2 * CH;                    // 2 RP
     T *sU = sa + 2 * RP;                     // (M-1) blocks k-major [t][row], stride LDC
-    const int stages = leafbasis_stages<T, RP>(M);
     T *sB0 = sU + (size_t)(M - 1) * RP * LDC;          // 1 or 2 stages of up to M-1 ancestor blocks
     T *sW = sB0 + (size_t)stages * (M - 1) * RP * RP; // RP x LDC k-major
     const T *pb = w.prior + (size_t)b * w.prior_stride;

@@ -17,6 +17,10 @@ static int set_smem(K kernel, size_t bytes, size_t *done)
 }
 
 template <typename T, int RP> size_t smem_prior(int m) { return smem_prior_bytes<T, RP>(m); }
+template <typename T, int RP> size_t smem_leafbasis_cfg(int M, int rows, int stages)
+{
+    return smem_leafbasis_bytes<T, RP>(M, stages, rows);
+}
 template <typename T, int RP> size_t smem_leafbasis(int M)
 {
     return smem_leafbasis_bytes<T, RP>(M, leafbasis_stages<T, RP>(M));
@@ -41,16 +45,29 @@ int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream)
     return (int)cudaGetLastError();
 }
 
-template <typename T, int RP>
-int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int B, void *stream)
+template <typename T, int RP, int CH>
+static int launch_leafbasis_ch(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int stages, int B,
+                               void *stream)
 {
     static size_t done = 0;
-    if (nchunks == 0) return 0;
-    const size_t sm = smem_leafbasis_bytes<T, RP>(t.M, leafbasis_stages<T, RP>(t.M));
-    if (int e = set_smem(k_leafbasis<T, RP>, sm, &done)) return e;
+    if (stages <= 0) stages = leafbasis_stages<T, RP>(t.M, CH);
+    const size_t sm = smem_leafbasis_bytes<T, RP>(t.M, stages, CH);
+    if (int e = set_smem(k_leafbasis<T, RP, CH>, sm, &done)) return e;
     dim3 grid((unsigned)nchunks, (unsigned)B);
-    k_leafbasis<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, chunks);
+    k_leafbasis<T, RP, CH><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, chunks, stages);
     return (int)cudaGetLastError();
+}
+
+// rows: observation rows per chunk (32, or 64 in FP32); stages: 1 or 2 stages
+// of ancestor blocks, 0 = two while two CTAs per SM still fit
+template <typename T, int RP>
+int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int rows, int stages,
+                     int B, void *stream)
+{
+    if (nchunks == 0) return 0;
+    if constexpr (sizeof(T) == 4)
+        if (rows == 64) return launch_leafbasis_ch<T, RP, 64>(t, w, chunks, nchunks, stages, B, stream);
+    return launch_leafbasis_ch<T, RP, 32>(t, w, chunks, nchunks, stages, B, stream);
 }
 
 template <typename T, int RP, int NMAX>
@@ -148,11 +165,13 @@ int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream)
 #define MRA_INSTANTIATE(T, RP)                                                                              \
     template size_t smem_prior<T, RP>(int);                                                                 \
     template size_t smem_leafbasis<T, RP>(int);                                                             \
+    template size_t smem_leafbasis_cfg<T, RP>(int, int, int);                                               \
     template size_t smem_leafpost_small<T, RP>(int, int);                                                   \
     template size_t smem_up<T, RP>(int);                                                                    \
     template size_t smem_leafgram<T, RP>(int);                                                              \
     template int launch_prior<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                   \
-    template int launch_leafbasis<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, void *); \
+    template int launch_leafbasis<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, int, int, \
+                                         void *);                                                           \
     template int launch_leafpost_small<T, RP>(const DevTree &, const Work<T> &, const int64_t *, int, int,   \
                                               int, void *);                                                 \
     template size_t smem_big<T, RP>(int);                                                                   \

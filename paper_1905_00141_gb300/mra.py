@@ -23,7 +23,7 @@ _STATUS = {0: "MRA_OK", 1: "MRA_EINVAL", 2: "MRA_ENOMEM", 3: "MRA_ENOTPD", 4: "M
 
 EXPORTED = ["mra_default_opts", "mra_build", "mra_loglik", "mra_loglik_device", "mra_set_precision",
             "mra_stats", "mra_tree_export", "mra_region_terms", "mra_profile", "mra_profile_read",
-            "mra_dense_loglik_noalloc", "mra_last_error", "mra_free"]
+            "mra_dense_loglik_noalloc", "mra_autotune", "mra_set_launch", "mra_last_error", "mra_free"]
 
 
 def last_error() -> str:
@@ -56,6 +56,12 @@ class Stats(ctypes.Structure):
 KERNEL_FAMILIES = ["prior", "leafbasis", "leafpost", "leafpost_big", "leafgram", "up", "root"]
 
 
+class Tune(ctypes.Structure):
+    _fields_ = [("leafbasis_rows", ctypes.c_int), ("leafbasis_stages", ctypes.c_int), ("bucket_set", ctypes.c_int),
+                ("concurrent", ctypes.c_int), ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double),
+                ("tried", ctypes.c_int)]
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
@@ -81,6 +87,10 @@ def lib():
         L.mra_loglik.argtypes = [vp, D, ctypes.c_int, D]
         L.mra_loglik_device.restype = ctypes.c_int
         L.mra_loglik_device.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp]
+        L.mra_autotune.restype = ctypes.c_int
+        L.mra_autotune.argtypes = [vp, D, ctypes.c_int, ctypes.POINTER(Tune)]
+        L.mra_set_launch.restype = ctypes.c_int
+        L.mra_set_launch.argtypes = [vp, ctypes.POINTER(Tune)]
         L.mra_set_precision.restype = ctypes.c_int
         L.mra_set_precision.argtypes = [vp, ctypes.c_int]
         L.mra_stats.restype = ctypes.c_int
@@ -202,6 +212,17 @@ class MRA:
         if check:
             self._check(st)
         return out
+
+    def autotune(self, theta, reps: int = 5) -> dict:
+        """Time the launch configurations on one theta and keep the fastest."""
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(3))
+        out = Tune()
+        self._check(lib().mra_autotune(self._h, _dp(th), int(reps), ctypes.byref(out)))
+        return {k: getattr(out, k) for k, _ in Tune._fields_}
+
+    def set_launch(self, leafbasis_rows=0, leafbasis_stages=0, bucket_set=0, concurrent=True):
+        cfg = Tune(int(leafbasis_rows), int(leafbasis_stages), int(bucket_set), int(bool(concurrent)), 0.0, 0.0, 0)
+        self._check(lib().mra_set_launch(self._h, ctypes.byref(cfg)))
 
     def loglik_status(self, theta):
         th = np.ascontiguousarray(np.atleast_2d(theta), dtype=np.float64)

@@ -209,3 +209,29 @@ def test_graph_replay_equals_direct_launches(precision):
                 g1.loglik_device(th[k].data_ptr(), 1, out[k].data_ptr(), 0, 0)
         torch.cuda.synchronize()
         assert np.array_equal(np.array([o.item() for o in out]), ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_launch_configurations_agree_bit_for_bit(precision):
+    # leaves of every bucket (<=32, <=48, <=64) and larger ones
+    rng = np.random.default_rng(31)
+    x, y, z = synth.uniform(6000, 24)
+    cx = 0.25 + 0.01 * rng.standard_normal(500)
+    cy = 0.6 + 0.01 * rng.standard_normal(500)
+    x, y, z = np.concatenate([x, cx]), np.concatenate([y, cy]), np.concatenate([z, rng.standard_normal(500)])
+    with mra.MRA(x, y, z, 4, 4, 16, precision=precision) as g:
+        s = g.stats()
+        assert s["max_leaf"] > 64
+        ref = g.loglik(THETAS)
+        rows = (32, 64) if precision == "mixed" else (32,)
+        for r in rows:
+            for stages in (1, 2):
+                for bset in (0, 1):
+                    for conc in (True, False):
+                        g.set_launch(r, stages, bset, conc)
+                        assert np.array_equal(g.loglik(THETAS), ref), (r, stages, bset, conc)
+        rep = g.autotune(THETAS[0], reps=2)
+        assert rep["tried"] >= 2 and rep["ms_best"] <= rep["ms_default"]
+        assert np.array_equal(g.loglik(THETAS), ref)
+        with pytest.raises(mra.MRAError):
+            g.set_launch(48, 1, 0, True)
