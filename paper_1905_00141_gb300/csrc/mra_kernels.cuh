@@ -709,7 +709,8 @@ template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_prior_bytes(int m)
 {
     return (size_t)RP * (RP + 1) * 8 + (RP + 2) * 8 + 8 * 8 + (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 +
-           4 * RP * sizeof(T) + (size_t)(2 * m + 2) * RP * RP * sizeof(T) + RP * sizeof(T) + 64;
+           4 * RP * sizeof(T) + (size_t)((m - 1) + 2 * (m > 1 ? m - 1 : 1) + 1) * RP * RP * sizeof(T) +
+           RP * sizeof(T) + 64;
 }
 
 template <typename T, int RP>
@@ -730,19 +731,33 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     T *sq = (T *)(flag + 16);               // own knots relative to the current origin: 2 RP
     T *sa = sq + 2 * RP;                    // ancestor knots: 2 RP
     T *sU = sa + 2 * RP;                    // (m-1) blocks k-major [t][row]
-    T *sB = sU + (size_t)(m - 1) * RP * RP; // up to m blocks of the ancestor (column-major)
-    T *sW = sB + (size_t)m * RP * RP;       // RP x RP k-major
-    T *sX = sW + RP * RP;                   // RP x RP scratch
+    T *sB0 = sU + (size_t)(m - 1) * RP * RP; // 2 stages of up to m-1 ancestor blocks (column-major)
+    T *sW = sB0 + (size_t)2 * (m > 1 ? m - 1 : 1) * RP * RP; // RP x RP k-major
 
     const int R = t.R;
     const int64_t g = t.lvl_off[m] + i;
     if (tid == 0) flag[0] = 0;
     T *pb = w.prior + (size_t)b * w.prior_stride;
     const int r0 = TL::r0(), c0 = TL::c0();
+    // the level-l ancestor's blocks go to stage l & 1; level l + 1 is fetched
+    // with cp.async while level l is computed
+    const size_t stage = (size_t)(m > 1 ? m - 1 : 1) * RP * RP;
+    auto fetch = [&](int l) {
+        const int64_t ia = (int64_t)i >> (t.lgJ * (m - l));
+        copy_g2s_async(sB0 + (size_t)(l & 1) * stage, pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP, l * RP * RP);
+        cp_async_commit();
+    };
+    if (m > 1) fetch(1);
     for (int l = 1; l < m; l++) {
         const int64_t ia = (int64_t)i >> (t.lgJ * (m - l));
         const int64_t ga = t.lvl_off[l] + ia;
-        copy_g2s(sB, pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP, l * RP * RP);
+        T *sB = sB0 + (size_t)(l & 1) * stage;
+        if (l + 1 < m) {
+            fetch(l + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         if (tid < RP) {
             const double ox = t.cx[ga], oy = t.cy[ga];
             sq[tid] = (T)(t.kx[g * RP + tid] - ox);
