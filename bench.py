@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "mixed_fast", "fp64"])
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the cpu_baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -57,6 +57,24 @@ def parse():
                    help="grid: n=131,072, 1 theta per call (default); clustered: n=2,097,152 with 64 theta per "
                         "call; massive: n=47,185,920, 1 theta per call")
     return p.parse_args()
+
+
+def max_over_ranks(x, world):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def whole_job_rate(n_obs, theta_per_call, steps, seconds, world):
+    """obs*evals/s of the whole job: every rank evaluates its own `steps` calls
+    of `theta_per_call` theta on the same tree (no data exchange), in the
+    slowest rank's time."""
+    return world * n_obs * theta_per_call * steps / seconds
 
 
 def dist_env():
@@ -311,15 +329,11 @@ def run_ours(args):
     ms, clocks, prof, ll = one_measure(args.precision, args)
     if clocks_rejected(clocks):
         ms, clocks, prof, ll = one_measure(args.precision, args)
-    t_total = sum(ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt[0])
-    value = world * n * per_call * args.steps / t_total
+    t_total = max_over_ranks(sum(ms) / 1e3, world)
+    value = whole_job_rate(n, per_call, args.steps, t_total, world)
 
     # the other precision on the same theta, for the mixed-vs-FP64 comparison
-    other = "fp64" if args.precision == "mixed" else "mixed"
+    other = "fp64" if args.precision != "fp64" else "mixed"
     other_line, ll_o = None, None
     if name != "massive":
         oargs = argparse.Namespace(**vars(args))
@@ -328,6 +342,16 @@ def run_ours(args):
         ms_o, _, prof_o, ll_o = one_measure(other, oargs)
         other_line = {"precision": other, "value": world * n * per_call * oargs.steps / (sum(ms_o) / 1e3),
                       "ms_per_step": sum(ms_o) / oargs.steps, "steps": oargs.steps}
+        g.set_precision(args.precision)
+        g.autotune(thetas[0][0], reps=3)
+    # the fast mixed mode (FP32 remainder recursions) on the same steps
+    fast_line, ll_f = None, None
+    if args.precision == "mixed" and name == "grid":
+        g.set_precision("mixed_fast")
+        g.autotune(thetas[0][0], reps=3)
+        ms_f, _, _, ll_f = one_measure("mixed_fast", args)
+        fast_line = {"precision": "mixed_fast", "value": whole_job_rate(n, per_call, args.steps, sum(ms_f) / 1e3, 1),
+                     "ms_per_step": sum(ms_f) / args.steps}
         g.set_precision(args.precision)
         g.autotune(thetas[0][0], reps=3)
 
@@ -341,11 +365,7 @@ def run_ours(args):
     for k in range(args.steps):
         g.loglik(th_host[k % C])
     e2e_dt = time.perf_counter() - t0
-    e2e_value = world * n * per_call * args.steps / e2e_dt if world == 1 else None
-    if world > 1:
-        tt = torch.tensor([e2e_dt], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_value = world * n * per_call * args.steps / float(tt[0])
+    e2e_value = whole_job_rate(n, per_call, args.steps, max_over_ranks(e2e_dt, world), world)
 
     if rank != 0:
         if world > 1:
@@ -363,6 +383,8 @@ def run_ours(args):
         ref = ref.reshape(thetas.shape[:2])
         acc = {"against": "FP64 CPU oracle", args.precision: float(np.max(np.abs(ll - ref)) / n),
                other: float(np.max(np.abs(ll_o - ref)) / n)}
+        if ll_f is not None:
+            acc["mixed_fast"] = float(np.max(np.abs(ll_f - ref)) / n)
     elif ll_o is not None:
         acc = {"against": "FP64 GPU path", args.precision: float(np.max(np.abs(ll - ll_o)) / n)}
     else:
@@ -374,7 +396,7 @@ def run_ours(args):
     launches, fam_ms = prof[fam]
     fl_per_launch = st["flops_by_kernel"][fam] * per_call * args.steps / launches
     achieved = fl_per_launch / (fam_ms / launches / 1e3) / 1e12
-    if args.precision == "mixed":
+    if args.precision != "fp64":
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz (derived, no tensor cores on this path)"
     else:
@@ -402,7 +424,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+ff",
         "data": WORKLOAD_INFO[name]["data"], "config": config(args.precision, name, d),
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -413,6 +435,7 @@ def run_ours(args):
         "clocks": clocks,
         "accuracy_abs_dl_per_n": acc,
         "other_precision": other_line,
+        "fast_mixed": fast_line,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "flops_per_eval": st["flops_per_theta"],
         "launch_config": {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent")},

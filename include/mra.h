@@ -47,12 +47,19 @@ typedef enum {
     MRA_EEMPTY = 6     /* no observation left after the eliminations of Sec. 1.2 */
 } mra_status;
 
-enum { MRA_FP64 = 0, MRA_MIXED = 1 };
+/* MRA_FP64: every step in FP64.  MRA_MIXED: FP32 storage and products; float
+ * pairs (double-float on the FP32 pipe) for the covariances, the remainder
+ * recursions C_l(., Q) = C - sum_k What^k What^k' of the prior and of the leaf
+ * basis (exact products), the leaf covariance, every Cholesky factor,
+ * log-determinant and quadratic form.  MRA_MIXED_FAST: as MRA_MIXED but the
+ * remainder recursions in FP32 (faster; its error grows with tree depth and
+ * covariance range, e.g. |dl|/n ~ 2e-5 at M = 14, range 0.3). */
+enum { MRA_FP64 = 0, MRA_MIXED = 1, MRA_MIXED_FAST = 2 };
 
 typedef struct {
     double offset;     /* knot offset f of Sec. 1.2; < 0 selects the paper's default e/100 */
     int dedup;         /* ELIMINATION_DUPLICATES_FLAG: drop repeated locations, keep the first */
-    int precision;     /* MRA_FP64 (default) or MRA_MIXED */
+    int precision;     /* MRA_FP64 (default), MRA_MIXED or MRA_MIXED_FAST */
     int device;        /* CUDA device ordinal; -1 builds the partition on the host only
                           (stats and tree queries work, likelihood calls give MRA_EINVAL) */
     int max_batch;     /* theta evaluated per device pass; 0 = choose from hbm_budget */
@@ -157,7 +164,7 @@ mra_status mra_autotune(mra_ctx *ctx, const double *theta, int reps, mra_tune_t 
  * memory does not fit. */
 mra_status mra_set_launch(mra_ctx *ctx, const mra_tune_t *cfg);
 
-/* Select MRA_FP64 or MRA_MIXED for later calls. */
+/* Select MRA_FP64, MRA_MIXED or MRA_MIXED_FAST for later calls. */
 mra_status mra_set_precision(mra_ctx *ctx, int precision);
 
 /* Counts, sizes and the algorithmic work of one evaluation. */

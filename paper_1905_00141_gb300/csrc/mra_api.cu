@@ -454,7 +454,7 @@ Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
 // layout make_work<T> lays out).
 size_t scratch_bytes_for(const Plan &p, const mra_ctx *c, int B)
 {
-    const size_t ts = c->precision == MRA_MIXED ? sizeof(float) : sizeof(double);
+    const size_t ts = c->precision != MRA_FP64 ? sizeof(float) : sizeof(double);
     size_t s = 0;
     auto addT = [&](size_t elems) { s = align256(s + elems * (size_t)B * ts); };
     auto addD = [&](size_t elems) { s = align256(s + elems * (size_t)B * sizeof(double)); };
@@ -797,8 +797,9 @@ mra_status pass_ops(mra_ctx *c, const double *theta_dev, int B, double *loglik_d
     cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int) * (size_t)B, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
     int rc;
-    if (c->precision == MRA_MIXED) {
+    if (c->precision != MRA_FP64) {
         Work<float> w = make_work<float>(c, p, B);
+        w.exact_rem = c->precision == MRA_MIXED;
         w.theta = theta_dev;
         w.loglik = loglik_dev;
         if (with_regions) {
@@ -979,7 +980,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     mra_opts opt;
     mra_default_opts(&opt);
     if (opt_in) opt = *opt_in;
-    if (opt.precision != MRA_FP64 && opt.precision != MRA_MIXED) return MRA_EINVAL;
+    if (opt.precision != MRA_FP64 && opt.precision != MRA_MIXED && opt.precision != MRA_MIXED_FAST) return MRA_EINVAL;
     mra_ctx *c = new (std::nothrow) mra_ctx();
     if (!c) return MRA_ENOMEM;
     *out = c;
@@ -1008,10 +1009,6 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     cudaError_t e = cudaSetDevice(opt.device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     // work lists
-    if (M - 1 > 12) {
-        c->err = "M - 1 > 12 levels above the leaves is not supported by this build";
-        return MRA_EINVAL;
-    }
     std::vector<Chunk> chunks32, chunks64;
     if (M > 1) {
         const int64_t nP = P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1];
@@ -1160,7 +1157,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         int rows, stages, set;
         bool conc;
     };
-    const bool mixed = c->precision == MRA_MIXED;
+    const bool mixed = c->precision != MRA_FP64;
     const int RP = c->RP, M = c->P.M;
     auto smem_ok = [&](int rows, int stages) {
         size_t b;
@@ -1248,7 +1245,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
 mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
 {
     if (!c || !g) return MRA_EINVAL;
-    const bool mixed = c->precision == MRA_MIXED;
+    const bool mixed = c->precision != MRA_FP64;
     const int rows = g->leafbasis_rows, stages = g->leafbasis_stages;
     if (!(rows == 0 || rows == 32 || (rows == 64 && mixed)) || stages < 0 || stages > 2 || g->bucket_set < 0 ||
         g->bucket_set > 1 || (g->bucket_set == 1 && c->nmax_small < 64)) {
@@ -1278,8 +1275,8 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
 mra_status mra_set_precision(mra_ctx *c, int precision)
 {
     if (!c) return MRA_EINVAL;
-    if (precision != MRA_FP64 && precision != MRA_MIXED) {
-        c->err = "precision must be MRA_FP64 or MRA_MIXED";
+    if (precision != MRA_FP64 && precision != MRA_MIXED && precision != MRA_MIXED_FAST) {
+        c->err = "precision must be MRA_FP64, MRA_MIXED or MRA_MIXED_FAST";
         return MRA_EINVAL;
     }
     if (precision == c->precision) return MRA_OK;

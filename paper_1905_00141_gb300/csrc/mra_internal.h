@@ -70,6 +70,7 @@ struct Work {
     double *Atil_w[MRA_MAXM + 1];
     double *Atil_du[MRA_MAXM + 1];
     size_t Atil_stride[MRA_MAXM + 1], Atilw_stride[MRA_MAXM + 1], Atildu_stride[MRA_MAXM + 1];
+    int exact_rem;  // FP32 storage: remainder recursions with float-pair covariance and exact products
     double *reg_du; // [nreg][2] or null
     double *reg_lw; // [n_nonleaf] or null
     size_t regdu_stride, reglw_stride;

@@ -221,6 +221,58 @@ __device__ __forceinline__ void ff_merge(FF &s, const FF &o)
     ff_add(s, o.hi);
     s.lo = __fadd_rn(s.lo, o.lo);
 }
+// acc[r][c] += sum_t A[t][r0 + r] * B[t][c0 + c] as exact FP32 products summed
+// in float pairs (the register tile of tile_fma).
+template <int ROWS, int COLS>
+__device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile<ROWS, COLS>::CT], const float *A,
+                                            int lda, const float *B, int ldb, int K)
+{
+    using TL = Tile<ROWS, COLS>;
+    const int r0 = TL::r0(), c0 = TL::c0();
+    for (int t = 0; t < K; t++) {
+        float a[TL::RT], b[TL::CT];
+        ldv<float, TL::RT>(a, A + t * lda + r0);
+        ldv<float, TL::CT>(b, B + t * ldb + c0);
+#pragma unroll
+        for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+            for (int c = 0; c < TL::CT; c++) ff_add_prod(acc[r][c], a[r], b[c]);
+    }
+}
+
+// The remainder C(P, Q) - sum_k What^k(P) What^k(Q)' of one RP-column block
+// (Sec. 1.1 recursion) for FP32 storage, with the covariance in float pairs
+// and the products exact: the prior evaluates it at knots and the leaf basis
+// at observations, and the two must agree far below FP32 relative to sigma2
+// where the remainder is small (deep levels, long ranges).  P coordinates at
+// pp[a], pp[ldp + a] (nP valid rows), Q at pq[j], pq[RP + j] (R valid); the
+// result is rounded to FP32.  Returns the float-pair value of entry (a, j).
+template <int ROWS, int RP>
+__device__ __forceinline__ void remainder_ff(float (&out)[Tile<ROWS, RP>::RT][Tile<ROWS, RP>::CT], const float *Ak,
+                                             int lda, const float *Bk, int K, const float *pp, int ldp, int nP,
+                                             const float *pq, int R, const double *th)
+{
+    using TL = Tile<ROWS, RP>;
+    FF fa[TL::RT][TL::CT];
+#pragma unroll
+    for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+        for (int c = 0; c < TL::CT; c++) fa[r][c] = FF{0.f, 0.f};
+    tile_fma_ff<ROWS, RP>(fa, Ak, lda, Bk, RP, K);
+    const ff s2f = ff_from_double(th[0]), ibf = ff_from_double(1.0 / th[1]);
+    const int r0 = TL::r0(), c0 = TL::c0();
+#pragma unroll
+    for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+        for (int c = 0; c < TL::CT; c++) {
+            const int a = r0 + r, j = c0 + c;
+            ff cv = ff{0.f, 0.f};
+            if (a < nP && j < R)
+                cv = ff_cov_exp(s2f, ibf, ff{pp[a], 0.f}, ff{pp[ldp + a], 0.f}, ff{pq[j], 0.f}, ff{pq[RP + j], 0.f});
+            out[r][c] = ff_sub(cv, ff{fa[r][c].hi, fa[r][c].lo}).hi;
+        }
+}
+
 __device__ __forceinline__ void dot2(const float *a, const float *b, int K, float &hi, float &lo)
 {
     // four independent pairs for instruction-level parallelism, merged exactly
@@ -767,16 +819,29 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
         }
         __syncthreads();
         T acc[TL::RT][TL::CT];
-        tile_zero(acc);
-        tile_fma<T, RP, RP>(acc, sU, RP, sB, RP, (l - 1) * RP);
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (w.exact_rem) {
+                remainder_ff<RP, RP>(acc, sU, RP, sB, (l - 1) * RP, sq, RP, R, sa, R, th);
 #pragma unroll
-        for (int r = 0; r < TL::RT; r++)
+                for (int r = 0; r < TL::RT; r++)
 #pragma unroll
-            for (int c = 0; c < TL::CT; c++) {
-                const int a = r0 + r, j = c0 + c;
-                const T cv = (a < R && j < R) ? cov_d(cp, sq[a] - sa[j], sq[RP + a] - sa[RP + j]) : T(0);
-                sW[j * RP + a] = cv - acc[r][c];
+                    for (int c = 0; c < TL::CT; c++) sW[(c0 + c) * RP + r0 + r] = acc[r][c];
+                done = true;
             }
+        }
+        if (!done) {
+            tile_zero(acc);
+            tile_fma<T, RP, RP>(acc, sU, RP, sB, RP, (l - 1) * RP);
+#pragma unroll
+            for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                for (int c = 0; c < TL::CT; c++) {
+                    const int a = r0 + r, j = c0 + c;
+                    const T cv = (a < R && j < R) ? cov_d(cp, sq[a] - sa[j], sq[RP + a] - sa[RP + j]) : T(0);
+                    sW[j * RP + a] = cv - acc[r][c];
+                }
+        }
         __syncthreads();
         tile_zero(acc);
         tile_fma<T, RP, RP>(acc, sW, RP, sB + (size_t)(l - 1) * RP * RP, RP, RP);
@@ -794,7 +859,35 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
         sq[RP + tid] = (T)(t.ky[g * RP + tid] - oy);
     }
     __syncthreads();
-    {
+    bool self_done = false;
+    if constexpr (sizeof(T) == 4) {
+        if (w.exact_rem) {
+            // W^m in float pairs straight into the factorization
+            FF fa[TL::RT][TL::CT];
+#pragma unroll
+            for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                for (int c = 0; c < TL::CT; c++) fa[r][c] = FF{0.f, 0.f};
+            tile_fma_ff<RP, RP>(fa, sU, RP, sU, RP, (m - 1) * RP);
+            const ff s2f = ff_from_double(th[0]), ibf = ff_from_double(1.0 / th[1]);
+#pragma unroll
+            for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                for (int c = 0; c < TL::CT; c++) {
+                    const int a = r0 + r, j = c0 + c;
+                    F v;
+                    if (a < R && j < R)
+                        v = ff_sub(ff_cov_exp(s2f, ibf, ff{sq[a], 0.f}, ff{sq[RP + a], 0.f}, ff{sq[j], 0.f},
+                                              ff{sq[RP + j], 0.f}),
+                                   ff{fa[r][c].hi, fa[r][c].lo});
+                    else
+                        v = f_of<F>(a == j ? 1.0 : 0.0);
+                    sL[a * (RP + 1) + j] = v;
+                }
+            self_done = true;
+        }
+    }
+    if (!self_done) {
         T acc[TL::RT][TL::CT];
         tile_zero(acc);
         tile_fma<T, RP, RP>(acc, sU, RP, sU, RP, (m - 1) * RP);
@@ -898,16 +991,29 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
         }
         __syncthreads();
         T acc[TL::RT][TL::CT];
-        tile_zero(acc);
-        tile_fma<T, CH, RP>(acc, sU, LDC, sB, RP, (l - 1) * RP);
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (w.exact_rem) {
+                remainder_ff<CH, RP>(acc, sU, LDC, sB, (l - 1) * RP, sp, CH, nr, sa, R, th);
 #pragma unroll
-        for (int r = 0; r < TL::RT; r++)
+                for (int r = 0; r < TL::RT; r++)
 #pragma unroll
-            for (int c = 0; c < TL::CT; c++) {
-                const int a = r0 + r, j = c0 + c;
-                const T cv = (a < nr && j < R) ? cov_d(cp, sp[a] - sa[j], sp[CH + a] - sa[RP + j]) : T(0);
-                sW[j * LDC + a] = cv - acc[r][c];
+                    for (int c = 0; c < TL::CT; c++) sW[(c0 + c) * LDC + r0 + r] = acc[r][c];
+                done = true;
             }
+        }
+        if (!done) {
+            tile_zero(acc);
+            tile_fma<T, CH, RP>(acc, sU, LDC, sB, RP, (l - 1) * RP);
+#pragma unroll
+            for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                for (int c = 0; c < TL::CT; c++) {
+                    const int a = r0 + r, j = c0 + c;
+                    const T cv = (a < nr && j < R) ? cov_d(cp, sp[a] - sa[j], sp[CH + a] - sa[RP + j]) : T(0);
+                    sW[j * LDC + a] = cv - acc[r][c];
+                }
+        }
         __syncthreads();
         tile_zero(acc);
         tile_fma<T, CH, RP>(acc, sW, LDC, sB + (size_t)(l - 1) * RP * RP, RP, RP);

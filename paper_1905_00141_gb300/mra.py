@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmra.so")
 
 OK, EINVAL, ENOMEM, ENOTPD, ECUDA, ETIMEDOUT, EEMPTY = 0, 1, 2, 3, 4, 5, 6
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_FAST = 0, 1, 2
 _STATUS = {0: "MRA_OK", 1: "MRA_EINVAL", 2: "MRA_ENOMEM", 3: "MRA_ENOTPD", 4: "MRA_ECUDA",
            5: "MRA_ETIMEDOUT", 6: "MRA_EEMPTY"}
 
@@ -285,7 +285,7 @@ def dense_loglik_noalloc(x_ptr: int, y_ptr: int, z_ptr: int, n: int, theta_ptr: 
 
 def _prec(p):
     if isinstance(p, str):
-        return {"fp64": FP64, "mixed": MIXED}[p]
+        return {"fp64": FP64, "mixed": MIXED, "mixed_fast": MIXED_FAST}[p]
     return int(p)
 
 
