@@ -221,14 +221,31 @@ __device__ __forceinline__ void ff_merge(FF &s, const FF &o)
     ff_add(s, o.hi);
     s.lo = __fadd_rn(s.lo, o.lo);
 }
-// acc[r][c] += sum_t A[t][r0 + r] * B[t][c0 + c] as exact FP32 products summed
-// in float pairs (the register tile of tile_fma).
+// acc[r][c] = sum_t A[t][r0 + r] * B[t][c0 + c] for rows of whitened basis
+// functions.  Since sum_k |What^k(x)|^2 <= C(x, x) = sigma2 (Sec. 1.1: the
+// remainder covariance stays positive), Cauchy-Schwarz bounds sum_t |a_t b_t|
+// by sigma2 < 2^E (E: binary exponent of sigma2).  Every product is split
+// exactly (TwoProd) into p + e.  The high sum H starts at Cq = 1.5 * 2^(E + 2)
+// and stays inside [2^(E + 2), 2^(E + 3)), where the FP32 grid is
+// delta = 2^(E - 21): H + p rounds p onto that grid, and since |H| > |p| the
+// part left over, p - ((H + p) - H), is exact (Fast2Sum) and below delta / 2.
+// That part plus e goes into a second FP32 sum whose rounding is
+// ~2^-24 * K * delta, near 1e-11 sigma2.  Seven FP32 operations a product
+// instead of the ten of a float-pair TwoSum accumulation.
 template <int ROWS, int COLS>
 __device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile<ROWS, COLS>::CT], const float *A,
-                                            int lda, const float *B, int ldb, int K)
+                                            int lda, const float *B, int ldb, int K, float Cq)
 {
     using TL = Tile<ROWS, COLS>;
     const int r0 = TL::r0(), c0 = TL::c0();
+    float hi[TL::RT][TL::CT], lo[TL::RT][TL::CT];
+#pragma unroll
+    for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+        for (int c = 0; c < TL::CT; c++) {
+            hi[r][c] = Cq;
+            lo[r][c] = 0.f;
+        }
     for (int t = 0; t < K; t++) {
         float a[TL::RT], b[TL::CT];
         ldv<float, TL::RT>(a, A + t * lda + r0);
@@ -236,8 +253,30 @@ __device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile
 #pragma unroll
         for (int r = 0; r < TL::RT; r++)
 #pragma unroll
-            for (int c = 0; c < TL::CT; c++) ff_add_prod(acc[r][c], a[r], b[c]);
+            for (int c = 0; c < TL::CT; c++) {
+                const float p = __fmul_rn(a[r], b[c]);
+                const float e = __fmaf_rn(a[r], b[c], -p);
+                const float h = __fadd_rn(hi[r][c], p);
+                const float pl = __fsub_rn(p, __fsub_rn(h, hi[r][c]));
+                hi[r][c] = h;
+                lo[r][c] = __fadd_rn(lo[r][c], __fadd_rn(pl, e));
+            }
     }
+#pragma unroll
+    for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+        for (int c = 0; c < TL::CT; c++) {
+            const ff v = two_sum(__fsub_rn(hi[r][c], Cq), lo[r][c]);
+            acc[r][c] = FF{v.hi, v.lo};
+        }
+}
+
+// Cq of tile_fma_ff for this sigma2.
+__device__ __forceinline__ float split_constant(double sigma2)
+{
+    int E;
+    frexp(sigma2, &E); // sigma2 < 2^E
+    return ldexpf(1.5f, E + 2);
 }
 
 // The remainder C(P, Q) - sum_k What^k(P) What^k(Q)' of one RP-column block
@@ -245,21 +284,17 @@ __device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile
 // and the products exact: the prior evaluates it at knots and the leaf basis
 // at observations, and the two must agree far below FP32 relative to sigma2
 // where the remainder is small (deep levels, long ranges).  P coordinates at
-// pp[a], pp[ldp + a] (nP valid rows), Q at pq[j], pq[RP + j] (R valid); the
+// pp[a], pp[ldp + a] (nP valid rows), Q at pq[j], pq[RP + j] (R valid); sigma2
+// and 1/beta as float pairs (s2f, ibf); the
 // result is rounded to FP32.  Returns the float-pair value of entry (a, j).
 template <int ROWS, int RP>
 __device__ __forceinline__ void remainder_ff(float (&out)[Tile<ROWS, RP>::RT][Tile<ROWS, RP>::CT], const float *Ak,
                                              int lda, const float *Bk, int K, const float *pp, int ldp, int nP,
-                                             const float *pq, int R, const double *th)
+                                             const float *pq, int R, ff s2f, ff ibf, float Cq)
 {
     using TL = Tile<ROWS, RP>;
     FF fa[TL::RT][TL::CT];
-#pragma unroll
-    for (int r = 0; r < TL::RT; r++)
-#pragma unroll
-        for (int c = 0; c < TL::CT; c++) fa[r][c] = FF{0.f, 0.f};
-    tile_fma_ff<ROWS, RP>(fa, Ak, lda, Bk, RP, K);
-    const ff s2f = ff_from_double(th[0]), ibf = ff_from_double(1.0 / th[1]);
+    tile_fma_ff<ROWS, RP>(fa, Ak, lda, Bk, RP, K, Cq);
     const int r0 = TL::r0(), c0 = TL::c0();
 #pragma unroll
     for (int r = 0; r < TL::RT; r++)
@@ -774,6 +809,12 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
     const CovP<T> cp(th);
+    __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
+    const float s_cq = split_constant(th[0]);
+    if (threadIdx.x == 0) {
+        s_par[0] = ff_from_double(th[0]);
+        s_par[1] = ff_from_double(1.0 / th[1]);
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     F *sL = (F *)smem_raw;                  // RP x (RP+1)
     F *srs = sL + RP * (RP + 1);            // RP + 2
@@ -822,7 +863,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
         bool done = false;
         if constexpr (sizeof(T) == 4) {
             if (w.exact_rem) {
-                remainder_ff<RP, RP>(acc, sU, RP, sB, (l - 1) * RP, sq, RP, R, sa, R, th);
+                remainder_ff<RP, RP>(acc, sU, RP, sB, (l - 1) * RP, sq, RP, R, sa, R, s_par[0], s_par[1], s_cq);
 #pragma unroll
                 for (int r = 0; r < TL::RT; r++)
 #pragma unroll
@@ -864,12 +905,8 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
         if (w.exact_rem) {
             // W^m in float pairs straight into the factorization
             FF fa[TL::RT][TL::CT];
-#pragma unroll
-            for (int r = 0; r < TL::RT; r++)
-#pragma unroll
-                for (int c = 0; c < TL::CT; c++) fa[r][c] = FF{0.f, 0.f};
-            tile_fma_ff<RP, RP>(fa, sU, RP, sU, RP, (m - 1) * RP);
-            const ff s2f = ff_from_double(th[0]), ibf = ff_from_double(1.0 / th[1]);
+            tile_fma_ff<RP, RP>(fa, sU, RP, sU, RP, (m - 1) * RP, s_cq);
+            const ff s2f = s_par[0], ibf = s_par[1];
 #pragma unroll
             for (int r = 0; r < TL::RT; r++)
 #pragma unroll
@@ -947,6 +984,12 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
     const CovP<T> cp(th);
+    __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
+    const float s_cq = split_constant(th[0]);
+    if (threadIdx.x == 0) {
+        s_par[0] = ff_from_double(th[0]);
+        s_par[1] = ff_from_double(1.0 / th[1]);
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = t.M, R = t.R, P = ch.parent, nr = ch.n;
     T *sp = (T *)smem_raw;                  // 2 CH rows relative to the ancestor corner
@@ -994,7 +1037,7 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
         bool done = false;
         if constexpr (sizeof(T) == 4) {
             if (w.exact_rem) {
-                remainder_ff<CH, RP>(acc, sU, LDC, sB, (l - 1) * RP, sp, CH, nr, sa, R, th);
+                remainder_ff<CH, RP>(acc, sU, LDC, sB, (l - 1) * RP, sp, CH, nr, sa, R, s_par[0], s_par[1], s_cq);
 #pragma unroll
                 for (int r = 0; r < TL::RT; r++)
 #pragma unroll
