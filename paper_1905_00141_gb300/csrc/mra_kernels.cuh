@@ -224,14 +224,14 @@ __device__ __forceinline__ void ff_merge(FF &s, const FF &o)
 // acc[r][c] = sum_t A[t][r0 + r] * B[t][c0 + c] for rows of whitened basis
 // functions.  Since sum_k |What^k(x)|^2 <= C(x, x) = sigma2 (Sec. 1.1: the
 // remainder covariance stays positive), Cauchy-Schwarz bounds sum_t |a_t b_t|
-// by sigma2 < 2^E (E: binary exponent of sigma2).  Every product is split
-// exactly (TwoProd) into p + e.  The high sum H starts at Cq = 1.5 * 2^(E + 2)
-// and stays inside [2^(E + 2), 2^(E + 3)), where the FP32 grid is
-// delta = 2^(E - 21): H + p rounds p onto that grid, and since |H| > |p| the
-// part left over, p - ((H + p) - H), is exact (Fast2Sum) and below delta / 2.
-// That part plus e goes into a second FP32 sum whose rounding is
-// ~2^-24 * K * delta, near 1e-11 sigma2.  Seven FP32 operations a product
-// instead of the ten of a float-pair TwoSum accumulation.
+// by sigma2 < 2^E (E: binary exponent of sigma2).  The high sum H starts at
+// Cq = 1.5 * 2^(E + 2) and stays inside [2^(E + 2), 2^(E + 3)), where the FP32
+// grid is delta = 2^(E - 21).  h = fma(a, b, H) adds the product rounded onto
+// that grid; t = h - H is exact (same binade), and fma(a, b, -t) returns the
+// part of the product left over, |.| <= delta / 2, to within 2^-24 of itself.
+// Those parts go into a second FP32 sum whose rounding is ~2^-24 * K * delta,
+// near 1e-11 sigma2.  Four FP32 operations a product instead of the ten of a
+// float-pair TwoSum accumulation of TwoProd products.
 template <int ROWS, int COLS>
 __device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile<ROWS, COLS>::CT], const float *A,
                                             int lda, const float *B, int ldb, int K, float Cq)
@@ -254,12 +254,10 @@ __device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile
         for (int r = 0; r < TL::RT; r++)
 #pragma unroll
             for (int c = 0; c < TL::CT; c++) {
-                const float p = __fmul_rn(a[r], b[c]);
-                const float e = __fmaf_rn(a[r], b[c], -p);
-                const float h = __fadd_rn(hi[r][c], p);
-                const float pl = __fsub_rn(p, __fsub_rn(h, hi[r][c]));
+                const float h = __fmaf_rn(a[r], b[c], hi[r][c]);
+                const float pl = __fmaf_rn(a[r], b[c], -__fsub_rn(h, hi[r][c]));
                 hi[r][c] = h;
-                lo[r][c] = __fadd_rn(lo[r][c], __fadd_rn(pl, e));
+                lo[r][c] = __fadd_rn(lo[r][c], pl);
             }
     }
 #pragma unroll
