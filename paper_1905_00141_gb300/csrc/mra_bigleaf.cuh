@@ -62,28 +62,6 @@ __device__ __forceinline__ BigView<typename FacT<T>::type> big_view(const DevTre
     return v;
 }
 
-// Exact products of float pairs for the trailing update: sum_m a_m b_m with
-// a = ah + al, b = bh + bl, as TwoProd/TwoSum of ah bh plus FP32 sums of
-// ah bl + al bh (the al bl terms are below double-float precision).
-struct FFAcc {
-    FF s;
-    float cross;
-};
-__device__ __forceinline__ void ffacc_zero(FFAcc &a)
-{
-    a.s = FF{0.f, 0.f};
-    a.cross = 0.f;
-}
-__device__ __forceinline__ void ffacc_add(FFAcc &a, ff x, ff y)
-{
-    ff_add_prod(a.s, x.hi, y.hi);
-    a.cross = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, a.cross));
-}
-__device__ __forceinline__ ff ffacc_value(const FFAcc &a)
-{
-    return fast_two_sum(a.s.hi, __fadd_rn(a.s.lo, a.cross));
-}
-
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_big_assemble_bytes(int M)
 {
@@ -137,7 +115,7 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
     const int a0 = 2 * (tid / (TB / 2)), q0 = 2 * (tid % (TB / 2));
     T hi[2][2], lo[2][2];
     dot2x2_exact(sUI + a0 * LDU, sUI + min(a0 + 1, TB - 1) * LDU, sUJ + q0 * LDU, sUJ + min(q0 + 1, TB - 1) * LDU, UC,
-                 hi, lo);
+                 split_constant(th[0]), hi, lo);
     const ff s2f = ff_from_double(th[0]), ibf = ff_from_double(ib64), tau2f = ff_from_double(tau2);
 #pragma unroll
     for (int i = 0; i < 2; i++)
@@ -374,25 +352,56 @@ __global__ void __launch_bounds__(NT) k_big_update(DevTree t, Work<T> w, const B
     }
     __syncthreads();
     const int a0 = 2 * (tid / (TB / 2)), q0 = 2 * (tid % (TB / 2));
+    F sum[2][2];
+    if constexpr (sizeof(T) == 4) {
+        // Rows of L satisfy sum_m L_am^2 = V_aa <= sigma2 + tau2, so every
+        // partial sum of |L_am L_qm| stays below sigma2 + tau2
+        // (Cauchy-Schwarz): the leading products go through the grid
+        // accumulation (see tile_fma_ff), the cross terms through FP32 FMAs.
+        const float Cq = split_constant(th[0] + th[2]);
+        float hs[2][2], ls[2][2];
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                hs[i][j] = Cq;
+                ls[i][j] = 0.f;
+            }
+        for (int m = 0; m < nk; m++) {
+            const ff x[2] = {sLi[a0 * (TB + 1) + m], sLi[(a0 + 1) * (TB + 1) + m]};
+            const ff y[2] = {sLj[q0 * (TB + 1) + m], sLj[(q0 + 1) * (TB + 1) + m]};
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const float h = __fmaf_rn(x[i].hi, y[j].hi, hs[i][j]);
+                    const float pl = __fmaf_rn(x[i].hi, y[j].hi, -__fsub_rn(h, hs[i][j]));
+                    hs[i][j] = h;
+                    ls[i][j] = __fmaf_rn(x[i].hi, y[j].lo, __fmaf_rn(x[i].lo, y[j].hi, __fadd_rn(ls[i][j], pl)));
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) sum[i][j] = two_sum(__fsub_rn(hs[i][j], Cq), ls[i][j]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                double acc = 0.0;
+                for (int m = 0; m < nk; m++) acc = fma(sLi[(a0 + i) * (TB + 1) + m], sLj[(q0 + j) * (TB + 1) + m], acc);
+                sum[i][j] = acc;
+            }
+    }
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
         for (int j = 0; j < 2; j++) {
             const int a = a0 + i, q = q0 + j;
-            F sum;
-            if constexpr (sizeof(T) == 4) {
-                FFAcc acc;
-                ffacc_zero(acc);
-                for (int m = 0; m < nk; m++) ffacc_add(acc, sLi[a * (TB + 1) + m], sLj[q * (TB + 1) + m]);
-                sum = ffacc_value(acc);
-            } else {
-                double acc = 0.0;
-                for (int m = 0; m < nk; m++) acc = fma(sLi[a * (TB + 1) + m], sLj[q * (TB + 1) + m], acc);
-                sum = acc;
-            }
             if (a < ni && q < nj && (it.i != it.j || q <= a)) {
                 F *p = v.V + (size_t)(ri + a) * n + rj + q;
-                *p = f_sub(*p, sum);
+                *p = f_sub(*p, sum[i][j]);
             }
         }
 }

@@ -269,11 +269,12 @@ __device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile
         }
 }
 
-// Cq of tile_fma_ff for this sigma2.
-__device__ __forceinline__ float split_constant(double sigma2)
+// Cq of the grid accumulation for sums of products whose absolute values
+// add up to less than bound.
+__device__ __forceinline__ float split_constant(double bound)
 {
     int E;
-    frexp(sigma2, &E); // sigma2 < 2^E
+    frexp(bound, &E); // bound < 2^E
     return ldexpf(1.5f, E + 2);
 }
 
@@ -376,38 +377,44 @@ __device__ __forceinline__ void dot2x2(const float *a0, const float *a1, const f
             lo[i][j] = __fsub_rn(s[i][j].lo, __fsub_rn(t, s[i][j].hi));
         }
 }
-// As dot2x2 with every product exact (TwoProd) and the running sums kept as
-// float pairs (TwoSum): the float-float product sum of the FP32 operands,
-// for leaves whose covariance loses many digits to cancellation (tight
-// clusters of observations).
+// As dot2x2 to float-float accuracy, for leaves whose covariance loses many
+// digits to cancellation (tight clusters of observations): the rows are
+// whitened basis rows, so every partial sum of |products| is below sigma2 and
+// the grid accumulation of tile_fma_ff applies (Cq = split_constant(sigma2)).
 __device__ __forceinline__ void dot2x2_exact(const float *a0, const float *a1, const float *q0, const float *q1,
-                                             int K, float (&hi)[2][2], float (&lo)[2][2])
+                                             int K, float Cq, float (&hi)[2][2], float (&lo)[2][2])
 {
-    FF s[2][2];
+    float hs[2][2], ls[2][2];
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
-        for (int j = 0; j < 2; j++) s[i][j] = FF{0.f, 0.f};
+        for (int j = 0; j < 2; j++) {
+            hs[i][j] = Cq;
+            ls[i][j] = 0.f;
+        }
     for (int k = 0; k < K; k += 4) {
-        const float4 x[2] = {*(const float4 *)(a0 + k), *(const float4 *)(a1 + k)};
-        const float4 y[2] = {*(const float4 *)(q0 + k), *(const float4 *)(q1 + k)};
+        const float4 x4[2] = {*(const float4 *)(a0 + k), *(const float4 *)(a1 + k)};
+        const float4 y4[2] = {*(const float4 *)(q0 + k), *(const float4 *)(q1 + k)};
 #pragma unroll
-        for (int i = 0; i < 2; i++)
+        for (int e = 0; e < 4; e++) {
+            const float x[2] = {(&x4[0].x)[e], (&x4[1].x)[e]}, y[2] = {(&y4[0].x)[e], (&y4[1].x)[e]};
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
-                ff_add_prod(s[i][j], x[i].x, y[j].x);
-                ff_add_prod(s[i][j], x[i].y, y[j].y);
-                ff_add_prod(s[i][j], x[i].z, y[j].z);
-                ff_add_prod(s[i][j], x[i].w, y[j].w);
-            }
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const float h = __fmaf_rn(x[i], y[j], hs[i][j]);
+                    ls[i][j] = __fadd_rn(ls[i][j], __fmaf_rn(x[i], y[j], -__fsub_rn(h, hs[i][j])));
+                    hs[i][j] = h;
+                }
+        }
     }
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
         for (int j = 0; j < 2; j++) {
-            const float t = __fadd_rn(s[i][j].hi, s[i][j].lo);
-            hi[i][j] = t;
-            lo[i][j] = __fsub_rn(s[i][j].lo, __fsub_rn(t, s[i][j].hi));
+            const ff v = two_sum(__fsub_rn(hs[i][j], Cq), ls[i][j]);
+            hi[i][j] = v.hi;
+            lo[i][j] = v.lo;
         }
 }
 __device__ __forceinline__ void dot2x2(const double *a0, const double *a1, const double *q0, const double *q1, int K,
@@ -430,7 +437,7 @@ __device__ __forceinline__ void dot2x2(const double *a0, const double *a1, const
         }
 }
 __device__ __forceinline__ void dot2x2_exact(const double *a0, const double *a1, const double *q0, const double *q1,
-                                             int K, double (&hi)[2][2], double (&lo)[2][2])
+                                             int K, float, double (&hi)[2][2], double (&lo)[2][2])
 {
     dot2x2(a0, a1, q0, q1, K, hi, lo);
 }
