@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
     const int a0 = 2 * (tid / (TB / 2)), q0 = 2 * (tid % (TB / 2));
     T hi[2][2], lo[2][2];
     dot2x2_exact(sUI + a0 * LDU, sUI + min(a0 + 1, TB - 1) * LDU, sUJ + q0 * LDU, sUJ + min(q0 + 1, TB - 1) * LDU, UC,
-                 split_constant(th[0]), hi, lo);
+                 grid_constant(th[0]), hi, lo);
     const ff s2f = ff_from_double(th[0]), ibf = ff_from_double(ib64), tau2f = ff_from_double(tau2);
 #pragma unroll
     for (int i = 0; i < 2; i++)
@@ -356,34 +356,25 @@ __global__ void __launch_bounds__(NT) k_big_update(DevTree t, Work<T> w, const B
     if constexpr (sizeof(T) == 4) {
         // Rows of L satisfy sum_m L_am^2 = V_aa <= sigma2 + tau2, so every
         // partial sum of |L_am L_qm| stays below sigma2 + tau2
-        // (Cauchy-Schwarz): the leading products go through the grid
-        // accumulation (see tile_fma_ff), the cross terms through FP32 FMAs.
-        const float Cq = split_constant(th[0] + th[2]);
-        float hs[2][2], ls[2][2];
+        // (Cauchy-Schwarz): grid accumulation of ff_math.h.
+        const float Cq = grid_constant(th[0] + th[2]);
+        grid_acc g[2][2];
 #pragma unroll
         for (int i = 0; i < 2; i++)
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
-                hs[i][j] = Cq;
-                ls[i][j] = 0.f;
-            }
+            for (int j = 0; j < 2; j++) grid_init(g[i][j], Cq);
         for (int m = 0; m < nk; m++) {
             const ff x[2] = {sLi[a0 * (TB + 1) + m], sLi[(a0 + 1) * (TB + 1) + m]};
             const ff y[2] = {sLj[q0 * (TB + 1) + m], sLj[(q0 + 1) * (TB + 1) + m]};
 #pragma unroll
             for (int i = 0; i < 2; i++)
 #pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    const float h = __fmaf_rn(x[i].hi, y[j].hi, hs[i][j]);
-                    const float pl = __fmaf_rn(x[i].hi, y[j].hi, -__fsub_rn(h, hs[i][j]));
-                    hs[i][j] = h;
-                    ls[i][j] = __fmaf_rn(x[i].hi, y[j].lo, __fmaf_rn(x[i].lo, y[j].hi, __fadd_rn(ls[i][j], pl)));
-                }
+                for (int j = 0; j < 2; j++) grid_add(g[i][j], x[i], y[j]);
         }
 #pragma unroll
         for (int i = 0; i < 2; i++)
 #pragma unroll
-            for (int j = 0; j < 2; j++) sum[i][j] = two_sum(__fsub_rn(hs[i][j], Cq), ls[i][j]);
+            for (int j = 0; j < 2; j++) sum[i][j] = grid_value(g[i][j], Cq);
     } else {
 #pragma unroll
         for (int i = 0; i < 2; i++)

@@ -222,30 +222,23 @@ __device__ __forceinline__ void ff_merge(FF &s, const FF &o)
     s.lo = __fadd_rn(s.lo, o.lo);
 }
 // acc[r][c] = sum_t A[t][r0 + r] * B[t][c0 + c] for rows of whitened basis
-// functions.  Since sum_k |What^k(x)|^2 <= C(x, x) = sigma2 (Sec. 1.1: the
-// remainder covariance stays positive), Cauchy-Schwarz bounds sum_t |a_t b_t|
-// by sigma2 < 2^E (E: binary exponent of sigma2).  The high sum H starts at
-// Cq = 1.5 * 2^(E + 2) and stays inside [2^(E + 2), 2^(E + 3)), where the FP32
-// grid is delta = 2^(E - 21).  h = fma(a, b, H) adds the product rounded onto
-// that grid; t = h - H is exact (same binade), and fma(a, b, -t) returns the
-// part of the product left over, |.| <= delta / 2, to within 2^-24 of itself.
-// Those parts go into a second FP32 sum whose rounding is ~2^-24 * K * delta,
-// near 1e-11 sigma2.  Four FP32 operations a product instead of the ten of a
-// float-pair TwoSum accumulation of TwoProd products.
+// functions, to an absolute error near 1e-11 sigma2.  Since
+// sum_k |What^k(x)|^2 <= C(x, x) = sigma2 (Sec. 1.1: the remainder covariance
+// stays positive), Cauchy-Schwarz bounds every partial sum of |a_t b_t| by
+// sigma2, so the grid accumulation of ff_math.h applies with
+// Cq = grid_constant(sigma2): four FP32 operations a product instead of the
+// ten of a float-pair TwoSum accumulation of TwoProd products.
 template <int ROWS, int COLS>
 __device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile<ROWS, COLS>::CT], const float *A,
                                             int lda, const float *B, int ldb, int K, float Cq)
 {
     using TL = Tile<ROWS, COLS>;
     const int r0 = TL::r0(), c0 = TL::c0();
-    float hi[TL::RT][TL::CT], lo[TL::RT][TL::CT];
+    grid_acc g[TL::RT][TL::CT];
 #pragma unroll
     for (int r = 0; r < TL::RT; r++)
 #pragma unroll
-        for (int c = 0; c < TL::CT; c++) {
-            hi[r][c] = Cq;
-            lo[r][c] = 0.f;
-        }
+        for (int c = 0; c < TL::CT; c++) grid_init(g[r][c], Cq);
     for (int t = 0; t < K; t++) {
         float a[TL::RT], b[TL::CT];
         ldv<float, TL::RT>(a, A + t * lda + r0);
@@ -253,39 +246,26 @@ __device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile
 #pragma unroll
         for (int r = 0; r < TL::RT; r++)
 #pragma unroll
-            for (int c = 0; c < TL::CT; c++) {
-                const float h = __fmaf_rn(a[r], b[c], hi[r][c]);
-                const float pl = __fmaf_rn(a[r], b[c], -__fsub_rn(h, hi[r][c]));
-                hi[r][c] = h;
-                lo[r][c] = __fadd_rn(lo[r][c], pl);
-            }
+            for (int c = 0; c < TL::CT; c++) grid_add(g[r][c], a[r], b[c]);
     }
 #pragma unroll
     for (int r = 0; r < TL::RT; r++)
 #pragma unroll
         for (int c = 0; c < TL::CT; c++) {
-            const ff v = two_sum(__fsub_rn(hi[r][c], Cq), lo[r][c]);
+            const ff v = grid_value(g[r][c], Cq);
             acc[r][c] = FF{v.hi, v.lo};
         }
 }
 
-// Cq of the grid accumulation for sums of products whose absolute values
-// add up to less than bound.
-__device__ __forceinline__ float split_constant(double bound)
-{
-    int E;
-    frexp(bound, &E); // bound < 2^E
-    return ldexpf(1.5f, E + 2);
-}
-
 // The remainder C(P, Q) - sum_k What^k(P) What^k(Q)' of one RP-column block
 // (Sec. 1.1 recursion) for FP32 storage, with the covariance in float pairs
-// and the products exact: the prior evaluates it at knots and the leaf basis
-// at observations, and the two must agree far below FP32 relative to sigma2
-// where the remainder is small (deep levels, long ranges).  P coordinates at
-// pp[a], pp[ldp + a] (nP valid rows), Q at pq[j], pq[RP + j] (R valid); sigma2
-// and 1/beta as float pairs (s2f, ibf); the
-// result is rounded to FP32.  Returns the float-pair value of entry (a, j).
+// and the product sum to ~1e-11 sigma2 (tile_fma_ff): the prior evaluates it
+// at knots and the leaf basis at observations, and the two must agree far
+// below FP32 relative to sigma2 where the remainder is small (deep levels,
+// long ranges).  P coordinates at pp[a], pp[ldp + a] (nP valid rows), Q at
+// pq[j], pq[RP + j] (R valid); sigma2 and 1/beta as float pairs (s2f, ibf),
+// Cq = grid_constant(sigma2).  out[r][c] is entry (r0 + r, c0 + c) rounded to
+// FP32.
 template <int ROWS, int RP>
 __device__ __forceinline__ void remainder_ff(float (&out)[Tile<ROWS, RP>::RT][Tile<ROWS, RP>::CT], const float *Ak,
                                              int lda, const float *Bk, int K, const float *pp, int ldp, int nP,
@@ -380,18 +360,15 @@ __device__ __forceinline__ void dot2x2(const float *a0, const float *a1, const f
 // As dot2x2 to float-float accuracy, for leaves whose covariance loses many
 // digits to cancellation (tight clusters of observations): the rows are
 // whitened basis rows, so every partial sum of |products| is below sigma2 and
-// the grid accumulation of tile_fma_ff applies (Cq = split_constant(sigma2)).
+// the grid accumulation of ff_math.h applies (Cq = grid_constant(sigma2)).
 __device__ __forceinline__ void dot2x2_exact(const float *a0, const float *a1, const float *q0, const float *q1,
                                              int K, float Cq, float (&hi)[2][2], float (&lo)[2][2])
 {
-    float hs[2][2], ls[2][2];
+    grid_acc g[2][2];
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
-        for (int j = 0; j < 2; j++) {
-            hs[i][j] = Cq;
-            ls[i][j] = 0.f;
-        }
+        for (int j = 0; j < 2; j++) grid_init(g[i][j], Cq);
     for (int k = 0; k < K; k += 4) {
         const float4 x4[2] = {*(const float4 *)(a0 + k), *(const float4 *)(a1 + k)};
         const float4 y4[2] = {*(const float4 *)(q0 + k), *(const float4 *)(q1 + k)};
@@ -401,18 +378,14 @@ __device__ __forceinline__ void dot2x2_exact(const float *a0, const float *a1, c
 #pragma unroll
             for (int i = 0; i < 2; i++)
 #pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    const float h = __fmaf_rn(x[i], y[j], hs[i][j]);
-                    ls[i][j] = __fadd_rn(ls[i][j], __fmaf_rn(x[i], y[j], -__fsub_rn(h, hs[i][j])));
-                    hs[i][j] = h;
-                }
+                for (int j = 0; j < 2; j++) grid_add(g[i][j], x[i], y[j]);
         }
     }
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
         for (int j = 0; j < 2; j++) {
-            const ff v = two_sum(__fsub_rn(hs[i][j], Cq), ls[i][j]);
+            const ff v = grid_value(g[i][j], Cq);
             hi[i][j] = v.hi;
             lo[i][j] = v.lo;
         }
@@ -473,6 +446,9 @@ __device__ __forceinline__ double f_mul(double a, double b) { return a * b; }
 __device__ __forceinline__ ff f_mul(ff a, ff b) { return ff_mul(a, b); }
 __device__ __forceinline__ double f_sub(double a, double b) { return a - b; }
 __device__ __forceinline__ ff f_sub(ff a, ff b) { return ff_sub(a, b); }
+// the subtraction of a factorisation update (absolute accuracy suffices)
+__device__ __forceinline__ double f_sub_upd(double a, double b) { return a - b; }
+__device__ __forceinline__ ff f_sub_upd(ff a, ff b) { return ff_sub_sloppy(a, b); }
 __device__ __forceinline__ double f_add(double a, double b) { return a + b; }
 __device__ __forceinline__ ff f_add(ff a, ff b) { return ff_add(a, b); }
 __device__ __forceinline__ double f_sqr(double a) { return a * a; }
@@ -561,7 +537,7 @@ static __device__ void chol_small(F *A, int lda, int n, F *rs, F *r2s, int *fail
         for (int s = 0; s < S; s++) {
             const int i = pi[s], k = pk[s];
             if (k > j) {
-                F v = f_sub(val[s], f_mul(f_mul(A[i * lda + j], A[k * lda + j]), r2));
+                F v = f_sub_upd(val[s], f_mul(f_mul(A[i * lda + j], A[k * lda + j]), r2));
                 if (k == j + 1) {
                     if (i == k) {
                         if (!((double)f_hi(v) > tol)) {
@@ -815,7 +791,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     if (!theta_ok(th)) return;
     const CovP<T> cp(th);
     __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
-    const float s_cq = split_constant(th[0]);
+    const float s_cq = grid_constant(th[0]);
     if (threadIdx.x == 0) {
         s_par[0] = ff_from_double(th[0]);
         s_par[1] = ff_from_double(1.0 / th[1]);
@@ -990,7 +966,7 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
     if (!theta_ok(th)) return;
     const CovP<T> cp(th);
     __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
-    const float s_cq = split_constant(th[0]);
+    const float s_cq = grid_constant(th[0]);
     if (threadIdx.x == 0) {
         s_par[0] = ff_from_double(th[0]);
         s_par[1] = ff_from_double(1.0 / th[1]);
@@ -1212,14 +1188,17 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
     chol_small<F, (tri_count(NMAX) + NT - 1) / NT>(sV, LDV, n, srs, sr2, flag, MRA_SINGULAR);
     const double dv = logdet_small(sV, LDV, n, red);
     trinv_warp<T, NMAX>(sV, LDV, srs, sLi, nmax, n);
-    // Y = L^{-1} U, block column by block column, straight to global
+    // Y = L^{-1} U, block column by block column, straight to global; row r
+    // of L^{-1} ends at column r, so a thread's rows r0 .. r0 + RT - 1 stop
+    // the sum there (the terms skipped are exact zeros)
     {
         using TL = Tile<NMAX, RP>;
         const int r0 = TL::r0(), c0 = TL::c0();
+        const int kend = min(n, r0 + TL::RT);
         for (int cb = 0; cb < UC; cb += RP) {
             T acc[TL::RT][TL::CT];
             tile_zero(acc);
-            tile_fma<T, NMAX, RP>(acc, sLi, nmax, sU + cb, LDU, n);
+            tile_fma<T, NMAX, RP>(acc, sLi, nmax, sU + cb, LDU, kend);
 #pragma unroll
             for (int r = 0; r < TL::RT; r++)
                 if (r0 + r < n)
