@@ -193,6 +193,30 @@ mra_status mra_region_terms(mra_ctx *ctx, const double *theta, double *d, double
                             double *logdetW, double *loglik);
 
 /*
+ * mra_predict -- posterior prediction of the latent process at new locations
+ *   (the prediction mode of the paper's program, Sec. 2.2; the model of
+ *   Sec. 1.1): mean[k] = E[y(s_k) | z] and var[k] = Var[y(s_k) | z] for the
+ *   MRA covariance at theta (host, 3 doubles), i.e. kriging with Sigma_MRA.
+ *   The variance is that of the process without the nugget; add theta[2] for
+ *   a new observation.
+ *   px, py: host, np locations each; mean, var: host, np doubles each.
+ *   Points outside the partition's domain (the bounding box of the data
+ *   extended by 1% at the top and right) get NaN in both outputs.
+ *   Runs one likelihood pass at theta that keeps the upward pass's factors,
+ *   the top-down pass for the posterior means of the basis weights, the
+ *   basis functions at the points, then one warp per point, all in the
+ *   context's precision for the pass and FP64 for the prediction
+ *   arithmetic.  Temporary device memory: about
+ *   8 (n_nonleaf (r^2 + 2 r + (M-2) r^2) + n_leaves 64 (65)) bytes plus
+ *   (M-1) r + 40 bytes per point.
+ *   Errors: EINVAL (null pointer, np < 0, theta not finite and positive),
+ *   ENOMEM, ENOTPD (a factor not positive definite at theta), ECUDA.
+ *   Synchronous.
+ */
+mra_status mra_predict(mra_ctx *ctx, const double *theta, const double *px, const double *py, int64_t np,
+                       double *mean, double *var);
+
+/*
  * mra_profile -- enable (1) or disable (0) per-kernel device timing: every
  *   later launch is bracketed by two CUDA events recorded on the call's
  *   stream.  Enabling clears the records.  Costs two event records per launch.

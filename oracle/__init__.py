@@ -10,8 +10,13 @@ Two independent references live here:
   likelihood recursion derived from the remainder covariances of Sec. 1.1
   (prior W/K blocks, leaf posterior, Woodbury upward pass, root), plain FP64.
 * ``dense.py``: a brute-force dense Sigma_MRA built pair by pair from the
-  C_m recursion of Sec. 1.1, then the textbook Gaussian log-density.  It has
-  its own tree code and is only meant for tiny inputs.
+  C_m recursion of Sec. 1.1, then the textbook Gaussian log-density, and
+  kriging with it (posterior predictive mean and variance at new points).
+  It has its own tree code and is only meant for tiny inputs.
+* ``predict_by_loglik``: the posterior predictive at one point from three
+  likelihood evaluations of the recursion oracle with the point added as an
+  observation, l(S + {s*: z*}) - l(S) = log N(z*; mean, var + tau2): an
+  independent route to the prediction at any data size.
 * ``mlp.py``: the surrogate network (an addition to the paper's method: a
   3 -> 64 -> 64 -> 1 SiLU perceptron of loglik/n over log theta) in FP64
   numpy -- BF16 rounding of the parameters, forward pass, hand-derived
@@ -180,3 +185,32 @@ def loglik(x, y, z, M, J, r, theta, offset=np.e / 100.0, dedup=False, nthreads: 
         return t.loglik(theta, nthreads)
     finally:
         t.close()
+
+
+def predict_by_loglik(x, y, z, M, J, r, theta, px, py, scale=1.0, nthreads: int = 0):
+    """Posterior predictive mean and variance of the latent process at
+    (px, py) through the Gaussian conditional density: with the point added
+    as an observation of value t, D(t) = l(S + {s*: t}) - l(S) is
+    -1/2 log(2 pi s) - (t - mean)^2 / (2 s), s = var + tau2, so three values
+    t in {-h, 0, h} give s = -h^2 / (D(h) + D(-h) - 2 D(0)) and
+    mean = s (D(h) - D(-h)) / (2 h).  The point must lie strictly inside the
+    bounding box of the data (the tree stays the same) and off every knot."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    th = np.asarray(theta, dtype=np.float64).reshape(1, 3)
+    if not (x.min() < px < x.max() and y.min() < py < y.max()):
+        raise ValueError("the point must lie strictly inside the data's bounding box")
+    base, st = loglik(x, y, z, M, J, r, th, nthreads=nthreads)
+    if st != OK:
+        raise OracleError(st)
+    h = float(scale)
+    D = []
+    for t in (-h, 0.0, h):
+        v, st = loglik(np.append(x, px), np.append(y, py), np.append(z, t), M, J, r, th, nthreads=nthreads)
+        if st != OK:
+            raise OracleError(st)
+        D.append(float(v[0] - base[0]))
+    s = -h * h / (D[2] + D[0] - 2.0 * D[1])
+    mean = s * (D[2] - D[0]) / (2.0 * h)
+    return mean, s - float(th[0, 2])

@@ -118,9 +118,10 @@ class Partition:
         return out
 
 
-def sigma_mra(part: Partition, sigma2: float, beta: float, return_all: bool = False):
+def sigma_mra(part: Partition, sigma2: float, beta: float, return_all: bool = False, extra=None):
     """Dense Sigma_MRA over the observations (and, with return_all, over the
-    point set Z = observations + knots, with the knot bookkeeping)."""
+    point set Z = observations + knots (+ the extra points, last), with the
+    knot bookkeeping).  Extra points must lie inside the root region."""
     M = part.M
     zx = [part.x]
     zy = [part.y]
@@ -134,6 +135,9 @@ def sigma_mra(part: Partition, sigma2: float, beta: float, return_all: bool = Fa
             zy.append(ky)
             base += len(kx)
         knot_ids.append(ids)
+    if extra is not None:
+        zx.append(np.asarray(extra[0], dtype=np.float64))
+        zy.append(np.asarray(extra[1], dtype=np.float64))
     X = np.concatenate(zx)
     Y = np.concatenate(zy)
     reg = [part.region_of(X, Y, m) for m in range(M)]
@@ -172,3 +176,31 @@ def loglik(x, y, z, M, J, r, theta, f=math.e / 100.0, dedup=False) -> float:
     part = Partition(x, y, z, M, J, r, f, dedup)
     S = sigma_mra(part, sigma2, beta)
     return gauss_loglik(S + tau2 * np.eye(len(part.z)), part.z)
+
+
+def predict(x, y, z, M, J, r, theta, px, py, f=math.e / 100.0, dedup=False):
+    """Kriging with Sigma_MRA (the plain definition of the MRA posterior
+    predictive of the latent process, Sec. 1.1 model):
+        mean = Sigma(P, S) (Sigma(S, S) + tau2 I)^{-1} z,
+        var  = diag Sigma(P, P) - diag Sigma(P, S) (Sigma(S, S) + tau2 I)^{-1} Sigma(S, P).
+    Points outside the root region give NaN."""
+    sigma2, beta, tau2 = [float(v) for v in theta]
+    part = Partition(x, y, z, M, J, r, f, dedup)
+    px = np.asarray(px, dtype=np.float64)
+    py = np.asarray(py, dtype=np.float64)
+    x0, x1, y0, y1 = part.levels[0][0]
+    inside = (px >= x0) & (px < x1) & (py >= y0) & (py < y1)
+    mean = np.full(len(px), np.nan)
+    var = np.full(len(px), np.nan)
+    if not inside.any():
+        return mean, var
+    Sig, info = sigma_mra(part, sigma2, beta, return_all=True, extra=(px[inside], py[inside]))
+    n = info["n_obs"]
+    P = np.arange(len(Sig) - int(inside.sum()), len(Sig))
+    K = Sig[:n, :n] + tau2 * np.eye(n)
+    L = np.linalg.cholesky(K)
+    A = np.linalg.solve(L, Sig[:n][:, P])          # L^{-1} Sigma(S, P)
+    w = np.linalg.solve(L, part.z)                 # L^{-1} z
+    mean[inside] = A.T @ w
+    var[inside] = np.diag(Sig[np.ix_(P, P)]) - np.sum(A * A, axis=0)
+    return mean, var

@@ -3,4 +3,6 @@
 namespace mra {
 MRA_INSTANTIATE(double, 16)
 MRA_INSTANTIATE(double, 32)
+MRA_INSTANTIATE_DOWN(16)
+MRA_INSTANTIATE_DOWN(32)
 } // namespace mra

@@ -323,6 +323,11 @@ struct mra_ctx {
     int launches_last = 0;
     int64_t max_leaf = 0, empty_leaves = 0;
     double flops = 0.0, covs = 0.0;
+    // set only while mra_predict runs its pass: where the kernels keep the
+    // factors prediction needs (Work::keep_*)
+    double *keep_up = nullptr, *keep_y = nullptr;
+    void *keep_li = nullptr;
+    size_t keep_stride = 0;
     double flops_k[8] = {0};
 };
 
@@ -802,6 +807,10 @@ mra_status pass_ops(mra_ctx *c, const double *theta_dev, int B, double *loglik_d
         w.exact_rem = c->precision == MRA_MIXED;
         w.theta = theta_dev;
         w.loglik = loglik_dev;
+        w.keep_up = c->keep_up;
+        w.keep_up_stride = c->keep_stride;
+        w.keep_li = (float *)c->keep_li;
+        w.keep_y = c->keep_y;
         if (with_regions) {
             w.reg_du = c->d_reg_du;
             w.reg_lw = c->d_reg_lw;
@@ -811,6 +820,10 @@ mra_status pass_ops(mra_ctx *c, const double *theta_dev, int B, double *loglik_d
         Work<double> w = make_work<double>(c, p, B);
         w.theta = theta_dev;
         w.loglik = loglik_dev;
+        w.keep_up = c->keep_up;
+        w.keep_up_stride = c->keep_stride;
+        w.keep_li = (double *)c->keep_li;
+        w.keep_y = c->keep_y;
         if (with_regions) {
             w.reg_du = c->d_reg_du;
             w.reg_lw = c->d_reg_lw;
@@ -925,6 +938,176 @@ mra_status ensure_stage(mra_ctx *c, int batch)
         return MRA_ENOMEM;
     }
     c->stage_cap = batch;
+    return MRA_OK;
+}
+
+// Leaf of a location by the descent build_partition bins observations with;
+// -1 outside the root box.
+int64_t leaf_of(const Partition &P, double a, double b)
+{
+    if (!(a >= P.bx0[0] && a < P.bx1[0] && b >= P.by0[0] && b < P.by1[0])) return -1;
+    int64_t i = 0;
+    for (int m = 1; m < P.M; m++) {
+        const int64_t g = P.lvl_off[(size_t)m] + i;
+        const double mx = 0.5 * (P.bx0[(size_t)g] + P.bx1[(size_t)g]);
+        const double my = 0.5 * (P.by0[(size_t)g] + P.by1[(size_t)g]);
+        int j;
+        if (P.J == 4)
+            j = (a >= mx) | ((b >= my) << 1);
+        else
+            j = P.cut_x[(size_t)m] ? (a >= mx) : (b >= my);
+        i = i * P.J + j;
+    }
+    return i;
+}
+
+// Device buffers of one mra_predict call, freed on every exit.
+struct PredBufs {
+    std::vector<void *> ptrs;
+    mra_ctx *c;
+    explicit PredBufs(mra_ctx *ctx) : c(ctx) {}
+    template <typename X>
+    X *take(size_t count)
+    {
+        void *p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return (X *)p;
+    }
+    ~PredBufs()
+    {
+        for (void *p : ptrs) cudaFree(p);
+        c->keep_up = c->keep_y = nullptr;
+        c->keep_li = nullptr;
+        c->keep_stride = 0;
+    }
+};
+
+// Prediction for storage type T: the likelihood pass at theta keeping the
+// factors, the downward pass, the basis at the points (the leaf-basis kernel
+// on a tree view whose observation rows are the points) and one warp per
+// point.  Points come grouped by leaf (px, py, leaf sorted the same way).
+template <typename T, int RP>
+mra_status predict_impl(mra_ctx *c, const double *theta, const std::vector<double> &sx,
+                        const std::vector<double> &sy, const std::vector<int64_t> &sl, double *mean_out,
+                        double *var_out)
+{
+    const Partition &P = c->P;
+    const int M = P.M;
+    const int64_t np = (int64_t)sx.size(), NK = P.nnonleaf(), NL = P.nleaf();
+    const int UC = (M - 1) * RP;
+    const size_t stride = keep_up_doubles(M, RP);
+    PredBufs bufs(c);
+    double *d_px = bufs.take<double>((size_t)np), *d_py = bufs.take<double>((size_t)np);
+    int64_t *d_leaf = bufs.take<int64_t>((size_t)np);
+    double *d_mean = bufs.take<double>((size_t)np), *d_var = bufs.take<double>((size_t)np);
+    T *d_ua = bufs.take<T>((size_t)np * (size_t)std::max(UC, 1));
+    double *d_xi = bufs.take<double>((size_t)std::max<int64_t>(NK, 1) * RP);
+    double *d_keep = bufs.take<double>((size_t)std::max<int64_t>(NK, 1) * stride);
+    T *d_li = bufs.take<T>((size_t)NL * kKeepLd * kKeepLd);
+    double *d_ky = bufs.take<double>((size_t)NL * kKeepLd);
+    int32_t *d_bigidx = bufs.take<int32_t>((size_t)NL);
+    if (!d_px || !d_py || !d_leaf || !d_mean || !d_var || !d_ua || !d_xi || !d_keep || !d_li || !d_ky || !d_bigidx) {
+        c->err = "cannot allocate the prediction buffers";
+        return MRA_ENOMEM;
+    }
+    // leaf -> large-leaf index
+    std::vector<int32_t> bigidx((size_t)NL, -1);
+    if (c->nbig > 0) {
+        std::vector<BigLeaf> hb((size_t)c->nbig);
+        if (cudaMemcpy(hb.data(), c->d_big, sizeof(BigLeaf) * hb.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            c->err = "cannot read the large-leaf list";
+            return MRA_ECUDA;
+        }
+        for (int k = 0; k < c->nbig; k++) bigidx[(size_t)hb[(size_t)k].leaf] = k;
+    }
+    // chunks of the basis evaluation: points below one level-(M-1) region
+    const int rows = chunk_rows<T>();
+    std::vector<Chunk> chunks;
+    if (M > 1)
+        for (int64_t k = 0; k < np; k++) {
+            if (sl[(size_t)k] < 0) continue;
+            const int32_t parent = (int32_t)(sl[(size_t)k] >> c->lgJ);
+            if (chunks.empty() || chunks.back().parent != parent || chunks.back().n == rows)
+                chunks.push_back(Chunk{parent, 0, k});
+            chunks.back().n++;
+        }
+    Chunk *d_chunks = bufs.take<Chunk>(chunks.size());
+    if (!d_chunks) {
+        c->err = "cannot allocate the prediction buffers";
+        return MRA_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(d_px, sx.data(), sizeof(double) * (size_t)np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_py, sy.data(), sizeof(double) * (size_t)np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_leaf, sl.data(), sizeof(int64_t) * (size_t)np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_bigidx, bigidx.data(), sizeof(int32_t) * (size_t)NL, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !chunks.empty())
+        e = cudaMemcpy(d_chunks, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_theta_stage, theta, sizeof(double) * 3, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "prediction upload");
+    // the likelihood pass, keeping the factors
+    c->keep_up = d_keep;
+    c->keep_stride = stride;
+    c->keep_li = d_li;
+    c->keep_y = d_ky;
+    int *d_st = (int *)(c->d_ll_stage + 1);
+    if (mra_status st = pass_ops(c, c->d_theta_stage, 1, c->d_ll_stage, d_st, (cudaStream_t)0, false)) return st;
+    c->keep_up = c->keep_y = nullptr;
+    c->keep_li = nullptr;
+    const DevTree t = dev_tree(c);
+    int rc = 0;
+    for (int m = 1; m < M && !rc; m++) rc = launch_down<RP>(t, d_keep, stride, d_xi, m, nullptr);
+    const Plan plan = make_plan(c);
+    Work<T> w = make_work<T>(c, plan, 1);
+    w.theta = c->d_theta_stage;
+    w.loglik = c->d_ll_stage;
+    w.exact_rem = c->precision == MRA_MIXED;
+    w.keep_li = d_li;
+    w.keep_y = d_ky;
+    if (!rc && !chunks.empty()) {
+        DevTree tp = t;
+        tp.sx = d_px;
+        tp.sy = d_py;
+        Work<T> wp = w;
+        wp.U = d_ua;
+        wp.U_stride = 0;
+        rc = launch_leafbasis<T, RP>(tp, wp, d_chunks, (int)chunks.size(), rows, c->lb_stages, 1, nullptr);
+    }
+    if (!rc) {
+        PredArgs q;
+        memset(&q, 0, sizeof(q));
+        q.np = np;
+        q.px = d_px;
+        q.py = d_py;
+        q.leaf = d_leaf;
+        q.Ua = d_ua;
+        q.xi = d_xi;
+        q.keep_up = d_keep;
+        q.keep_stride = stride;
+        q.bigidx = d_bigidx;
+        q.big = c->d_big;
+        q.mean = d_mean;
+        q.var = d_var;
+        q.nl = (int)std::max<int64_t>(c->max_leaf, 1);
+        const size_t per_warp = predict_warp_doubles(M, RP, q.nl) * sizeof(double);
+        if (per_warp > 200 * 1024) {
+            c->err = "largest leaf too large for the prediction kernel";
+            return MRA_EINVAL;
+        }
+        q.wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (160 * 1024) / per_warp));
+        rc = launch_predict<T, RP>(t, w, q, nullptr);
+    }
+    if (rc) return cuda_fail(c, (cudaError_t)rc, "prediction launch");
+    int hs = 0;
+    e = cudaMemcpy(&hs, d_st, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(mean_out, d_mean, sizeof(double) * (size_t)np, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(var_out, d_var, sizeof(double) * (size_t)np, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "prediction readback");
+    if (hs != MRA_OK) {
+        c->err = "Cholesky factor not positive definite";
+        return (mra_status)hs;
+    }
     return MRA_OK;
 }
 
@@ -1385,6 +1568,59 @@ mra_status mra_region_terms(mra_ctx *c, const double *theta, double *d, double *
     }
     if (loglik) *loglik = ll;
     return (mra_status)hs;
+}
+
+mra_status mra_predict(mra_ctx *c, const double *theta, const double *px, const double *py, int64_t np,
+                       double *mean, double *var)
+{
+    if (!c) return MRA_EINVAL;
+    if (!c->d_sx) {
+        c->err = "context was built without a device";
+        return MRA_EINVAL;
+    }
+    if (!theta || np < 0 || (np > 0 && (!px || !py || !mean || !var))) {
+        c->err = "bad count or null pointer";
+        return MRA_EINVAL;
+    }
+    for (int k = 0; k < 3; k++)
+        if (!(std::isfinite(theta[k]) && theta[k] > 0.0)) {
+            c->err = "theta must be finite and positive";
+            return MRA_EINVAL;
+        }
+    if (np == 0) return MRA_OK;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    if (mra_status st = ensure_stage(c, 1)) return st;
+    if (mra_status st = ensure_capacity(c, 1)) return st;
+    // group the points by leaf (stable), outside points first
+    std::vector<int64_t> leaf((size_t)np), order((size_t)np);
+    for (int64_t k = 0; k < np; k++) {
+        leaf[(size_t)k] = std::isfinite(px[k]) && std::isfinite(py[k]) ? leaf_of(c->P, px[k], py[k]) : -1;
+        order[(size_t)k] = k;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return leaf[(size_t)a] < leaf[(size_t)b]; });
+    std::vector<double> sx((size_t)np), sy((size_t)np), m((size_t)np), v((size_t)np);
+    std::vector<int64_t> sl((size_t)np);
+    for (int64_t k = 0; k < np; k++) {
+        const int64_t o = order[(size_t)k];
+        sx[(size_t)k] = leaf[(size_t)o] >= 0 ? px[o] : 0.0;
+        sy[(size_t)k] = leaf[(size_t)o] >= 0 ? py[o] : 0.0;
+        sl[(size_t)k] = leaf[(size_t)o];
+    }
+    mra_status st;
+    if (c->precision != MRA_FP64)
+        st = c->RP == 16 ? predict_impl<float, 16>(c, theta, sx, sy, sl, m.data(), v.data())
+                         : predict_impl<float, 32>(c, theta, sx, sy, sl, m.data(), v.data());
+    else
+        st = c->RP == 16 ? predict_impl<double, 16>(c, theta, sx, sy, sl, m.data(), v.data())
+                         : predict_impl<double, 32>(c, theta, sx, sy, sl, m.data(), v.data());
+    if (st != MRA_OK) return st;
+    for (int64_t k = 0; k < np; k++) {
+        mean[order[(size_t)k]] = m[(size_t)k];
+        var[order[(size_t)k]] = v[(size_t)k];
+    }
+    return MRA_OK;
 }
 
 mra_status mra_stats(const mra_ctx *c, mra_stats_t *o)

@@ -74,7 +74,52 @@ struct Work {
     double *reg_du; // [nreg][2] or null
     double *reg_lw; // [n_nonleaf] or null
     size_t regdu_stride, reglw_stride;
+    // prediction (null otherwise; batch slot 0 only): the upward pass keeps
+    // its factors per non-leaf region (keep_up, FP64, keep_up_stride doubles
+    // each), the shared-memory leaf posterior its L^{-1} (keep_li, k-major,
+    // kKeepLd x kKeepLd per leaf) and y = L^{-1} z (keep_y, kKeepLd per leaf)
+    double *keep_up;
+    size_t keep_up_stride;
+    T *keep_li;
+    double *keep_y;
 };
+
+// Leading dimension of a kept leaf factor: the largest shared-memory bucket.
+constexpr int kKeepLd = 64;
+
+// Doubles kept per non-leaf region (Work::keep_up):
+//   [0, RP^2)              L~, the factor of I + A^{m,m}: lower, row-major
+//   [RP^2, RP^2 + RP)      1 / L~_ii
+//   [RP^2 + RP, RP^2 + 2RP) v = L~^{-1} omega^m
+//   then Z = L~^{-1} [A^{m,1} .. A^{m,m-1}] as RP rows of (M-2) RP doubles
+//   (level m uses the first (m-1) RP)
+__host__ __device__ inline size_t keep_up_doubles(int M, int RP)
+{
+    return (size_t)RP * RP + 2 * (size_t)RP + (size_t)RP * (size_t)(M > 2 ? (M - 2) * RP : 0);
+}
+
+struct BigLeaf;
+struct PredArgs {
+    int64_t np;
+    const double *px, *py; // prediction points, grouped by leaf
+    const int64_t *leaf;   // leaf of each point, -1 outside the domain
+    const void *Ua;        // per point: (M-1) RP basis values a* (storage type)
+    const double *xi;      // per non-leaf region: RP posterior means
+    const double *keep_up;
+    size_t keep_stride;
+    const int32_t *bigidx; // per leaf: index into big, -1 for a shared-memory leaf
+    const BigLeaf *big;
+    double *mean, *var;
+    int nl;  // per-warp scratch rows (largest leaf, at least 1)
+    int wpb; // warps per block
+};
+
+// Doubles of per-warp scratch.
+__host__ __device__ inline size_t predict_warp_doubles(int M, int RP, int nl)
+{
+    return 3 * (size_t)(M - 1) * RP + 2 * (size_t)nl + (size_t)RP;
+}
+
 
 // Leaf-posterior buckets: a leaf with n observations runs in the kernel of the
 // smallest cap >= n (shared-memory footprint grows as cap^2).
@@ -111,6 +156,10 @@ template <typename T> __host__ __device__ constexpr int chunk_rows() { return si
 // Launchers (one instantiation per precision T and padding RP).
 template <typename T, int RP>
 int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream);
+template <int RP>
+int launch_down(const DevTree &t, const double *keep, size_t stride, double *xi, int m, void *stream);
+template <typename T, int RP>
+int launch_predict(const DevTree &t, const Work<T> &w, const PredArgs &q, void *stream);
 template <typename T, int RP>
 int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int rows, int stages,
                      int B, void *stream);

@@ -1228,6 +1228,15 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
         for (int r = k; r < n; r++) acc.add(sLi[k * nmax + r], sy2[r]);
         sy[k] = acc.value();
     }
+    if (w.keep_li && b == 0) {
+        // L^{-1} and y for prediction
+        T *kl = w.keep_li + (size_t)c * kKeepLd * kKeepLd;
+        for (int e = tid; e < n * n; e += NT) {
+            const int k = e / n, r = e % n;
+            kl[k * kKeepLd + r] = sLi[k * nmax + r];
+        }
+        for (int a = tid; a < n; a += NT) w.keep_y[(size_t)c * kKeepLd + a] = f_dbl(sy2[a]);
+    }
     __syncthreads();
     const double uv = red[0];
     gram_vec(sU, LDU, UC, sy, n, w.leaf_w + (size_t)b * w.leafw_stride + (size_t)c * UC);
@@ -1552,6 +1561,23 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
     const double q2 = red[0];
     const double dR = dsum + ld, uR = usum - q2;
     const int64_t g = t.lvl_off[m] + i;
+    if (w.keep_up && b == 0) {
+        // factors for prediction (layout: keep_up_doubles)
+        double *kp = w.keep_up + (size_t)g * w.keep_up_stride;
+        for (int e = tid; e < B2; e += NT) {
+            const int a = e / RP, q = e % RP;
+            kp[e] = q <= a ? f_dbl(sL[q * (RP + 1) + a]) : 0.0;
+        }
+        for (int a = tid; a < RP; a += NT) {
+            kp[B2 + a] = f_dbl(srs[a]);
+            kp[B2 + RP + a] = f_dbl(sz[a]);
+        }
+        const int ldk = (M - 2) * RP;
+        for (int e = tid; e < RP * ncol; e += NT) {
+            const int a = e / ncol, q = e % ncol;
+            kp[B2 + 2 * RP + (size_t)a * ldk + q] = (double)sZ[a * ldz + q];
+        }
+    }
     if (m > 1) {
         T *out = w.Atil[m] + (size_t)b * w.Atil_stride[m] + (size_t)i * npo * B2;
         const int i0 = TL::r0(), j0 = TL::c0();
@@ -1628,3 +1654,4 @@ __global__ void k_root_single(DevTree t, Work<T> w)
 } // namespace mra
 
 #include "mra_bigleaf.cuh"
+#include "mra_predict.cuh"

@@ -162,6 +162,30 @@ int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream)
     return (int)cudaGetLastError();
 }
 
+// Prediction: the downward pass (one level) and the per-point kernel.
+template <int RP>
+int launch_down(const DevTree &t, const double *keep, size_t stride, double *xi, int m, void *stream)
+{
+    const unsigned nreg = (unsigned)(t.lvl_off[m + 1] - t.lvl_off[m]);
+    k_down<RP><<<nreg, 32, 0, (cudaStream_t)stream>>>(t, keep, stride, xi, m);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, int RP>
+int launch_predict(const DevTree &t, const Work<T> &w, const PredArgs &q, void *stream)
+{
+    if (q.np <= 0) return 0;
+    static size_t done = 0;
+    const size_t sm = predict_warp_doubles(t.M, RP, q.nl) * sizeof(double) * (size_t)q.wpb;
+    if (int e = set_smem(k_predict<T, RP>, sm, &done)) return e;
+    const unsigned nb = (unsigned)((q.np + q.wpb - 1) / q.wpb);
+    k_predict<T, RP><<<nb, 32 * q.wpb, sm, (cudaStream_t)stream>>>(t, w, q);
+    return (int)cudaGetLastError();
+}
+
+#define MRA_INSTANTIATE_DOWN(RP) \
+    template int launch_down<RP>(const DevTree &, const double *, size_t, double *, int, void *);
+
 #define MRA_INSTANTIATE(T, RP)                                                                              \
     template size_t smem_prior<T, RP>(int);                                                                 \
     template size_t smem_leafbasis<T, RP>(int);                                                             \
@@ -179,6 +203,7 @@ int launch_root_single(const DevTree &t, const Work<T> &w, int B, void *stream)
                                    int, int, int, void *);                                                  \
     template int launch_leafgram<T, RP>(const DevTree &, const Work<T> &, int, int, int, void *);           \
     template int launch_up<T, RP>(const DevTree &, const Work<T> &, int, int, int, int, void *);            \
-    template int launch_root_single<T, RP>(const DevTree &, const Work<T> &, int, void *);
+    template int launch_root_single<T, RP>(const DevTree &, const Work<T> &, int, void *);                   \
+    template int launch_predict<T, RP>(const DevTree &, const Work<T> &, const PredArgs &, void *);
 
 } // namespace mra

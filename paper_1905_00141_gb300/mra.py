@@ -23,7 +23,8 @@ _STATUS = {0: "MRA_OK", 1: "MRA_EINVAL", 2: "MRA_ENOMEM", 3: "MRA_ENOTPD", 4: "M
 
 EXPORTED = ["mra_default_opts", "mra_build", "mra_loglik", "mra_loglik_device", "mra_set_precision",
             "mra_stats", "mra_tree_export", "mra_region_terms", "mra_profile", "mra_profile_read",
-            "mra_dense_loglik_noalloc", "mra_autotune", "mra_set_launch", "mra_last_error", "mra_free"]
+            "mra_dense_loglik_noalloc", "mra_autotune", "mra_set_launch", "mra_predict", "mra_last_error",
+            "mra_free"]
 
 
 def last_error() -> str:
@@ -99,6 +100,8 @@ def lib():
         L.mra_tree_export.argtypes = [vp, D, D, I64, I64, D]
         L.mra_region_terms.restype = ctypes.c_int
         L.mra_region_terms.argtypes = [vp, D, D, D, D, D]
+        L.mra_predict.restype = ctypes.c_int
+        L.mra_predict.argtypes = [vp, D, D, D, ctypes.c_int64, D, D]
         L.mra_profile.restype = ctypes.c_int
         L.mra_profile.argtypes = [vp, ctypes.c_int]
         L.mra_profile_read.restype = ctypes.c_int
@@ -266,6 +269,20 @@ class MRA:
         d, u, lw, ll = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(1)
         st = lib().mra_region_terms(self._h, _dp(th), _dp(d), _dp(u), _dp(lw), _dp(ll))
         return dict(d=d, u=u, logdetW=lw, loglik=float(ll[0]), status=int(st))
+
+
+    def predict(self, theta, px, py):
+        """Posterior predictive mean and variance of the latent process at the
+        points (px, py) for one theta (mra_predict); NaN outside the domain."""
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(3)
+        px = np.ascontiguousarray(px, dtype=np.float64).ravel()
+        py = np.ascontiguousarray(py, dtype=np.float64).ravel()
+        if px.shape != py.shape:
+            raise ValueError("px and py differ in length")
+        mean = np.empty(len(px))
+        var = np.empty(len(px))
+        self._check(lib().mra_predict(self._h, _dp(th), _dp(px), _dp(py), len(px), _dp(mean), _dp(var)))
+        return mean, var
 
 
 NOALLOC_MAX_N = 1024

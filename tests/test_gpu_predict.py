@@ -1,0 +1,147 @@
+"""GPU prediction (mra_predict: posterior predictive mean and variance of the
+latent process) against the oracle, through the C ABI.
+
+References:
+* small trees: dense kriging with Sigma_MRA (oracle/dense.py), the plain
+  definition;
+* the 131,072-point gridded workload: the recursion oracle's likelihood with
+  the point added as an observation (oracle.predict_by_loglik), at sampled
+  points.
+
+Tolerances.  FP64 path: 1e-9 absolute on the mean and the variance (data and
+sigma2 of order one; both sides are FP64 by different routes; measured
+<= 4e-13).  Mixed path: the basis values, Y = L^{-1} U and the small leaves'
+L^{-1} are stored in FP32 (unit roundoff u = 2^-24 = 6e-8).  The mean is a
+sum of n_R + (M-1) r such products weighted by the solution of the leaf's
+kriging system, whose condition number is up to (sigma2 + tau2) / tau2
+(= 250 at theta = (2.5, 0.3, 0.01)); the rounding errors add up like
+sqrt(n_R) (n_R <= 300 here): u * 250 * sqrt(300) = 2.6e-4 bounds the error,
+and the tests use 1e-4 (measured at most 1.9e-5, in the 300-point cluster
+at the long range and small nugget).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+from paper_1905_00141_gb300 import build as mbuild
+from paper_1905_00141_gb300 import mra, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+TOLMIX = 1e-4
+THETAS = [[1.0, 0.1, 0.05], [2.5, 0.3, 0.01]]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    mbuild.build()
+    oracle.build()
+
+
+def _points(rng, k, lo=0.02, hi=0.98):
+    return rng.uniform(lo, hi, k), rng.uniform(lo, hi, k)
+
+
+def _check(x, y, z, M, J, r, px, py, thetas=THETAS, precisions=("fp64", "mixed")):
+    worst = {}
+    with mra.MRA(x, y, z, M, J, r) as g:
+        for th in thetas:
+            ref_m, ref_v = dense.predict(x, y, z, M, J, r, th, px, py)
+            for p in precisions:
+                g.set_precision(p)
+                m, v = g.predict(th, px, py)
+                assert np.array_equal(np.isnan(m), np.isnan(ref_m)), p
+                ok = ~np.isnan(ref_m)
+                em = np.max(np.abs(m[ok] - ref_m[ok]))
+                ev = np.max(np.abs(v[ok] - ref_v[ok]))
+                tol = TOL64 if p == "fp64" else TOLMIX
+                assert em <= tol and ev <= tol, (p, th, em, ev)
+                worst[p] = max(worst.get(p, 0.0), em, ev)
+    return worst
+
+
+def test_predict_quadtree_small():
+    """n = 1500, M = 3, J = 4, r = 16: mean and variance at 40 points, plus
+    points on observations, in the top/right extension of the domain and
+    outside it (NaN)."""
+    x, y, z = synth.uniform(1500, 11)
+    rng = np.random.default_rng(5)
+    px, py = _points(rng, 40)
+    px = np.concatenate([px, x[:3], [x.max() + 1e-4, 2.0, -1.0]])
+    py = np.concatenate([py, y[:3], [0.5, 0.5, np.nan]])
+    _check(x, y, z, 3, 4, 16, px, py)
+
+
+def test_predict_binary_tree_deeper():
+    """J = 2, M = 6, r = 9 (odd knot count, padding to 16)."""
+    x, y, z = synth.uniform(900, 12)
+    rng = np.random.default_rng(6)
+    px, py = _points(rng, 30)
+    _check(x, y, z, 6, 2, 9, px, py)
+
+
+def test_predict_empty_leaf_and_large_leaf():
+    """A tight cluster makes a leaf of more than 64 observations (the tiled
+    large-leaf path) and a hole leaves leaves empty; points land in both."""
+    rng = np.random.default_rng(7)
+    xc = 0.3 + 0.02 * rng.standard_normal(300)
+    yc = 0.3 + 0.02 * rng.standard_normal(300)
+    xu, yu = rng.random(500), rng.random(500)
+    keep = ~((xu > 0.6) & (yu > 0.6))
+    x = np.concatenate([xc, xu[keep]])
+    y = np.concatenate([yc, yu[keep]])
+    z = synth.gp_exact(x, y, 1.0, 0.1, 0.05, rng)
+    px = np.concatenate([0.3 + 0.02 * rng.standard_normal(10), [0.8, 0.9, 0.75], rng.uniform(0.05, 0.95, 10)])
+    py = np.concatenate([0.3 + 0.02 * rng.standard_normal(10), [0.8, 0.7, 0.95], rng.uniform(0.05, 0.55, 10)])
+    with mra.MRA(x, y, z, 3, 4, 16) as g:
+        assert g.stats()["max_leaf"] > 64
+    _check(x, y, z, 3, 4, 16, px, py)
+
+
+def test_predict_single_level():
+    """M = 1: the prediction is plain kriging with the exponential covariance
+    (one small leaf and one large one)."""
+    for n, seed in ((50, 13), (200, 14)):
+        x, y, z = synth.uniform(n, seed)
+        rng = np.random.default_rng(seed)
+        px, py = _points(rng, 12)
+        _check(x, y, z, 1, 4, 16, px, py)
+
+
+def test_predict_grid_workload_sampled():
+    """The 131,072-point gridded workload (M = 7, J = 4, r = 32) at sampled
+    points against the recursion oracle's likelihood differences."""
+    d = synth.grid()
+    rng = np.random.default_rng(8)
+    x, y = d["x"], d["y"]
+    px = rng.uniform(x.min() + 0.05, x.max() - 0.05, 4)
+    py = rng.uniform(y.min() + 0.05, y.max() - 0.05, 4)
+    th = [1.0, 0.05, 0.01]
+    ref = np.array([oracle.predict_by_loglik(x, y, d["z"], d["M"], d["J"], d["r"], th, a, b)
+                    for a, b in zip(px, py)])
+    with mra.MRA(x, y, d["z"], d["M"], d["J"], d["r"]) as g:
+        for p in ("fp64", "mixed"):
+            g.set_precision(p)
+            m, v = g.predict(th, px, py)
+            tol = 1e-8 if p == "fp64" else TOLMIX
+            assert np.max(np.abs(m - ref[:, 0])) <= tol, (p, m, ref[:, 0])
+            assert np.max(np.abs(v - ref[:, 1])) <= tol, (p, v, ref[:, 1])
+
+
+def test_predict_many_points_consistent():
+    """100,000 points in one call: the same values as the points one by one
+    (grouping by leaf, chunking and the per-warp scratch do not mix points),
+    and 0 <= var <= sigma2."""
+    x, y, z = synth.uniform(4096, 15, exact=False)
+    rng = np.random.default_rng(9)
+    px, py = _points(rng, 100000)
+    th = [1.3, 0.08, 0.02]
+    with mra.MRA(x, y, z, 4, 4, 16, precision="mixed") as g:
+        m, v = g.predict(th, px, py)
+        assert np.all(np.isfinite(m)) and np.all(v >= -1e-6) and np.all(v <= th[0] + 1e-6)
+        idx = rng.choice(len(px), 20, replace=False)
+        for k in idx:
+            m1, v1 = g.predict(th, px[k:k + 1], py[k:k + 1])
+            assert m1[0] == m[k] and v1[0] == v[k]
