@@ -420,6 +420,8 @@ def run_ours(args):
             cpu.pop("seconds", None)
             cpu.pop("evals", None)
 
+    pred = prediction_line(g, d, args.precision) if name == "grid" else None
+
     step_ms = 1e3 * t_total / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -439,12 +441,48 @@ def run_ours(args):
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "flops_per_eval": st["flops_per_theta"],
         "launch_config": {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent")},
+        "predict": pred,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
     g.close()
     return 0
+
+
+def prediction_line(g, d, precision, npts=131072, reps=3):
+    """Posterior prediction (mra_predict) at npts random points of the
+    workload's domain: host-API wall time per call (one likelihood pass that
+    keeps the factors, the top-down pass, the basis at the points, one warp
+    per point, transfers included), the largest difference from the other
+    precision, and two points against the oracle's likelihood differences."""
+    import oracle
+    x, y = d["x"], d["y"]
+    rng = np.random.default_rng(1905)
+    px = rng.uniform(x.min(), x.max(), npts)
+    py = rng.uniform(y.min(), y.max(), npts)
+    th = [1.0, 0.05, 0.01]
+    g.predict(th, px[:1024], py[:1024])
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        m, v = g.predict(th, px, py)
+    dt = (time.perf_counter() - t0) / reps
+    other = "fp64" if precision != "fp64" else "mixed"
+    g.set_precision(other)
+    mo, vo = g.predict(th, px[:4096], py[:4096])
+    g.set_precision(precision)
+    chk = []
+    for k in range(2):
+        a, b = float(px[k]), float(py[k])
+        if x.min() < a < x.max() and y.min() < b < y.max():
+            rm, rv = oracle.predict_by_loglik(x, y, d["z"], d["M"], d["J"], d["r"], th, a, b)
+            chk.append((abs(m[k] - rm), abs(v[k] - rv)))
+    return {"points": npts, "theta": th, "ms_per_call": 1e3 * dt, "points_per_s": npts / dt,
+            "timing": "host API wall time, transfers included",
+            "max_abs_diff_vs_" + other: float(max(np.max(np.abs(m[:4096] - mo)), np.max(np.abs(v[:4096] - vo)))),
+            "oracle_check": {"points": len(chk), "route": "likelihood differences of the FP64 CPU oracle",
+                             "max_abs_err_mean": float(max(c[0] for c in chk)) if chk else None,
+                             "max_abs_err_var": float(max(c[1] for c in chk)) if chk else None}}
 
 
 def main():
