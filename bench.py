@@ -167,7 +167,8 @@ class ClockSampler:
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("mra_kernels.cuh", "mra_launch.cuh"):
+    for f in ("mra_kernels.cuh", "mra_launch.cuh", "mra_bigleaf.cuh", "mra_predict.cuh", "ff_math.h",
+              "mra_internal.h"):
         with open(os.path.join(ROOT, "paper_1905_00141_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

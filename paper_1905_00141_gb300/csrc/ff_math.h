@@ -132,8 +132,14 @@ struct grid_acc {
 };
 MRA_HD float grid_constant(double bound)
 {
+#if defined(__CUDA_ARCH__)
+    // bound = m 2^E with m in [0.5, 1) for a positive normal bound, read off
+    // the exponent field (integer operations instead of FP64 ones)
+    const int E = (int)((__double_as_longlong(bound) >> 52) & 0x7ff) - 1022;
+#else
     int E;
     frexp(bound, &E); // bound < 2^E
+#endif
     return ldexpf(1.5f, E + 2);
 }
 MRA_HD void grid_init(grid_acc &s, float c)

@@ -109,9 +109,11 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
         sc[2 * TB + a] = a < nJ ? t.sx[v.o0 + rJ + a] - ox : 0.0;
         sc[3 * TB + a] = a < nJ ? t.sy[v.o0 + rJ + a] - oy : 0.0;
     }
+    __shared__ double s_ib; // 1/beta, one FP64 division per CTA
+    if (tid == 0) s_ib = 1.0 / th[1];
     cp_async_wait<0>();
     __syncthreads();
-    const double tau2 = th[2], ib64 = 1.0 / th[1];
+    const double tau2 = th[2], ib64 = s_ib;
     const int a0 = 2 * (tid / (TB / 2)), q0 = 2 * (tid % (TB / 2));
     T hi[2][2], lo[2][2];
     dot2x2_exact(sUI + a0 * LDU, sUI + min(a0 + 1, TB - 1) * LDU, sUJ + q0 * LDU, sUJ + min(q0 + 1, TB - 1) * LDU, UC,

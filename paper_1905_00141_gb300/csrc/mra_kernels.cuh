@@ -61,7 +61,7 @@ __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000
 template <typename T>
 struct CovP {
     T s2, ib; // sigma2 and 1/beta
-    __device__ CovP(const double *th) : s2((T)th[0]), ib((T)(1.0 / th[1])) {}
+    __device__ CovP(double sigma2, double inv_beta) : s2((T)sigma2), ib((T)inv_beta) {}
 };
 
 // Exponential covariance sigma2 * exp(-|d| / beta) of a coordinate difference
@@ -789,12 +789,14 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     const int i = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const CovP<T> cp(th);
+    // 1/beta once per CTA (an FP64 division), read after the first barrier
+    __shared__ double s_ib;
     __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
     const float s_cq = grid_constant(th[0]);
     if (threadIdx.x == 0) {
+        s_ib = 1.0 / th[1];
         s_par[0] = ff_from_double(th[0]);
-        s_par[1] = ff_from_double(1.0 / th[1]);
+        s_par[1] = ff_from_double(s_ib);
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     F *sL = (F *)smem_raw;                  // RP x (RP+1)
@@ -860,7 +862,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
 #pragma unroll
                 for (int c = 0; c < TL::CT; c++) {
                     const int a = r0 + r, j = c0 + c;
-                    const T cv = (a < R && j < R) ? cov_d(cp, sq[a] - sa[j], sq[RP + a] - sa[RP + j]) : T(0);
+                    const T cv = (a < R && j < R) ? cov_d(CovP<T>(th[0], s_ib), sq[a] - sa[j], sq[RP + a] - sa[RP + j]) : T(0);
                     sW[j * RP + a] = cv - acc[r][c];
                 }
         }
@@ -916,7 +918,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
                 const int a = r0 + r, j = c0 + c;
                 F v;
                 if (a < R && j < R)
-                    v = f_of_T(cov_d(cp, sq[a] - sq[j], sq[RP + a] - sq[RP + j]) - acc[r][c]);
+                    v = f_of_T(cov_d(CovP<T>(th[0], s_ib), sq[a] - sq[j], sq[RP + a] - sq[RP + j]) - acc[r][c]);
                 else
                     v = f_of<F>(a == j ? 1.0 : 0.0);
                 sL[a * (RP + 1) + j] = v;
@@ -964,12 +966,14 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
     const int b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const CovP<T> cp(th);
+    // 1/beta once per CTA (an FP64 division), read after the first barrier
+    __shared__ double s_ib;
     __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
     const float s_cq = grid_constant(th[0]);
     if (threadIdx.x == 0) {
+        s_ib = 1.0 / th[1];
         s_par[0] = ff_from_double(th[0]);
-        s_par[1] = ff_from_double(1.0 / th[1]);
+        s_par[1] = ff_from_double(s_ib);
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = t.M, R = t.R, P = ch.parent, nr = ch.n;
@@ -1034,7 +1038,7 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
 #pragma unroll
                 for (int c = 0; c < TL::CT; c++) {
                     const int a = r0 + r, j = c0 + c;
-                    const T cv = (a < nr && j < R) ? cov_d(cp, sp[a] - sa[j], sp[CH + a] - sa[RP + j]) : T(0);
+                    const T cv = (a < nr && j < R) ? cov_d(CovP<T>(th[0], s_ib), sp[a] - sa[j], sp[CH + a] - sa[RP + j]) : T(0);
                     sW[j * LDC + a] = cv - acc[r][c];
                 }
         }
@@ -1105,7 +1109,8 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
     const int b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const double tau2 = th[2], ib64 = 1.0 / th[1];
+    const double tau2 = th[2];
+    __shared__ double s_ib; // 1/beta, one FP64 division per CTA
     const int M = t.M;
     const int64_t o0 = t.leaf_off[c];
     const int n = (int)(t.leaf_off[c + 1] - o0);
@@ -1148,8 +1153,9 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
     for (int e = tid; e < nmax * nmax; e += NT) sLi[e] = T(0);
     if (tid == 0) {
         flag[0] = 0;
+        s_ib = 1.0 / th[1];
         s_par[0] = ff_from_double(th[0]);
-        s_par[1] = ff_from_double(ib64);
+        s_par[1] = ff_from_double(s_ib);
     }
     const ff tau2f = ff_from_double(tau2);
     cp_async_wait<0>();
@@ -1178,7 +1184,7 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
                         if (a == q) v = ff_add(v, tau2f);
                         sV[a * LDV + q] = v;
                     } else {
-                        const double cv = cov64(th[0], ib64, sp[a] - sp[q], sp[nmax + a] - sp[nmax + q]);
+                        const double cv = cov64(th[0], s_ib, sp[a] - sp[q], sp[nmax + a] - sp[nmax + q]);
                         sV[a * LDV + q] = cancel_sub(cv, hi[i][j], lo[i][j]) + (a == q ? tau2 : 0.0);
                     }
                 }
