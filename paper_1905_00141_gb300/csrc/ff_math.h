@@ -87,6 +87,14 @@ MRA_HD ff ff_sub_sloppy(ff a, ff b)
     const ff s = two_sum(a.hi, -b.hi);
     return fast_two_sum(s.hi, FADD(s.lo, FSUB(a.lo, b.lo)));
 }
+// a + b when the sum does not cancel (both non-negative, say): one TwoSum of
+// the leading parts, the trailing parts added in FP32; relative error a few
+// 2^-48.  11 operations instead of 20.
+MRA_HD ff ff_add_sloppy(ff a, ff b)
+{
+    const ff s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, FADD(s.lo, FADD(a.lo, b.lo)));
+}
 MRA_HD ff ff_add_f(ff a, float b)
 {
     const ff s = two_sum(a.hi, b);
@@ -107,10 +115,17 @@ MRA_HD ff ff_sqr(ff a)
 MRA_HD ff ff_sqrt(ff a)
 {
     if (!(a.hi > 0.f)) return ff{0.f, 0.f};
-    const float s = sqrtf(a.hi);
+    // s ~ sqrt(a.hi) from the reciprocal square root y, then one Newton step
+    // s + (a - s^2) y / 2 with s^2 exact: the error after it is O(ulp^2)
+#if defined(__CUDA_ARCH__)
+    const float y = rsqrtf(a.hi);
+#else
+    const float y = 1.0f / sqrtf(a.hi);
+#endif
+    const float s = FMUL(a.hi, y);
     const ff p = two_prod(s, s);
     const float r = FADD(FSUB(FSUB(a.hi, p.hi), p.lo), a.lo);
-    return fast_two_sum(s, FMUL(r, FMUL(0.5f, 1.0f / s)));
+    return fast_two_sum(s, FMUL(r, FMUL(0.5f, y)));
 }
 
 MRA_HD ff ff_mul_f(ff a, float b)
@@ -209,24 +224,40 @@ MRA_HD ff ff_exp_neg(ff x)
     const ff p2 = two_prod(kf, MRA_FF_C2);
     ff r = two_sum(t1, -p2.hi);
     r = fast_two_sum(r.hi, FADD(r.lo, FSUB(FSUB(x.lo, p2.lo), FMUL(kf, MRA_FF_C3))));
-    // exp(-r) = 1 - r + r^2/2 - q, q = r^3 (1/6 - r/24 + r^2/120 - r^3/720) in float
-    const float rh = r.hi;
-    const float poly = FFMA(rh, FFMA(rh, FFMA(rh, -1.0f / 720.0f, 1.0f / 120.0f), -1.0f / 24.0f), 1.0f / 6.0f);
-    const float q = FMUL(FMUL(FMUL(rh, rh), rh), poly);
-    ff s = ff_add(ff{1.0f, 0.0f}, ff_neg(r));
-    const ff r2 = ff_sqr(r);
-    s = ff_add(s, ff{FMUL(r2.hi, 0.5f), FMUL(r2.lo, 0.5f)});
-    s = ff_add_f(s, -q);
-    const ff e = ff_mul(s, tab[k & 63]);
-    const int a = k >> 6;
-    return ff{ldexpf(e.hi, -a), ldexpf(e.lo, -a)};
+    // exp(-r) = 1 - r + r^2/2 - r^3 (1/6 - r/24 + r^2/120), |r| <= ln2/128:
+    // 1 - r.hi and + r.hi^2/2 as exact pairs, every other term (each below
+    // 2^-24) added in FP32
+    const float rh = r.hi, rl = r.lo;
+    const ff s0 = fast_two_sum(1.0f, -rh);
+    const ff p = two_prod(rh, rh);
+    const ff s1 = fast_two_sum(s0.hi, FMUL(p.hi, 0.5f));
+    const float poly = FFMA(rh, FFMA(rh, 1.0f / 120.0f, -1.0f / 24.0f), 1.0f / 6.0f);
+    const float q = FMUL(FMUL(p.hi, rh), poly);
+    float t = FSUB(FADD(s0.lo, s1.lo), rl);
+    t = FFMA(p.lo, 0.5f, t);
+    t = FFMA(rh, rl, t);
+    t = FSUB(t, q);
+    const ff e = ff_mul(fast_two_sum(s1.hi, t), tab[k & 63]);
+    // times 2^-(k >> 6), 0 <= k >> 6 <= 125 for 0 <= x < 87
+#if defined(__CUDA_ARCH__)
+    const float sc = __int_as_float((127 - (k >> 6)) << 23);
+#else
+    const float sc = ldexpf(1.0f, -(k >> 6));
+#endif
+    return ff{FMUL(e.hi, sc), FMUL(e.lo, sc)};
 }
-
-// sigma2 * exp(-|p - q| / beta) from float-pair coordinates and parameters.
+// sigma2 exp(-|p - q| / beta) from float-pair coordinates, sigma2 and 1/beta
 MRA_HD ff ff_cov_exp(ff s2, ff ib, ff px, ff py, ff qx, ff qy)
 {
-    const ff dx = ff_sub(px, qx), dy = ff_sub(py, qy);
-    const ff d = ff_sqrt(ff_add(ff_sqr(dx), ff_sqr(dy)));
+    const ff dx = ff_sub_sloppy(px, qx), dy = ff_sub_sloppy(py, qy);
+    const ff d = ff_sqrt(ff_add_sloppy(ff_sqr(dx), ff_sqr(dy)));
+    return ff_mul(s2, ff_exp_neg(ff_mul(d, ib)));
+}
+// the same for FP32 coordinates (differences exact by TwoSum)
+MRA_HD ff ff_cov_exp(ff s2, ff ib, float px, float py, float qx, float qy)
+{
+    const ff dx = two_sum(px, -qx), dy = two_sum(py, -qy);
+    const ff d = ff_sqrt(ff_add_sloppy(ff_sqr(dx), ff_sqr(dy)));
     return ff_mul(s2, ff_exp_neg(ff_mul(d, ib)));
 }
 

@@ -282,7 +282,7 @@ __device__ __forceinline__ void remainder_ff(float (&out)[Tile<ROWS, RP>::RT][Ti
             const int a = r0 + r, j = c0 + c;
             ff cv = ff{0.f, 0.f};
             if (a < nP && j < R)
-                cv = ff_cov_exp(s2f, ibf, ff{pp[a], 0.f}, ff{pp[ldp + a], 0.f}, ff{pq[j], 0.f}, ff{pq[RP + j], 0.f});
+                cv = ff_cov_exp(s2f, ibf, pp[a], pp[ldp + a], pq[j], pq[RP + j]);
             out[r][c] = ff_sub(cv, ff{fa[r][c].hi, fa[r][c].lo}).hi;
         }
 }
@@ -897,8 +897,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
                     const int a = r0 + r, j = c0 + c;
                     F v;
                     if (a < R && j < R)
-                        v = ff_sub(ff_cov_exp(s2f, ibf, ff{sq[a], 0.f}, ff{sq[RP + a], 0.f}, ff{sq[j], 0.f},
-                                              ff{sq[RP + j], 0.f}),
+                        v = ff_sub(ff_cov_exp(s2f, ibf, sq[a], sq[RP + a], sq[j], sq[RP + j]),
                                    ff{fa[r][c].hi, fa[r][c].lo});
                     else
                         v = f_of<F>(a == j ? 1.0 : 0.0);

@@ -24,6 +24,16 @@ int main() {
             long double ref = expl(-(long double)x);
             printf("%.17g %.21Lg\n", mra::ff_to_double(r), ref);
         }
+    } else if (mode == 2) {
+        // FP32 coordinates (the overload the remainder recursions use)
+        double s2, beta;
+        float ax, ay, bx, by;
+        while (scanf("%lf %lf %f %f %f %f", &s2, &beta, &ax, &ay, &bx, &by) == 6) {
+            mra::ff c = mra::ff_cov_exp(mra::ff_from_double(s2), mra::ff_from_double(1.0 / beta), ax, ay, bx, by);
+            long double dx = (long double)ax - bx, dy = (long double)ay - by;
+            long double ref = (long double)s2 * expl(-sqrtl(dx * dx + dy * dy) / (long double)beta);
+            printf("%.17g %.21Lg\n", mra::ff_to_double(c), ref);
+        }
     } else {
         double s2, beta, ax, ay, bx, by;
         while (scanf("%lf %lf %lf %lf %lf %lf", &s2, &beta, &ax, &ay, &bx, &by) == 6) {
@@ -82,10 +92,30 @@ def test_cov_exp_relative_error(prog):
     rows.append("1.3 0.1 0.25 0.5 0.25 0.5")  # zero distance: exactly sigma2
     got, ref = _run(prog, "1\n" + "\n".join(rows))
     s2 = np.array([float(r.split()[0]) for r in rows])
-    assert (np.abs(got - ref) / s2).max() < 2e-14
+    # the covariance enters sums of products carried to ~1e-11 sigma2 (grid
+    # accumulation); the float-pair evaluation is held to 2e-13, fifty
+    # times below that (sloppy float-pair adds for the coordinate differences
+    # and the squared distance, whose terms do not cancel)
+    assert (np.abs(got - ref) / s2).max() < 2e-13
     big = ref > 1e-3 * s2
-    assert (np.abs(got - ref) / ref)[big].max() < 5e-14
+    assert (np.abs(got - ref) / ref)[big].max() < 2e-13
     assert got[-1] == 1.3 or abs(got[-1] - 1.3) < 1e-15
+
+
+def test_cov_exp_float_coordinates(prog):
+    """The FP32-coordinate overload: exact coordinate differences, the same
+    2e-13 bound (coordinates rounded to FP32 first, on both sides)."""
+    rng = np.random.default_rng(3)
+    rows = []
+    for _ in range(4000):
+        s2 = rng.uniform(0.1, 5)
+        beta = 10 ** rng.uniform(-2.5, 1)
+        a = rng.uniform(0.0, 0.05, 2).astype(np.float32)
+        b = (a + rng.normal(0, 10 ** rng.uniform(-4, -1), 2)).astype(np.float32)
+        rows.append("%.17g %.17g %.9g %.9g %.9g %.9g" % (s2, beta, a[0], a[1], b[0], b[1]))
+    got, ref = _run(prog, "2\n" + "\n".join(rows))
+    s2 = np.array([float(r.split()[0]) for r in rows])
+    assert (np.abs(got - ref) / s2).max() < 2e-13
 
 
 PROG2 = r"""
