@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
             if constexpr (sizeof(T) == 4) {
                 const ff cv = ff_cov_exp(s2f, ibf, ff_from_double(sc[a]), ff_from_double(sc[TB + a]),
                                          ff_from_double(sc[2 * TB + q]), ff_from_double(sc[3 * TB + q]));
-                val = ff_sub(cv, ff{(float)hi[i][j], (float)lo[i][j]});
-                if (diag) val = ff_add(val, tau2f);
+                val = ff_sub_sloppy(cv, ff{(float)hi[i][j], (float)lo[i][j]});
+                if (diag) val = ff_add_sloppy(val, tau2f);
             } else {
                 const double cv = cov64(th[0], ib64, sc[a] - sc[2 * TB + q], sc[TB + a] - sc[3 * TB + q]);
                 val = cancel_sub(cv, hi[i][j], lo[i][j]) + (diag ? tau2 : 0.0);

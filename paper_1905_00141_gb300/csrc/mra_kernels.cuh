@@ -283,7 +283,9 @@ __device__ __forceinline__ void remainder_ff(float (&out)[Tile<ROWS, RP>::RT][Ti
             ff cv = ff{0.f, 0.f};
             if (a < nP && j < R)
                 cv = ff_cov_exp(s2f, ibf, pp[a], pp[ldp + a], pq[j], pq[RP + j]);
-            out[r][c] = ff_sub(cv, ff{fa[r][c].hi, fa[r][c].lo}).hi;
+            // rounded to FP32: the leading parts subtract exactly when they
+            // are close (Sterbenz), the trailing parts only move the last bit
+            out[r][c] = FADD(FSUB(cv.hi, fa[r][c].hi), FSUB(cv.lo, fa[r][c].lo));
         }
 }
 
@@ -897,7 +899,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
                     const int a = r0 + r, j = c0 + c;
                     F v;
                     if (a < R && j < R)
-                        v = ff_sub(ff_cov_exp(s2f, ibf, sq[a], sq[RP + a], sq[j], sq[RP + j]),
+                        v = ff_sub_sloppy(ff_cov_exp(s2f, ibf, sq[a], sq[RP + a], sq[j], sq[RP + j]),
                                    ff{fa[r][c].hi, fa[r][c].lo});
                     else
                         v = f_of<F>(a == j ? 1.0 : 0.0);
@@ -1179,8 +1181,8 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
                     if (a >= n || q > a) continue;
                     if constexpr (sizeof(T) == 4) {
                         const ff cv = ff_cov_exp(s_par[0], s_par[1], spf[a], spf[nmax + a], spf[q], spf[nmax + q]);
-                        ff v = ff_sub(cv, ff{(float)hi[i][j], (float)lo[i][j]});
-                        if (a == q) v = ff_add(v, tau2f);
+                        ff v = ff_sub_sloppy(cv, ff{(float)hi[i][j], (float)lo[i][j]});
+                        if (a == q) v = ff_add_sloppy(v, tau2f);
                         sV[a * LDV + q] = v;
                     } else {
                         const double cv = cov64(th[0], s_ib, sp[a] - sp[q], sp[nmax + a] - sp[nmax + q]);
