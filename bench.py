@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of the cpu_baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--launch", default=None, metavar="ROWS,STAGES,BUCKETS,CONCURRENT",
+                   help="pin the launch configuration (mra_set_launch) instead of running the autotuner, "
+                        "e.g. 64,1,0,1")
     p.add_argument("--workload", default="grid", choices=["grid", "clustered", "massive"],
                    help="grid: n=131,072, 1 theta per call (default); clustered: n=2,097,152 with 64 theta per "
                         "call; massive: n=47,185,920, 1 theta per call")
@@ -325,8 +328,16 @@ def run_ours(args):
             dist.barrier()
         return ms, clocks, prof, ll
 
-    # launch configuration chosen by the library's autotuner (outside the timed region)
-    tune = g.autotune(thetas[0][0], reps=3)
+    # launch configuration chosen by the library's autotuner (outside the timed region), or pinned
+    def choose_launch():
+        if args.launch:
+            keys = ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent")
+            cfg = dict(zip(keys, (int(v) for v in args.launch.split(","))))
+            g.set_launch(**cfg)
+            return dict(cfg, pinned=True)
+        return g.autotune(thetas[0][0], reps=3)
+
+    tune = choose_launch()
     ms, clocks, prof, ll = one_measure(args.precision, args)
     if clocks_rejected(clocks):
         ms, clocks, prof, ll = one_measure(args.precision, args)
@@ -344,17 +355,17 @@ def run_ours(args):
         other_line = {"precision": other, "value": world * n * per_call * oargs.steps / (sum(ms_o) / 1e3),
                       "ms_per_step": sum(ms_o) / oargs.steps, "steps": oargs.steps}
         g.set_precision(args.precision)
-        g.autotune(thetas[0][0], reps=3)
+        choose_launch()
     # the fast mixed mode (FP32 remainder recursions) on the same steps
     fast_line, ll_f = None, None
     if args.precision == "mixed" and name == "grid":
         g.set_precision("mixed_fast")
-        g.autotune(thetas[0][0], reps=3)
+        choose_launch()
         ms_f, _, _, ll_f = one_measure("mixed_fast", args)
         fast_line = {"precision": "mixed_fast", "value": whole_job_rate(n, per_call, args.steps, sum(ms_f) / 1e3, 1),
                      "ms_per_step": sum(ms_f) / args.steps}
         g.set_precision(args.precision)
-        g.autotune(thetas[0][0], reps=3)
+        choose_launch()
 
     # end to end: host theta (pinned) in, host loglik out, through mra_loglik
     th_host = torch.tensor(thetas, dtype=torch.float64).pin_memory().numpy()
@@ -441,7 +452,8 @@ def run_ours(args):
         "fast_mixed": fast_line,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "flops_per_eval": st["flops_per_theta"],
-        "launch_config": {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent")},
+        "launch_config": {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent",
+                                                "pinned") if k in tune},
         "predict": pred,
     }
     print(json.dumps(line), flush=True)
