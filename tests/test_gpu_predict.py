@@ -145,3 +145,20 @@ def test_predict_many_points_consistent():
         for k in idx:
             m1, v1 = g.predict(th, px[k:k + 1], py[k:k + 1])
             assert m1[0] == m[k] and v1[0] == v[k]
+
+
+def test_predict_errors_and_empty_call():
+    """EINVAL for a theta that is not finite and positive (the context stays
+    usable), nothing to do for zero points, NaN for non-finite locations."""
+    x, y, z = synth.uniform(300, 16)
+    with mra.MRA(x, y, z, 3, 4, 9) as g:
+        for bad in ([0.0, 0.1, 0.05], [1.0, -0.1, 0.05], [1.0, 0.1, np.inf]):
+            with pytest.raises(mra.MRAError) as e:
+                g.predict(bad, [0.5], [0.5])
+            assert e.value.status == 1
+        m, v = g.predict([1.0, 0.1, 0.05], [], [])
+        assert m.size == 0 and v.size == 0
+        m, v = g.predict([1.0, 0.1, 0.05], [np.nan, 0.5, np.inf], [0.5, 0.5, 0.5])
+        assert np.isnan(m[0]) and np.isnan(m[2]) and np.isfinite(m[1]) and np.isfinite(v[1])
+        ref_m, ref_v = dense.predict(x, y, z, 3, 4, 9, [1.0, 0.1, 0.05], [0.5], [0.5])
+        assert abs(m[1] - ref_m[0]) <= TOL64 and abs(v[1] - ref_v[0]) <= TOL64
