@@ -8,7 +8,7 @@
  * theta by a derivative-free optimiser (BOBYQA, "likelihood" mode of
  * Sec. 2.2.5) that calls the exact log-likelihood at every step; here the
  * network proposes where the exact likelihood is evaluated next, and the
- * exact values judge every proposal.
+ * exact values decide on every proposal.
  *
  * Network (all sizes fixed):
  *   x_i  = 2 (log theta_i - log lo_i) / (log hi_i - log lo_i) - 1,  i = 0..2
