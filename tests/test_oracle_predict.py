@@ -68,3 +68,36 @@ def test_likelihood_difference_route_detects_a_wrong_mean():
     m2, v2 = oracle.predict_by_loglik(x, y, z, 2, 4, 9, th, px[0], py[0])
     assert abs(mean[0] - m2) < 1e-10
     assert abs(mean[0] + 1e-6 - m2) > 5e-7
+
+
+PREDICT_MUTATIONS = {
+    "no_nugget": ("K = Sig[:n, :n] + tau2 * np.eye(n)", "K = Sig[:n, :n] + 0.5 * tau2 * np.eye(n)"),
+    "mean_without_solve": ("mean[inside] = A.T @ w", "mean[inside] = A.T @ part.z"),
+    "variance_sign": ("- np.sum(A * A, axis=0)", "+ np.sum(A * A, axis=0)"),
+    "nugget_in_variance": ("var[inside] = np.diag(Sig[np.ix_(P, P)])",
+                           "var[inside] = tau2 + np.diag(Sig[np.ix_(P, P)])"),
+    "prior_instead_of_mra": ("Sig, info = sigma_mra(part, sigma2, beta, return_all=True, extra=(px[inside], py[inside]))",
+                             "Sig, info = sigma_mra(part, sigma2, beta, return_all=True, extra=(px[inside], py[inside]))\n"
+                             "    Sig = sigma2 * np.exp(-np.hypot(info['X'][:, None] - info['X'][None, :], "
+                             "info['Y'][:, None] - info['Y'][None, :]) / beta)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PREDICT_MUTATIONS))
+def test_prediction_pin_catches_mutation(name):
+    """Each plausible mistake planted in a private copy of dense.predict
+    breaks the likelihood-difference pin."""
+    import inspect
+    src = inspect.getsource(dense.predict)
+    old, new = PREDICT_MUTATIONS[name]
+    assert src.count(old) == 1
+    ns = dict(vars(dense))
+    exec(src.replace(old, new), ns)
+    bad = ns["predict"]
+    x, y, z, rng = _data(220, 51)
+    th = [1.2, 0.1, 0.05]
+    px, py = np.array([0.37, 0.71]), np.array([0.52, 0.26])
+    m, v = bad(x, y, z, 3, 4, 9, th, px, py)
+    ref = [oracle.predict_by_loglik(x, y, z, 3, 4, 9, th, a, b) for a, b in zip(px, py)]
+    err = max(max(abs(m[k] - ref[k][0]), abs(v[k] - ref[k][1])) for k in range(2))
+    assert err > 1e-6, (name, err)
