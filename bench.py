@@ -177,10 +177,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(family, precision):
-    """DRAM bytes per launch of a kernel family from the committed ncu launch
-    list, or None when that capture is of another precision or of kernel
-    source that has changed since."""
+def measured_counters(family, precision, key="bytes_per_launch"):
+    """A per-family figure from the committed ncu captures (profiles/
+    dram_traffic.json): DRAM bytes per launch, or the fraction of issue slots
+    busy; None when the capture is of another precision or of kernel source
+    that has changed since."""
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as fh:
             t = json.load(fh)
@@ -188,7 +189,11 @@ def measured_traffic(family, precision):
         return None
     if precision != "mixed" or t.get("csrc_sha256_prefix") != kernel_source_hash():
         return None
-    return t.get("bytes_per_launch", {}).get(family)
+    return t.get(key, {}).get(family)
+
+
+def measured_traffic(family, precision):
+    return measured_counters(family, precision)
 
 
 def clocks_rejected(c):
@@ -417,7 +422,9 @@ def run_ours(args):
     roof = {"bound": "alu", "kernel": fam, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": measured_traffic(fam, args.precision) if name == "grid" else None,
-            "peak_source": peak_note, "launch_ms": fam_ms / launches, "flops_per_launch": fl_per_launch}
+            "peak_source": peak_note, "launch_ms": fam_ms / launches, "flops_per_launch": fl_per_launch,
+            "issue_active_frac_ncu": measured_counters(fam, args.precision, "issue_active_frac")
+            if name == "grid" else None}
 
     cpu = None
     if not args.no_cpu_baseline:
