@@ -328,6 +328,18 @@ struct mra_ctx {
     double *keep_up = nullptr, *keep_y = nullptr;
     void *keep_li = nullptr;
     size_t keep_stride = 0;
+    // every device pass counts itself; mra_predict reuses the factors of its
+    // last pass while theta, the precision and the scratch are unchanged and
+    // no other pass has run since
+    uint64_t pass_count = 0;
+    struct PredState {
+        unsigned char *pt = nullptr, *tree = nullptr; // per-point and per-tree buffers (grow-only)
+        size_t pt_bytes = 0, tree_bytes = 0;
+        double theta[3] = {0.0, 0.0, 0.0};
+        int precision = -1;
+        uint64_t pass_id = 0, gen = 0;
+        bool valid = false;
+    } pred;
     double flops_k[8] = {0};
 };
 
@@ -798,6 +810,7 @@ int max_batch_for(mra_ctx *c, size_t budget)
 mra_status pass_ops(mra_ctx *c, const double *theta_dev, int B, double *loglik_dev, int *status_dev, cudaStream_t s,
                     bool with_regions)
 {
+    c->pass_count++;
     Plan p = make_plan(c);
     cudaError_t e = cudaMemsetAsync(c->d_status, 0, sizeof(int) * (size_t)B, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
@@ -851,6 +864,7 @@ void drop_graphs(mra_ctx *c)
 mra_status graph_pass(mra_ctx *c, const double *theta_dev, int B, double *loglik_dev, int *status_dev,
                       cudaStream_t s, bool with_regions)
 {
+    c->pass_count++;
     const int regions = with_regions ? 1 : 0;
     auto same = [&](const mra_ctx::GraphEntry &g) {
         return g.theta == theta_dev && g.loglik == loglik_dev && g.status == status_dev && g.B == B &&
@@ -961,22 +975,26 @@ int64_t leaf_of(const Partition &P, double a, double b)
     return i;
 }
 
-// Device buffers of one mra_predict call, freed on every exit.
-struct PredBufs {
-    std::vector<void *> ptrs;
-    mra_ctx *c;
-    explicit PredBufs(mra_ctx *ctx) : c(ctx) {}
-    template <typename X>
-    X *take(size_t count)
-    {
-        void *p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) return nullptr;
-        ptrs.push_back(p);
-        return (X *)p;
+// Grow-only device buffer of the prediction state.
+bool pred_reserve(unsigned char **buf, size_t *have, size_t need)
+{
+    if (need <= *have) return true;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc((void **)buf, need) != cudaSuccess) {
+        *buf = nullptr;
+        return false;
     }
-    ~PredBufs()
+    *have = need;
+    return true;
+}
+
+// Clears the pointers the kernels keep factors through, on every exit.
+struct KeepGuard {
+    mra_ctx *c;
+    ~KeepGuard()
     {
-        for (void *p : ptrs) cudaFree(p);
         c->keep_up = c->keep_y = nullptr;
         c->keep_li = nullptr;
         c->keep_stride = 0;
@@ -984,9 +1002,10 @@ struct PredBufs {
 };
 
 // Prediction for storage type T: the likelihood pass at theta keeping the
-// factors, the downward pass, the basis at the points (the leaf-basis kernel
-// on a tree view whose observation rows are the points) and one warp per
-// point.  Points come grouped by leaf (px, py, leaf sorted the same way).
+// factors and the downward pass (both skipped while the factors of the last
+// call still hold), the basis at the points (the leaf-basis kernel on a tree
+// view whose observation rows are the points) and one warp per point.
+// Points come grouped by leaf (sx, sy, sl sorted the same way).
 template <typename T, int RP>
 mra_status predict_impl(mra_ctx *c, const double *theta, const std::vector<double> &sx,
                         const std::vector<double> &sy, const std::vector<int64_t> &sl, double *mean_out,
@@ -997,31 +1016,31 @@ mra_status predict_impl(mra_ctx *c, const double *theta, const std::vector<doubl
     const int64_t np = (int64_t)sx.size(), NK = P.nnonleaf(), NL = P.nleaf();
     const int UC = (M - 1) * RP;
     const size_t stride = keep_up_doubles(M, RP);
-    PredBufs bufs(c);
-    double *d_px = bufs.take<double>((size_t)np), *d_py = bufs.take<double>((size_t)np);
-    int64_t *d_leaf = bufs.take<int64_t>((size_t)np);
-    double *d_mean = bufs.take<double>((size_t)np), *d_var = bufs.take<double>((size_t)np);
-    T *d_ua = bufs.take<T>((size_t)np * (size_t)std::max(UC, 1));
-    double *d_xi = bufs.take<double>((size_t)std::max<int64_t>(NK, 1) * RP);
-    double *d_keep = bufs.take<double>((size_t)std::max<int64_t>(NK, 1) * stride);
-    T *d_li = bufs.take<T>((size_t)NL * kKeepLd * kKeepLd);
-    double *d_ky = bufs.take<double>((size_t)NL * kKeepLd);
-    int32_t *d_bigidx = bufs.take<int32_t>((size_t)NL);
-    if (!d_px || !d_py || !d_leaf || !d_mean || !d_var || !d_ua || !d_xi || !d_keep || !d_li || !d_ky || !d_bigidx) {
+    KeepGuard guard{c};
+    // per-tree buffers: keep_up, L^{-1} and y of the leaves, xi, leaf -> large-leaf index
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + std::max<size_t>(bytes, 1));
+        return o;
+    };
+    const size_t o_keep = carve(sizeof(double) * (size_t)std::max<int64_t>(NK, 1) * stride);
+    const size_t o_li = carve(sizeof(T) * (size_t)NL * kKeepLd * kKeepLd);
+    const size_t o_ky = carve(sizeof(double) * (size_t)NL * kKeepLd);
+    const size_t o_xi = carve(sizeof(double) * (size_t)std::max<int64_t>(NK, 1) * RP);
+    const size_t o_bi = carve(sizeof(int32_t) * (size_t)NL);
+    const size_t tree_need = off;
+    if (tree_need > c->pred.tree_bytes) c->pred.valid = false;
+    if (!pred_reserve(&c->pred.tree, &c->pred.tree_bytes, tree_need)) {
         c->err = "cannot allocate the prediction buffers";
         return MRA_ENOMEM;
     }
-    // leaf -> large-leaf index
-    std::vector<int32_t> bigidx((size_t)NL, -1);
-    if (c->nbig > 0) {
-        std::vector<BigLeaf> hb((size_t)c->nbig);
-        if (cudaMemcpy(hb.data(), c->d_big, sizeof(BigLeaf) * hb.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
-            c->err = "cannot read the large-leaf list";
-            return MRA_ECUDA;
-        }
-        for (int k = 0; k < c->nbig; k++) bigidx[(size_t)hb[(size_t)k].leaf] = k;
-    }
-    // chunks of the basis evaluation: points below one level-(M-1) region
+    double *d_keep = (double *)(c->pred.tree + o_keep);
+    T *d_li = (T *)(c->pred.tree + o_li);
+    double *d_ky = (double *)(c->pred.tree + o_ky);
+    double *d_xi = (double *)(c->pred.tree + o_xi);
+    int32_t *d_bigidx = (int32_t *)(c->pred.tree + o_bi);
+    // per-point buffers
     const int rows = chunk_rows<T>();
     std::vector<Chunk> chunks;
     if (M > 1)
@@ -1032,32 +1051,57 @@ mra_status predict_impl(mra_ctx *c, const double *theta, const std::vector<doubl
                 chunks.push_back(Chunk{parent, 0, k});
             chunks.back().n++;
         }
-    Chunk *d_chunks = bufs.take<Chunk>(chunks.size());
-    if (!d_chunks) {
+    off = 0;
+    const size_t o_px = carve(sizeof(double) * (size_t)np), o_py = carve(sizeof(double) * (size_t)np);
+    const size_t o_lf = carve(sizeof(int64_t) * (size_t)np);
+    const size_t o_mn = carve(sizeof(double) * (size_t)np), o_vr = carve(sizeof(double) * (size_t)np);
+    const size_t o_ua = carve(sizeof(T) * (size_t)np * (size_t)std::max(UC, 1));
+    const size_t o_ch = carve(sizeof(Chunk) * chunks.size());
+    if (!pred_reserve(&c->pred.pt, &c->pred.pt_bytes, off)) {
         c->err = "cannot allocate the prediction buffers";
         return MRA_ENOMEM;
     }
+    double *d_px = (double *)(c->pred.pt + o_px), *d_py = (double *)(c->pred.pt + o_py);
+    int64_t *d_leaf = (int64_t *)(c->pred.pt + o_lf);
+    double *d_mean = (double *)(c->pred.pt + o_mn), *d_var = (double *)(c->pred.pt + o_vr);
+    T *d_ua = (T *)(c->pred.pt + o_ua);
+    Chunk *d_chunks = (Chunk *)(c->pred.pt + o_ch);
     cudaError_t e = cudaMemcpy(d_px, sx.data(), sizeof(double) * (size_t)np, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_py, sy.data(), sizeof(double) * (size_t)np, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_leaf, sl.data(), sizeof(int64_t) * (size_t)np, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(d_bigidx, bigidx.data(), sizeof(int32_t) * (size_t)NL, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !chunks.empty())
         e = cudaMemcpy(d_chunks, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_theta_stage, theta, sizeof(double) * 3, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "prediction upload");
-    // the likelihood pass, keeping the factors
-    c->keep_up = d_keep;
-    c->keep_stride = stride;
-    c->keep_li = d_li;
-    c->keep_y = d_ky;
-    int *d_st = (int *)(c->d_ll_stage + 1);
-    if (mra_status st = pass_ops(c, c->d_theta_stage, 1, c->d_ll_stage, d_st, (cudaStream_t)0, false)) return st;
-    c->keep_up = c->keep_y = nullptr;
-    c->keep_li = nullptr;
     const DevTree t = dev_tree(c);
+    int *d_st = (int *)(c->d_ll_stage + 1);
+    const bool reuse = c->pred.valid && c->pred.precision == c->precision && c->pred.gen == c->scratch_gen &&
+                       c->pred.pass_id == c->pass_count && memcmp(c->pred.theta, theta, sizeof(c->pred.theta)) == 0;
     int rc = 0;
-    for (int m = 1; m < M && !rc; m++) rc = launch_down<RP>(t, d_keep, stride, d_xi, m, nullptr);
+    if (!reuse) {
+        c->pred.valid = false;
+        // leaf -> large-leaf index
+        std::vector<int32_t> bigidx((size_t)NL, -1);
+        if (c->nbig > 0) {
+            std::vector<BigLeaf> hb((size_t)c->nbig);
+            if (cudaMemcpy(hb.data(), c->d_big, sizeof(BigLeaf) * hb.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                c->err = "cannot read the large-leaf list";
+                return MRA_ECUDA;
+            }
+            for (int k = 0; k < c->nbig; k++) bigidx[(size_t)hb[(size_t)k].leaf] = k;
+        }
+        e = cudaMemcpy(d_bigidx, bigidx.data(), sizeof(int32_t) * (size_t)NL, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "prediction upload");
+        // the likelihood pass, keeping the factors
+        c->keep_up = d_keep;
+        c->keep_stride = stride;
+        c->keep_li = d_li;
+        c->keep_y = d_ky;
+        if (mra_status st = pass_ops(c, c->d_theta_stage, 1, c->d_ll_stage, d_st, (cudaStream_t)0, false)) return st;
+        c->keep_up = c->keep_y = nullptr;
+        c->keep_li = nullptr;
+        for (int m = 1; m < M && !rc; m++) rc = launch_down<RP>(t, d_keep, stride, d_xi, m, nullptr);
+    }
     const Plan plan = make_plan(c);
     Work<T> w = make_work<T>(c, plan, 1);
     w.theta = c->d_theta_stage;
@@ -1107,6 +1151,13 @@ mra_status predict_impl(mra_ctx *c, const double *theta, const std::vector<doubl
     if (hs != MRA_OK) {
         c->err = "Cholesky factor not positive definite";
         return (mra_status)hs;
+    }
+    if (!reuse) {
+        memcpy(c->pred.theta, theta, sizeof(c->pred.theta));
+        c->pred.precision = c->precision;
+        c->pred.gen = c->scratch_gen;
+        c->pred.pass_id = c->pass_count;
+        c->pred.valid = true;
     }
     return MRA_OK;
 }
@@ -1592,14 +1643,15 @@ mra_status mra_predict(mra_ctx *c, const double *theta, const double *px, const 
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     if (mra_status st = ensure_stage(c, 1)) return st;
     if (mra_status st = ensure_capacity(c, 1)) return st;
-    // group the points by leaf (stable), outside points first
-    std::vector<int64_t> leaf((size_t)np), order((size_t)np);
+    // group the points by leaf (a stable counting sort), outside points first
+    const int64_t NL = c->P.nleaf();
+    std::vector<int64_t> leaf((size_t)np), order((size_t)np), pos((size_t)NL + 2, 0);
     for (int64_t k = 0; k < np; k++) {
         leaf[(size_t)k] = std::isfinite(px[k]) && std::isfinite(py[k]) ? leaf_of(c->P, px[k], py[k]) : -1;
-        order[(size_t)k] = k;
+        pos[(size_t)(leaf[(size_t)k] + 2)]++;
     }
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int64_t a, int64_t b) { return leaf[(size_t)a] < leaf[(size_t)b]; });
+    for (int64_t l = 1; l < NL + 2; l++) pos[(size_t)l] += pos[(size_t)(l - 1)];
+    for (int64_t k = 0; k < np; k++) order[(size_t)pos[(size_t)(leaf[(size_t)k] + 1)]++] = k;
     std::vector<double> sx((size_t)np), sy((size_t)np), m((size_t)np), v((size_t)np);
     std::vector<int64_t> sl((size_t)np);
     for (int64_t k = 0; k < np; k++) {
@@ -1724,7 +1776,7 @@ void mra_free(mra_ctx *c)
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
                     c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_leaves_m, c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
-                    c->d_reg_du, c->d_reg_lw};
+                    c->d_reg_du, c->d_reg_lw, c->pred.pt, c->pred.tree};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);

@@ -162,3 +162,28 @@ def test_predict_errors_and_empty_call():
         assert np.isnan(m[0]) and np.isnan(m[2]) and np.isfinite(m[1]) and np.isfinite(v[1])
         ref_m, ref_v = dense.predict(x, y, z, 3, 4, 9, [1.0, 0.1, 0.05], [0.5], [0.5])
         assert abs(m[1] - ref_m[0]) <= TOL64 and abs(v[1] - ref_v[0]) <= TOL64
+
+
+def test_predict_reuses_factors_only_while_valid():
+    """The factors of the last prediction pass are reused for the same theta
+    and recomputed after any other pass or theta: the values stay those of a
+    fresh context."""
+    x, y, z = synth.uniform(600, 17)
+    rng = np.random.default_rng(10)
+    px, py = _points(rng, 50)
+    t1, t2 = [1.0, 0.1, 0.05], [1.7, 0.2, 0.02]
+    with mra.MRA(x, y, z, 4, 4, 9, precision="mixed") as fresh:
+        r1 = fresh.predict(t1, px, py)
+    with mra.MRA(x, y, z, 4, 4, 9, precision="mixed") as fresh:
+        r2 = fresh.predict(t2, px, py)
+    with mra.MRA(x, y, z, 4, 4, 9, precision="mixed") as g:
+        for th, ref in ((t1, r1), (t1, r1), (t2, r2), (t1, r1)):
+            m, v = g.predict(th, px, py)
+            assert np.array_equal(m, ref[0]) and np.array_equal(v, ref[1])
+        g.loglik([t2])  # another pass: the kept factors of t1 are stale
+        m, v = g.predict(t1, px, py)
+        assert np.array_equal(m, r1[0]) and np.array_equal(v, r1[1])
+        g.set_precision("fp64")
+        m, v = g.predict(t1, px, py)
+        ref_m, ref_v = dense.predict(x, y, z, 4, 4, 9, t1, px, py)
+        assert np.max(np.abs(m - ref_m)) <= TOL64 and np.max(np.abs(v - ref_v)) <= TOL64
