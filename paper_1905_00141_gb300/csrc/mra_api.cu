@@ -1286,12 +1286,22 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         }
     }
     c->vbig_elems = voff;
-    // bucket set 1: the 48- and 64-observation leaves as one list, in leaf order
+    // bucket set 1: the 48- and 64-observation leaves as one list
     std::vector<int64_t> lbm;
     for (int64_t l = 0; l < P.nleaf(); l++) {
         const int64_t nl = P.leaf_off[(size_t)l + 1] - P.leaf_off[(size_t)l];
         if (nl > kLeafCap[0] && nl <= nmax_small) lbm.push_back(l);
     }
+    // largest leaves first within each list (the block scheduler starts CTAs
+    // in index order, so the longest leaves do not form the tail; the
+    // dynamic-scheduling idea of Sec. 4.1, cost ~ n^2 and up, inside one GPU)
+    auto by_size = [&](std::vector<int64_t> &v) {
+        std::stable_sort(v.begin(), v.end(), [&](int64_t a, int64_t b) {
+            return P.leaf_off[(size_t)a + 1] - P.leaf_off[(size_t)a] > P.leaf_off[(size_t)b + 1] - P.leaf_off[(size_t)b];
+        });
+    };
+    for (int k = 0; k < kLeafBuckets; k++) by_size(lb[k]);
+    by_size(lbm);
     // tiled large-leaf work lists
     std::vector<BigTile> items;
     {
