@@ -1574,10 +1574,13 @@ mra_status mra_loglik(mra_ctx *c, const double *theta, int batch, double *loglik
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy theta");
     mra_status st = enqueue(c, c->d_theta_stage, batch, c->d_ll_stage, d_st, (cudaStream_t)0, false);
     if (st != MRA_OK) return st;
-    std::vector<int> hs((size_t)batch);
-    e = cudaMemcpy(loglik, c->d_ll_stage, sizeof(double) * (size_t)batch, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), d_st, sizeof(int) * (size_t)batch, cudaMemcpyDeviceToHost);
+    // loglik and status are adjacent in the staging buffer: one copy back
+    std::vector<unsigned char> back(sizeof(double) * (size_t)batch + sizeof(int) * (size_t)batch);
+    e = cudaMemcpy(back.data(), c->d_ll_stage, back.size(), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy loglik");
+    std::vector<int> hs((size_t)batch);
+    memcpy(loglik, back.data(), sizeof(double) * (size_t)batch);
+    memcpy(hs.data(), back.data() + sizeof(double) * (size_t)batch, sizeof(int) * (size_t)batch);
     for (int b = 0; b < batch; b++)
         if (hs[(size_t)b] != MRA_OK) {
             c->err = hs[(size_t)b] == MRA_EINVAL ? "theta must be finite and positive" : "Cholesky factor not positive definite";
