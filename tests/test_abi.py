@@ -118,3 +118,20 @@ def test_stats_work_counts():
     assert s["r_hat"] == 30 and s["n_leaves"] == 4 ** 6 and s["n_used"] == 131072
     assert 5e9 < s["flops_per_theta"] < 5e10
     assert s["cov_evals_per_theta"] > 131072 * 6 * 30
+
+
+def test_host_only_context_refuses_prediction():
+    x, y, z = synth.uniform(100, 4, exact=False)
+    g = mra.MRA(x, y, z, 3, 4, 16, device=-1)
+    with pytest.raises(mra.MRAError) as e:
+        g.predict([1.0, 0.1, 0.05], [0.5], [0.5])
+    assert e.value.status == mra.EINVAL and "without a device" in str(e.value)
+    g.close()
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the compiled library the binding raises."""
+    monkeypatch.setattr(mra, "_lib", None)
+    monkeypatch.setattr(mra, "LIB_PATH", str(tmp_path / "libmra.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        mra.lib()
