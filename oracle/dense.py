@@ -118,10 +118,16 @@ class Partition:
         return out
 
 
-def sigma_mra(part: Partition, sigma2: float, beta: float, return_all: bool = False, extra=None):
+def sigma_mra(part: Partition, sigma2: float, beta: float, return_all: bool = False, extra=None,
+              first_level: int = 1):
     """Dense Sigma_MRA over the observations (and, with return_all, over the
     point set Z = observations + knots (+ the extra points, last), with the
-    knot bookkeeping).  Extra points must lie inside the root region."""
+    knot bookkeeping).  Extra points must lie inside the root region.
+
+    first_level > 1 keeps only the terms of levels first_level..M: the
+    covariance of the data given that the basis weights eta of the coarser
+    levels are zero (Sec. 1.1: the levels' terms are independent and add up).
+    The remainder recursion itself always runs from level 1."""
     M = part.M
     zx = [part.x]
     zy = [part.y]
@@ -153,7 +159,8 @@ def sigma_mra(part: Partition, sigma2: float, beta: float, return_all: bool = Fa
             CaQ = Cm[np.ix_(members, q)]
             CQQ = Cm[np.ix_(q, q)]
             proj[np.ix_(members, members)] = CaQ @ np.linalg.solve(CQQ, CaQ.T)
-        Sig += proj
+        if m + 1 >= first_level:
+            Sig += proj
         same_next = reg[m + 1][:, None] == reg[m + 1][None, :]
         Cm = np.where(same_next, Cm - proj, 0.0)
     same_leaf = reg[M - 1][:, None] == reg[M - 1][None, :]
