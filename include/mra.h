@@ -253,7 +253,10 @@ int mra_profile_read(mra_ctx *ctx, mra_kernel_time *out, int cap);
  *   compiled into the library, present on every device that loads it until
  *   the process exits.  The first call on a device looks up the array's device
  *   address (cudaGetSymbolAddress, with that device current); make that first
- *   call before any stream capture.  All calls on a device share the array and
+ *   call before any stream capture.  The lookup is made again when the
+ *   device's current context is not the one of the last lookup (after a
+ *   cudaDeviceReset, say), so the first call after such a reset must also come
+ *   outside stream capture.  All calls on a device share the array and
  *   it keeps the previous call's contents (every element a call reads it first
  *   writes): calls whose kernels may overlap on the GPU (different streams
  *   without ordering) race and give wrong results.  Calls no cudaMalloc,

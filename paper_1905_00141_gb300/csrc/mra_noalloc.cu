@@ -30,8 +30,45 @@ void set_thread_error(const std::string &msg); // mra_api.cu: text of mra_last_e
 
 namespace {
 
+// Device address of the array per device ordinal, and the context it was
+// looked up in: a reset device (cudaDeviceReset) gets a new primary context in
+// which the module, and with it the array, may sit elsewhere.
+struct NoallocSlot {
+    double *ptr = nullptr;
+    unsigned long long ctx_id = 0;
+    bool ctx_known = false;
+};
 std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[MRA_NOALLOC_MAX_DEVICES] = {nullptr};
+NoallocSlot g_noalloc_slot[MRA_NOALLOC_MAX_DEVICES];
+
+// Unique id of the context current on this thread (cuCtxGetCurrent and
+// cuCtxGetId, reached through the runtime's driver entry points so that the
+// library does not link the driver directly).  False when no context is
+// current yet or the entry points are missing.
+bool current_context_id(unsigned long long *id)
+{
+    typedef int (*get_current_fn)(void **);
+    typedef int (*get_id_fn)(void *, unsigned long long *);
+    static get_current_fn get_current = nullptr;
+    static get_id_fn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = (get_current_fn)f;
+            get_id = (get_id_fn)g;
+        }
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return false;
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
 
 // One CTA: V = C(S,S) + tau2 I (lower triangle), V = L L' in place, y = L^{-1} z,
 // loglik = -(log|V| + y'y + n log 2 pi) / 2.  Every scratch element read is
@@ -104,10 +141,14 @@ extern "C" mra_status mra_dense_loglik_noalloc(const double *x_dev, const double
     }
     double *scratch;
     {
-        // Once per device, with that device current: the host-side name of the
-        // array is not a device address, so ask the runtime for it.
+        // Once per device (and again if the device's context has changed since),
+        // with that device current: the host-side name of the array is not a
+        // device address, so ask the runtime for it.
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        NoallocSlot &slot = g_noalloc_slot[dev];
+        unsigned long long id = 0;
+        bool have_id = current_context_id(&id);
+        if (!slot.ptr || !have_id || !slot.ctx_known || slot.ctx_id != id) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
@@ -115,9 +156,12 @@ extern "C" mra_status mra_dense_loglik_noalloc(const double *x_dev, const double
                                       cudaGetErrorString(e));
                 return MRA_ECUDA;
             }
-            g_noalloc_ptr[dev] = (double *)p;
+            if (!have_id) have_id = current_context_id(&id); // the lookup made the primary context current
+            slot.ptr = (double *)p;
+            slot.ctx_id = id;
+            slot.ctx_known = have_id;
         }
-        scratch = g_noalloc_ptr[dev];
+        scratch = slot.ptr;
     }
     k_dense_noalloc<<<1, mra::NT, 0, (cudaStream_t)stream>>>(x_dev, y_dev, z_dev, (int)n, theta_dev, loglik_dev,
                                                             status_dev, scratch);
