@@ -1,0 +1,80 @@
+"""The batched clustered workload (n = 2,097,152, M = 9, J = 4, r = 32; 70% of
+the points in 8 Gaussian clusters, leaves of 0 to ~700 observations) at full
+size, in the launch configuration the benchmark times (64 theta per call),
+against the FP64 CPU oracle at four theta of its 4x4x4 grid -- the corner
+sigma2 = 2, beta = 0.2, tau2 = 0.005, where FP32 remainder recursions once
+failed, among them.
+
+The oracle's values are stored in tests/golden/full_size_oracle.txt by
+tests/golden/make_full_size_oracle.py (oracle/ and the seeded generators
+only).  Each stored line carries a fingerprint of the data it belongs to; when
+this machine's draw of the workload does not match it, the oracle runs here
+instead (about a minute and a half per theta on 8 host cores).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from golden_values import fingerprint_matches, golden
+from paper_1905_00141_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOLMIX = 1e-6
+TOL64 = 1e-10
+
+
+def reference(name, d):
+    """(theta rows, oracle loglik): the stored values when the data match,
+    else the oracle on this machine at the first stored theta."""
+    rows = golden(name)
+    assert rows, "no stored oracle values for " + name
+    if all(fingerprint_matches(d, r[3]) for r in rows):
+        return np.stack([r[0] for r in rows]), np.array([r[1] for r in rows]), "stored"
+    oracle.build()
+    th = rows[0][0][None, :]
+    ref, st = oracle.loglik(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], th)
+    assert st == oracle.OK
+    return th, ref, "computed here"
+
+
+@pytest.fixture(scope="module")
+def clustered():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1905_00141_gb300 import build, mra
+    build.build()
+    d = synth.clustered()
+    g = mra.MRA(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], precision="mixed")
+    yield d, g
+    g.close()
+
+
+def test_clustered_full_size_mixed_matches_oracle(clustered):
+    d, g = clustered
+    th, ref, src = reference("clustered", d)
+    n = g.stats()["n_used"]
+    assert n == len(d["x"])
+    grid = synth.theta_grid_4x4x4()
+    # the 64-theta call the benchmark times, then the checked rows picked out of it
+    ll = g.loglik(grid)
+    assert np.all(np.isfinite(ll))
+    pick = [int(np.flatnonzero(np.all(grid == t, axis=1))[0]) for t in th]
+    err = np.abs(ll[pick] - ref) / n
+    print("clustered mixed |dl|/n against the oracle (%s):" % src, err.tolist())
+    assert np.all(err <= TOLMIX), err
+
+
+def test_clustered_full_size_fp64_matches_oracle(clustered):
+    d, g = clustered
+    th, ref, _ = reference("clustered", d)
+    n = g.stats()["n_used"]
+    g.set_precision("fp64")
+    try:
+        ll = g.loglik(th)
+    finally:
+        g.set_precision("mixed")
+    err = np.abs(ll - ref) / n
+    print("clustered fp64 |dl|/n against the oracle:", err.tolist())
+    assert np.all(err <= TOL64), err

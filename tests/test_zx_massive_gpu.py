@@ -1,22 +1,38 @@
 """The 47,185,920-observation tree (M=12, J=4, r=16, mixed precision) at full
-size on one GPU, checked on sampled outputs the oracle computes one by one.
+size on one GPU.
 
-A leaf's terms (log|V|, z'V^{-1}z) depend only on its own observations and on
-the prior of its ancestors, which the knots fix; the knots depend on the data
-only through its bounding box.  So the oracle evaluates a reduced data set --
-the points that set the bounding box plus the observations of a few sampled
-leaves -- on the same M=12 tree (its empty subtrees cost nothing), and those
-leaves' terms must equal the GPU's terms from the full data, to the precision
-of mixed-mode leaf terms.  The full
-likelihood itself is checked for a finite value and an OK status, and the
-theta-batched call against single calls."""
+1. The full log-likelihood against the FP64 CPU oracle's value, stored in
+   tests/golden/full_size_oracle.txt by tests/golden/make_full_size_oracle.py
+   (oracle/ and the seeded generator only; about ten minutes of 8 host cores),
+   at 1e-6 per observation.
+2. Sampled outputs the oracle computes one by one.  A region's terms (d_R,
+   u_R: the log-determinant and quadratic form of its data with the coarser
+   basis weights held at zero) depend only on its own observations and on the
+   prior of its ancestors, which the knots fix; the knots depend on the data
+   only through its bounding box.  So the oracle evaluates a reduced data set
+   -- the points that set the bounding box plus the observations of a few
+   sampled regions -- on the same M=12 tree (its empty subtrees cost nothing),
+   and those regions' terms must equal the GPU's terms from the full data.
+   Sampled: 12 leaves and the largest one, and one region at each of the levels
+   M-1 .. M-4 (leaf parents up to subtrees of 256 leaves), so the prior, the
+   leaf posterior, the Gram blocks and four upward steps are all covered.
+3. The theta-batched call against single calls.
+"""
 import numpy as np
 import pytest
 
 import oracle
+from golden_values import fingerprint_matches, golden
 from paper_1905_00141_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+# Mixed-mode tolerances of region terms (the reasoning of test_gpu_parity.py): a
+# region's -(d + u + n log 2 pi) / 2 to 2e-5 per observation below the root (the
+# FP32-rounded basis enters V and the coarse part, and the two perturbations cancel
+# exactly only at the root), d and u alone to 1e-5 of (|term| + n).
+TOL_SUM = 2e-5
+TOL_TERM = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -36,45 +52,83 @@ def massive():
     g.close()
 
 
-def test_massive_sampled_leaves_match_oracle(massive):
+def test_massive_full_loglik_matches_oracle(massive):
+    d, g = massive
+    rows = golden("massive")
+    assert rows, "no stored oracle value for the 47M tree"
+    th, ref, n_used, fp = rows[0]
+    if not fingerprint_matches(d, fp):
+        pytest.fail("this machine's draw of the 47M workload differs from the one the stored oracle value "
+                    "belongs to (fingerprint %s)" % (fp,))
+    ll = g.loglik(th)[0]
+    n = g.stats()["n_used"]
+    assert n == n_used
+    err = abs(ll - ref) / n
+    print("massive mixed |dl|/n against the oracle: %.3g (loglik %.6f, oracle %.6f)" % (err, ll, ref))
+    assert err <= 1e-6
+
+
+def _counts_by_level(off, J, M):
+    """Observations below every region of levels 1..M (index m-1: array by region)."""
+    cnt = np.diff(off).astype(np.int64)
+    out = [cnt]
+    for _ in range(M - 1):
+        out.append(out[-1].reshape(-1, J).sum(1))
+    return out[::-1]
+
+
+def test_massive_sampled_regions_match_oracle(massive):
     d, g = massive
     th = d["theta"][0]
     st = g.stats()
+    M, J = d["M"], d["J"]
     assert st["n_used"] == len(d["x"])
     rg = g.region_terms(th)
     assert rg["status"] == 0 and np.isfinite(rg["loglik"])
     tr = g.tree()
     off, perm = np.asarray(tr["leaf_off"]), np.asarray(tr["perm"])
     nleaf = len(off) - 1
-    lvl_leaf = st["n_regions"] - nleaf  # global id of the first leaf
+    per_level = _counts_by_level(off, J, M)
+    lvl_off = np.concatenate([[0], np.cumsum([len(c) for c in per_level])])
     ext = {int(np.argmin(d["x"])), int(np.argmax(d["x"])), int(np.argmin(d["y"])), int(np.argmax(d["y"]))}
     rng = np.random.default_rng(7)
     counts = np.diff(off)
     cand = np.flatnonzero(counts > 0)
-    picks = list(rng.choice(cand, 12, replace=False)) + [int(np.argmax(counts))]
-    picks = [c for c in picks if not (set(perm[off[c]:off[c + 1]].tolist()) & ext)]
-    assert len(picks) >= 8
-    rows = sorted(ext) + [int(k) for c in picks for k in perm[off[c]:off[c + 1]]]
-    xr, yr, zr = d["x"][rows], d["y"][rows], d["z"][rows]
-    t = oracle.Tree(xr, yr, zr, d["M"], d["J"], d["r"])
+    leaves = list(rng.choice(cand, 12, replace=False)) + [int(np.argmax(counts))]
+    leaves = [c for c in leaves if not (set(perm[off[c]:off[c + 1]].tolist()) & ext)]
+    assert len(leaves) >= 8
+    picks = [(M, c) for c in leaves]  # (level, index within the level)
+    for k in range(1, 5):
+        m = M - k
+        nonempty = np.flatnonzero(per_level[m - 1] > 0)
+        picks.append((m, int(rng.choice(nonempty))))
+    rows = set(ext)
+    for m, i in picks:
+        span = J ** (M - m)
+        a, b = off[i * span], off[(i + 1) * span]
+        rows.update(int(v) for v in perm[a:b])
+    rows = sorted(rows)
+    t = oracle.Tree(d["x"][rows], d["y"][rows], d["z"][rows], M, J, d["r"])
     try:
         ro = t.region_terms(th)
         eo = t.export()
     finally:
         t.close()
     assert ro["status"] == 0
-    ooff = np.asarray(eo["leaf_off"])
-    for c in picks:
-        nl = off[c + 1] - off[c]
-        assert ooff[c + 1] - ooff[c] == nl  # the same leaf holds the same observations
-        gid = lvl_leaf + c
-        for key in ("d", "u"):
-            # mixed-mode leaf terms are those of the FP32-rounded basis U, a model
-            # within ~1e-7 of the exact one, whose log|V| and z'V^{-1}z move by up
-            # to ~1e-5 relative on their own (the upward pass cancels most of it);
-            # a wrong index or term would move them by O(1)
-            assert abs(rg[key][gid] - ro[key][gid]) <= 1e-4 * (abs(ro[key][gid]) + nl), \
-                (c, key, rg[key][gid], ro[key][gid])
+    o_level = _counts_by_level(np.asarray(eo["leaf_off"]), J, M)
+    worst = {}
+    for m, i in picks:
+        nr = int(per_level[m - 1][i])
+        assert int(o_level[m - 1][i]) == nr  # the same region holds the same observations
+        gid = int(lvl_off[m - 1] + i)
+        e_sum = abs((rg["d"][gid] + rg["u"][gid]) - (ro["d"][gid] + ro["u"][gid])) / nr
+        e_d = abs(rg["d"][gid] - ro["d"][gid]) / (abs(ro["d"][gid]) + nr)
+        e_u = abs(rg["u"][gid] - ro["u"][gid]) / (abs(ro["u"][gid]) + nr)
+        w = worst.setdefault("leaf" if m == M else "level %d" % m, [0.0, 0.0, 0.0])
+        w[0], w[1], w[2] = max(w[0], e_sum), max(w[1], e_d), max(w[2], e_u)
+        assert e_sum <= TOL_SUM and e_d <= TOL_TERM and e_u <= TOL_TERM, (m, i, nr, e_sum, e_d, e_u)
+    print("massive sampled regions, max (|d+u| err / n, d err, u err):", worst)
+    assert nleaf == J ** (M - 1)
 
 
 def test_massive_batch_equals_single_calls(massive):
