@@ -538,6 +538,11 @@ def clustered_line(torch, stream, flush, local, precision="mixed", calls=2, warm
         sys.path.pop(0)
     d = synth.clustered()
     grid = synth.theta_grid_4x4x4()
+    rows0 = golden("clustered")
+    for r in rows0:
+        k = int(np.argmin(np.abs(grid - r[0]).sum(axis=1)))
+        if np.allclose(grid[k], r[0], rtol=1e-12, atol=0):
+            grid[k] = r[0]
     g = mra.MRA(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], device=local, precision=precision)
     try:
         n = g.stats()["n_used"]
@@ -557,7 +562,9 @@ def clustered_line(torch, stream, flush, local, precision="mixed", calls=2, warm
         acc = None
         pick = []
         if rows and all(fingerprint_matches(d, r[3]) for r in rows):
-            pick = [int(np.flatnonzero(np.all(grid == r[0], axis=1))[0]) for r in rows]
+            # the stored theta sit in their slots of the grid up to the last bits
+            # of the platform's libm; the accuracy call uses the stored values
+            pick = [int(np.argmin(np.abs(grid - r[0]).sum(axis=1))) for r in rows]
             ref = np.array([r[1] for r in rows])
             acc = {"against": "FP64 CPU oracle (stored values)", "theta_index": pick,
                    precision: float(np.max(np.abs(ll[pick] - ref)) / n)}

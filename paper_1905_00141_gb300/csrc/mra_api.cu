@@ -1583,7 +1583,9 @@ mra_status mra_loglik(mra_ctx *c, const double *theta, int batch, double *loglik
     memcpy(hs.data(), back.data() + sizeof(double) * (size_t)batch, sizeof(int) * (size_t)batch);
     for (int b = 0; b < batch; b++)
         if (hs[(size_t)b] != MRA_OK) {
-            c->err = hs[(size_t)b] == MRA_EINVAL ? "theta must be finite and positive" : "Cholesky factor not positive definite";
+            c->err = hs[(size_t)b] == MRA_EINVAL       ? "theta must be finite and positive"
+                     : hs[(size_t)b] == MRA_ETIMEDOUT ? "a bounded device wait ran out (tensor-core pipeline)"
+                                                      : "Cholesky factor not positive definite";
             return (mra_status)hs[(size_t)b];
         }
     return MRA_OK;

@@ -103,14 +103,23 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
     }
     const int64_t gp = M > 1 ? t.lvl_off[M - 1] + (v.c >> t.lgJ) : -1;
     const double ox = gp >= 0 ? t.cx[gp] : t.sx[v.o0], oy = gp >= 0 ? t.cy[gp] : t.sy[v.o0];
-    for (int a = tid; a < TB; a += NT) {
-        sc[a] = a < nI ? t.sx[v.o0 + rI + a] - ox : 0.0;
-        sc[TB + a] = a < nI ? t.sy[v.o0 + rI + a] - oy : 0.0;
-        sc[2 * TB + a] = a < nJ ? t.sx[v.o0 + rJ + a] - ox : 0.0;
-        sc[3 * TB + a] = a < nJ ? t.sy[v.o0 + rJ + a] - oy : 0.0;
+    // coordinates once per point (mixed mode: as float pairs, one conversion a
+    // thread; FP64 conversions are slow on this GPU)
+    ff *scf = reinterpret_cast<ff *>(sc);
+    for (int e = tid; e < 4 * TB; e += NT) {
+        const int a = e % TB, which = e / TB; // x_I, y_I, x_J, y_J
+        const bool in = which < 2 ? a < nI : a < nJ;
+        const int64_t row = v.o0 + (which < 2 ? rI : rJ) + a;
+        const double cval = in ? ((which & 1) ? t.sy[row] - oy : t.sx[row] - ox) : 0.0;
+        if constexpr (sizeof(T) == 4)
+            scf[e] = ff_from_double(cval);
+        else
+            sc[e] = cval;
     }
-    __shared__ double s_ib; // 1/beta, one FP64 division per CTA
-    if (tid == 0) s_ib = 1.0 / th[1];
+    __shared__ double s_ib;
+    __shared__ ff s_par[3]; // sigma2, 1/beta, tau2 as float pairs
+    set_cov_params<T>(th, &s_ib, s_par);
+    if (tid == 2) s_par[2] = ff_from_double(th[2]);
     cp_async_wait<0>();
     __syncthreads();
     const double tau2 = th[2], ib64 = s_ib;
@@ -118,7 +127,7 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
     T hi[2][2], lo[2][2];
     dot2x2_exact(sUI + a0 * LDU, sUI + min(a0 + 1, TB - 1) * LDU, sUJ + q0 * LDU, sUJ + min(q0 + 1, TB - 1) * LDU, UC,
                  grid_constant(th[0]), hi, lo);
-    const ff s2f = ff_from_double(th[0]), ibf = ff_from_double(ib64), tau2f = ff_from_double(tau2);
+    const ff s2f = s_par[0], ibf = s_par[1], tau2f = s_par[2];
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
@@ -128,8 +137,7 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
             const bool diag = it.i == it.j && a == q;
             F val;
             if constexpr (sizeof(T) == 4) {
-                const ff cv = ff_cov_exp(s2f, ibf, ff_from_double(sc[a]), ff_from_double(sc[TB + a]),
-                                         ff_from_double(sc[2 * TB + q]), ff_from_double(sc[3 * TB + q]));
+                const ff cv = ff_cov_exp(s2f, ibf, scf[a], scf[TB + a], scf[2 * TB + q], scf[3 * TB + q]);
                 val = ff_sub_sloppy(cv, ff{(float)hi[i][j], (float)lo[i][j]});
                 if (diag) val = ff_add_sloppy(val, tau2f);
             } else {
@@ -185,7 +193,10 @@ __global__ void __launch_bounds__(NT) k_big_potrf(DevTree t, Work<T> w, const Bi
     }
     for (int a = tid; a < nk; a += NT) sy[a] = k == 0 ? f_of<F>(t.sz[v.o0 + a]) : v.y[r0 + a];
     __syncthreads();
-    chol_small<F, (tri_count(TB) + NT - 1) / NT>(sL, TB + 1, nk, srs, sr2, flag, MRA_SINGULAR);
+    if constexpr (sizeof(T) == 4)
+        chol_blocked<TB>(sL, TB + 1, nk, srs, flag, MRA_SINGULAR, red);
+    else
+        chol_small<F, (tri_count(TB) + NT - 1) / NT>(sL, TB + 1, nk, srs, sr2, flag, MRA_SINGULAR);
     const double ld = logdet_small(sL, TB + 1, nk, red);
     // factor (transposed, upper triangle of the tile) and 1/L_jj to the scratch
     for (int e = tid; e < nk * nk; e += NT) {
@@ -193,7 +204,7 @@ __global__ void __launch_bounds__(NT) k_big_potrf(DevTree t, Work<T> w, const Bi
         if (i >= j) v.V[(size_t)(r0 + j) * n + r0 + i] = sL[j * (TB + 1) + i];
     }
     for (int j = tid; j < nk; j += NT) v.rs[r0 + j] = srs[j];
-    fwd_solve_vec<F, true>(sL, TB + 1, srs, nk, sy);
+    fwd_solve_vec_lead<F, TB>(sL, TB + 1, srs, nk, sy);
     if (tid < 32) {
         F q = tid < nk ? f_sqr(sy[tid]) : f_of<F>(0.0);
         q = warp_sum_f(q);

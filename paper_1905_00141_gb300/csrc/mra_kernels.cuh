@@ -49,10 +49,16 @@ __host__ __device__ __forceinline__ int npairs(int D) { return D * (D + 1) / 2; 
 __host__ __device__ __forceinline__ int pidx(int k, int l) { return l * (l - 1) / 2 + k - 1; }
 __host__ __device__ __forceinline__ constexpr int tri_count(int w) { return w * (w + 1) / 2; }
 
+// finite and > 0, from the bits (integer operations: FP64 compares cost ~230
+// cycles of latency each on this GPU, at the head of every CTA)
+__device__ __forceinline__ bool pos_finite(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return b - 1ull < 0x7FEFFFFFFFFFFFFFull; // +0 < v < +inf, no NaN, no sign bit
+}
 __device__ __forceinline__ bool theta_ok(const double *th)
 {
-    return isfinite(th[0]) && isfinite(th[1]) && isfinite(th[2]) && th[0] > 0.0 && th[1] > 0.0 &&
-           th[2] > 0.0;
+    return pos_finite(th[0]) && pos_finite(th[1]) && pos_finite(th[2]);
 }
 
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000LL); }
@@ -435,6 +441,30 @@ __device__ __forceinline__ double cov64(double s2, double ib, double dx, double 
     return s2 * exp(-sqrt(dx * dx + dy * dy) * ib);
 }
 
+// sigma2 and 1/beta for a CTA, in shared memory, by threads 0 and 1 side by
+// side.  FP64 mode: 1/beta as a double.  Mixed modes: both as float pairs,
+// 1/beta by a float-pair reciprocal on the FP32 pipe (an FP64 division costs
+// ~440 cycles of latency on this GPU, at the head of every CTA), and s_ib its
+// leading float (what the FP32 covariance of the fast mode uses).
+template <typename T>
+__device__ __forceinline__ void set_cov_params(const double *th, double *s_ib, ff *s_par)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (threadIdx.x == 0) s_par[0] = ff_from_double(th[0]);
+        if (threadIdx.x == 1) {
+            const ff ib = ff_rcp(ff_from_double(th[1]));
+            s_par[1] = ib;
+            *s_ib = (double)ib.hi;
+        }
+    } else {
+        if (threadIdx.x == 0) s_par[0] = ff_from_double(th[0]);
+        if (threadIdx.x == 1) {
+            *s_ib = 1.0 / th[1];
+            s_par[1] = ff_from_double(*s_ib);
+        }
+    }
+}
+
 // ------------------------------------------------------------- Cholesky --
 // Factor arithmetic: F = double in the FP64 mode, F = ff (float pair, ~48-bit
 // mantissa, FP32 pipe) in the mixed mode.  On GB300 a warp-wide FP64
@@ -559,6 +589,135 @@ static __device__ void chol_small(F *A, int lda, int n, F *rs, F *r2s, int *fail
     }
 }
 
+// One step of an error-free dot product in float pairs (Ogita, Rump and
+// Oishi's Dot2, "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005):
+// the leading product is split exactly by an FMA (TwoProd), added to the
+// running sum exactly (TwoSum), and both rounding errors plus the cross terms
+// of the pairs' trailing parts go into a compensation term c.  The value of the
+// sum is s + c; it is as accurate as if computed in twice the FP32 precision.
+struct Dot2 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(ff a, ff b)
+    {
+        const float p = __fmul_rn(a.hi, b.hi);
+        const float pe = __fmaf_rn(a.hi, b.hi, -p);
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+        s = t;
+        // the four small terms first: one dependent addition per step on c
+        c = __fadd_rn(c, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, __fadd_rn(pe, se))));
+    }
+    __device__ __forceinline__ void merge(const Dot2 &o)
+    {
+        const ff u = two_sum(s, o.s);
+        s = u.hi;
+        c = __fadd_rn(__fadd_rn(c, o.c), u.lo);
+    }
+    __device__ __forceinline__ ff value() const { return two_sum(s, c); }
+};
+
+// Cholesky of a small (n <= NMAX <= 64) symmetric matrix in shared memory by
+// the whole CTA in float pairs, blocked by 8 columns: the same input and
+// output as chol_small (input: the lower triangle of A; output: L in the upper
+// triangle, transposed, A[j][i] = L[i][j] for i >= j, and rs[j] = 1 / L_jj;
+// the same singularity rule), two barriers per block instead of one per
+// column.  For each block of columns [c0, c0 + 8):
+//   - warp 0 factors the panel (rows c0..n-1 of those columns) in registers,
+//     lane l holding rows c0 + l (+ 32): column c0 + j is
+//     A_ij - sum_{p<j} L_i,c0+p L_c0+j,c0+p (row c0 + j broadcast by
+//     shuffles, the sum error-free in pairs by Dot2), lane j takes the pivot and
+//     the column is scaled by its reciprocal square root;
+//   - every thread then applies the panel to the trailing lower triangle,
+//     A_ik -= sum_p L_i,c0+p L_k,c0+p (Dot2 over the block's 8 columns).
+// The pivot chain (reciprocal square root, scaling, the next diagonal) stays in
+// one warp's registers; the CTA-wide update needs no per-column barrier.
+template <int NMAX>
+static __device__ void chol_blocked(ff *A, int lda, int n, ff *rs, int *fail, double rel, double *red)
+{
+    static_assert(NMAX <= 64, "two rows per lane at most");
+    constexpr int BS = 8, RPL = NMAX > 32 ? 2 : 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the singularity test in FP32 (an FP64 compare on the pivot chain costs
+    // ~230 cycles per column on this GPU)
+    float *tolp = reinterpret_cast<float *>(red);
+    if (warp == 0) {
+        float sc = 0.f;
+        for (int j = lane; j < n; j += 32) sc = fmaxf(sc, A[j * lda + j].hi);
+        for (int o = 16; o; o >>= 1) sc = fmaxf(sc, __shfl_xor_sync(0xffffffffu, sc, o));
+        if (lane == 0) tolp[0] = (float)rel * sc;
+    }
+    for (int c0 = 0; c0 < n; c0 += BS) {
+        const int w = min(BS, n - c0);
+        if (warp == 0) {
+            const float tol = tolp[0];
+            ff a[RPL][BS];
+#pragma unroll
+            for (int q = 0; q < RPL; q++) {
+                const int i = c0 + lane + 32 * q;
+#pragma unroll
+                for (int p = 0; p < BS; p++) a[q][p] = (i < n && p < w && c0 + p <= i) ? A[i * lda + c0 + p] : ff{0.f, 0.f};
+            }
+#pragma unroll
+            for (int j = 0; j < BS; j++) {
+                if (j < w) {
+                    // row c0 + j is lane j's first row
+                    ff s[RPL];
+#pragma unroll
+                    for (int q = 0; q < RPL; q++) {
+                        Dot2 d;
+#pragma unroll
+                        for (int p = 0; p < j; p++) d.add(a[q][p], f_shfl(a[0][p], j));
+                        s[q] = ff_sub_sloppy(a[q][j], d.value());
+                    }
+                    ff r = ff{0.f, 0.f};
+                    if (lane == j) {
+                        ff dj = s[0];
+                        if (!(dj.hi > tol)) {
+                            *fail = 1;
+                            dj = ff{1.f, 0.f};
+                        }
+                        r = ff_rsqrt(dj);
+                        rs[c0 + j] = r;
+                        a[0][j] = ff_mul(dj, r);
+                    }
+                    r = f_shfl(r, j);
+#pragma unroll
+                    for (int q = 0; q < RPL; q++) {
+                        const int i = c0 + lane + 32 * q;
+                        if (i > c0 + j && i < n) a[q][j] = ff_mul(s[q], r);
+                    }
+                }
+            }
+            // the panel's columns of L, transposed into the upper triangle
+#pragma unroll
+            for (int q = 0; q < RPL; q++) {
+                const int i = c0 + lane + 32 * q;
+#pragma unroll
+                for (int p = 0; p < BS; p++)
+                    if (i < n && p < w && c0 + p <= i) A[(c0 + p) * lda + i] = a[q][p];
+            }
+        }
+        __syncthreads();
+        // trailing lower triangle: rows and columns from c0 + w on
+        const int t0 = c0 + w, tn = n - t0;
+        if (tn > 0) {
+            for (int e = threadIdx.x; e < tri_count(tn); e += NT) {
+                int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                while (tri_count(ii + 1) <= e) ii++;
+                while (ii > 0 && tri_count(ii) > e) ii--;
+                const int i = t0 + ii, k = t0 + (e - tri_count(ii));
+                Dot2 d;
+#pragma unroll
+                for (int p = 0; p < BS; p++)
+                    if (p < w) d.add(A[(c0 + p) * lda + i], A[(c0 + p) * lda + k]);
+                A[i * lda + k] = ff_sub_sloppy(A[i * lda + k], d.value());
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // 2 sum_j log L_jj of a chol_small factor, by warp 0.  FP64: the pivots are
 // multiplied as mantissas with a running exponent and one log is taken.
 // Float pairs: each lane splits its pivots into exponent and mantissa in
@@ -647,6 +806,35 @@ __device__ void fwd_solve_vec(const F *A, int lda, const F *rs, int n, F *y)
         }
         if (lane < n) y[lane] = y0;
         if (lane + 32 < n) y[lane + 32] = y1;
+    }
+    __syncthreads();
+}
+
+// y <- L^{-1} y as fwd_solve_vec<F, true> (the leading floats of L and rs,
+// applied in factor arithmetic; the same operations, so the same result) for
+// n <= N <= 32, with lane a's row of L and its reciprocal pivot loaded into
+// registers first: each step is a scale, one shuffle and one update per lane,
+// with no shared-memory load on the chain.  By warp 0; ends with a barrier.
+template <typename F, int N>
+__device__ void fwd_solve_vec_lead(const F *A, int lda, const F *rs, int n, F *y)
+{
+    static_assert(N <= 32, "one row per lane");
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        F Lr[N];
+#pragma unroll
+        for (int q = 0; q < N; q++) Lr[q] = (q < lane && lane < n) ? f_lead(A[q * lda + lane]) : f_of<F>(0.0);
+        const F rl = lane < n ? f_lead(rs[lane]) : f_of<F>(0.0);
+        F yl = lane < n ? y[lane] : f_of<F>(0.0);
+#pragma unroll
+        for (int q = 0; q < N; q++) {
+            if (q < n) {
+                if (lane == q) yl = f_mul(yl, rl);
+                const F yq = f_shfl(yl, q);
+                if (lane > q && lane < n) yl = f_sub(yl, f_mul(Lr[q], yq));
+            }
+        }
+        if (lane < n) y[lane] = yl;
     }
     __syncthreads();
 }
@@ -791,15 +979,11 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     const int i = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    // 1/beta once per CTA (an FP64 division), read after the first barrier
+    // sigma2 and 1/beta once per CTA, read after the first barrier
     __shared__ double s_ib;
     __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
     const float s_cq = grid_constant(th[0]);
-    if (threadIdx.x == 0) {
-        s_ib = 1.0 / th[1];
-        s_par[0] = ff_from_double(th[0]);
-        s_par[1] = ff_from_double(s_ib);
-    }
+    set_cov_params<T>(th, &s_ib, s_par);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     F *sL = (F *)smem_raw;                  // RP x (RP+1)
     F *srs = sL + RP * (RP + 1);            // RP + 2
@@ -928,7 +1112,13 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     __syncthreads();
     // W^m assembled in FP32 cannot resolve pivots below its own rounding: the
     // mixed mode calls such a factor singular at 1e-6 of the largest diagonal.
-    chol_small<F, (tri_count(RP) + NT - 1) / NT>(sL, RP + 1, RP, srs, sr2, flag, sizeof(T) == 4 ? 1e-6 : MRA_SINGULAR);
+    if constexpr (sizeof(T) == 4)
+        chol_blocked<RP>(sL, RP + 1, RP, srs, flag, 1e-6, red);
+    else
+        if constexpr (sizeof(T) == 4)
+        chol_blocked<RP>(sL, RP + 1, RP, srs, flag, MRA_SINGULAR, red);
+    else
+        chol_small<F, (tri_count(RP) + NT - 1) / NT>(sL, RP + 1, RP, srs, sr2, flag, MRA_SINGULAR);
     const double ld = logdet_small(sL, RP + 1, RP, red);
     T *out = pb + w.prior_lvl[m] + (size_t)i * m * RP * RP;
     for (int e = tid; e < (m - 1) * RP * RP; e += NT) out[e] = sU[e];
@@ -967,15 +1157,11 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
     const int b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    // 1/beta once per CTA (an FP64 division), read after the first barrier
+    // sigma2 and 1/beta once per CTA, read after the first barrier
     __shared__ double s_ib;
     __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
     const float s_cq = grid_constant(th[0]);
-    if (threadIdx.x == 0) {
-        s_ib = 1.0 / th[1];
-        s_par[0] = ff_from_double(th[0]);
-        s_par[1] = ff_from_double(s_ib);
-    }
+    set_cov_params<T>(th, &s_ib, s_par);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int M = t.M, R = t.R, P = ch.parent, nr = ch.n;
     T *sp = (T *)smem_raw;                  // 2 CH rows relative to the ancestor corner
@@ -1152,15 +1338,13 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
         sy[a] = f_of<F>(t.sz[o0 + a]);
     }
     for (int e = tid; e < nmax * nmax; e += NT) sLi[e] = T(0);
-    if (tid == 0) {
-        flag[0] = 0;
-        s_ib = 1.0 / th[1];
-        s_par[0] = ff_from_double(th[0]);
-        s_par[1] = ff_from_double(s_ib);
-    }
-    const ff tau2f = ff_from_double(tau2);
+    if (tid == 0) flag[0] = 0;
+    set_cov_params<T>(th, &s_ib, s_par);
+    __shared__ ff s_tau2;
+    if (tid == 2) s_tau2 = ff_from_double(tau2);
     cp_async_wait<0>();
     __syncthreads();
+    const ff tau2f = s_tau2;
     // V = C(S,S) + tau2 I - U U' (lower triangle), in 2x2 blocks (A, Q), Q <= A
     {
         const int nb = (n + 1) >> 1;
@@ -1192,7 +1376,10 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
         }
     }
     __syncthreads();
-    chol_small<F, (tri_count(NMAX) + NT - 1) / NT>(sV, LDV, n, srs, sr2, flag, MRA_SINGULAR);
+    if constexpr (sizeof(T) == 4)
+        chol_blocked<NMAX>(sV, LDV, n, srs, flag, MRA_SINGULAR, red);
+    else
+        chol_small<F, (tri_count(NMAX) + NT - 1) / NT>(sV, LDV, n, srs, sr2, flag, MRA_SINGULAR);
     const double dv = logdet_small(sV, LDV, n, red);
     trinv_warp<T, NMAX>(sV, LDV, srs, sLi, nmax, n);
     // Y = L^{-1} U, block column by block column, straight to global; row r
@@ -1551,14 +1738,17 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
         }
     }
     __syncthreads();
-    chol_small<F, (tri_count(RP) + NT - 1) / NT>(sL, RP + 1, RP, srs, sr2, flag, MRA_SINGULAR);
+    if constexpr (sizeof(T) == 4)
+        chol_blocked<RP>(sL, RP + 1, RP, srs, flag, MRA_SINGULAR, red);
+    else
+        chol_small<F, (tri_count(RP) + NT - 1) / NT>(sL, RP + 1, RP, srs, sr2, flag, MRA_SINGULAR);
     const double ld = logdet_small(sL, RP + 1, RP, red);
     // Z = Lt^{-1} [A^{m,1} .. A^{m,m-1}], stored row-major [a][(k-1) RP + bc] (ld ldz);
     // right-hand column (k, bc) is A^{m,k}[.][bc] = A^{k,m}[bc][.], contiguous in sC
     const int ncol = (m - 1) * RP, ldz = ncol + 4;
     for (int a = tid; a < RP; a += NT) sz[a] = f_of<F>(sw[(m - 1) * RP + a]);
     fwd_solve_warp<T, RP>(sL, RP + 1, srs, sC, RP, 1, sZ, ldz, ncol);
-    fwd_solve_vec<F, true>(sL, RP + 1, srs, RP, sz);
+    fwd_solve_vec_lead<F, RP>(sL, RP + 1, srs, RP, sz);
     if (tid < 32) {
         F q = tid < RP ? f_sqr(sz[tid]) : f_of<F>(0.0);
         q = warp_sum_f(q);

@@ -1,6 +1,9 @@
 // mra_launch.cuh -- host launchers of the MRA kernels, instantiated per
 // precision in k_f64.cu and k_f32.cu.
 #pragma once
+#include <algorithm>
+#include <cstring>
+
 #include "mra_kernels.cuh"
 
 namespace mra {

@@ -27,12 +27,15 @@ from paper_1905_00141_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# Mixed-mode tolerances of region terms (the reasoning of test_gpu_parity.py): a
-# region's -(d + u + n log 2 pi) / 2 to 2e-5 per observation below the root (the
-# FP32-rounded basis enters V and the coarse part, and the two perturbations cancel
-# exactly only at the root), d and u alone to 1e-5 of (|term| + n).
-TOL_SUM = 2e-5
-TOL_TERM = 1e-5
+# Mixed-mode tolerances of region terms, relative to (|d| + |u| + n) for d + u and to
+# (|term| + n) for d and u alone.  The path carries the FP32-rounded whitened basis,
+# which enters a leaf's V = C - U U' + tau2 I and its coarse part U U'; the two
+# perturbations cancel exactly only at the root.  A leaf's own terms carry the
+# rounding of U U' amplified by sigma2 / tau2 (here 100): measured up to 8.8e-6, bound
+# 3e-5.  Regions above the leaves: measured up to 4.4e-7, bound 3e-6.  The root (the
+# likelihood) is held to 1e-6 per observation above.
+TOL_LEAF = 3e-5
+TOL_UPPER = 3e-6
 
 
 @pytest.fixture(scope="module")
@@ -121,13 +124,15 @@ def test_massive_sampled_regions_match_oracle(massive):
         nr = int(per_level[m - 1][i])
         assert int(o_level[m - 1][i]) == nr  # the same region holds the same observations
         gid = int(lvl_off[m - 1] + i)
-        e_sum = abs((rg["d"][gid] + rg["u"][gid]) - (ro["d"][gid] + ro["u"][gid])) / nr
+        e_sum = abs((rg["d"][gid] + rg["u"][gid]) - (ro["d"][gid] + ro["u"][gid])) / \
+            (abs(ro["d"][gid]) + abs(ro["u"][gid]) + nr)
         e_d = abs(rg["d"][gid] - ro["d"][gid]) / (abs(ro["d"][gid]) + nr)
         e_u = abs(rg["u"][gid] - ro["u"][gid]) / (abs(ro["u"][gid]) + nr)
         w = worst.setdefault("leaf" if m == M else "level %d" % m, [0.0, 0.0, 0.0])
         w[0], w[1], w[2] = max(w[0], e_sum), max(w[1], e_d), max(w[2], e_u)
-        assert e_sum <= TOL_SUM and e_d <= TOL_TERM and e_u <= TOL_TERM, (m, i, nr, e_sum, e_d, e_u)
-    print("massive sampled regions, max (|d+u| err / n, d err, u err):", worst)
+        tol = TOL_LEAF if m == M else TOL_UPPER
+        assert e_sum <= tol and e_d <= tol and e_u <= tol, (m, i, nr, e_sum, e_d, e_u)
+    print("massive sampled regions, max relative (d+u, d, u) errors:", worst)
     assert nleaf == J ** (M - 1)
 
 
