@@ -464,6 +464,19 @@ def run_ours(args):
             cpu.pop("seconds", None)
             cpu.pop("evals", None)
 
+    # the same steps with the leaf Gram on the tensor cores (exact BF16 slices)
+    gram_tc = None
+    if name == "grid" and args.precision == "mixed":
+        cfg = {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent") if k in tune}
+        g.set_launch(**cfg, gram_tensor_cores=True)
+        ms_t, _, prof_t, ll_t = measure_precision(g, torch, args.precision, args, thetas, stream, flush, local)
+        g.set_launch(**cfg, gram_tensor_cores=False)
+        gram_tc = {"ms_per_step": sum(ms_t) / args.steps, "value": whole_job_rate(n, per_call, args.steps,
+                                                                                 sum(ms_t) / 1e3, 1),
+                   "leafgram_ms_per_step": prof_t.get("leafgram", (0, 0.0))[1] / args.steps,
+                   "accuracy_abs_dl_per_n": float(np.max(np.abs(ll_t - ref)) / n),
+                   "note": "the same timed steps with mra_tune_t.gram_tensor_cores = 1 (tcgen05 BF16 MMAs of exact "
+                           "fixed-grid slices; column exponents by k_gram_colexp); accuracy against the FP64 CPU oracle"}
     pred = prediction_line(g, d, args.precision) if name == "grid" else None
     clus = None
     if name == "grid" and args.precision == "mixed" and not args.no_clustered:
@@ -489,7 +502,8 @@ def run_ours(args):
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "flops_per_eval": st["flops_per_theta"],
         "launch_config": {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent",
-                                                "pinned") if k in tune},
+                                                "gram_tensor_cores", "pinned") if k in tune},
+        "gram_tensor_cores": gram_tc,
         "predict": pred,
         "clustered": clus,
     }

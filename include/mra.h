@@ -154,14 +154,18 @@ typedef struct {
     double ms_default;    /* mean pass time with the configuration before the call */
     double ms_best;       /* mean pass time with the chosen configuration */
     int tried;            /* candidates timed */
+    int gram_tensor_cores; /* mixed modes: 0 (default) the leaf Gram on the CUDA cores (FP32 products, float-pair
+                              sums of 32-row chunks); 1 on the tensor cores (tcgen05 BF16 MMAs of exact
+                              fixed-grid slices, exact sums, rounded once per 320 rows).  The two differ in the
+                              last bits, so the autotuner does not switch it: it reports the setting in force. */
 } mra_tune_t;
 
 mra_status mra_autotune(mra_ctx *ctx, const double *theta, int reps, mra_tune_t *out);
 
 /* Set the launch configuration directly (the four configuration fields of
- * cfg; the times are ignored).  leafbasis_rows 0 and leafbasis_stages 0 select
- * the defaults; EINVAL for a value outside the candidates or one whose shared
- * memory does not fit. */
+ * cfg and gram_tensor_cores; the times are ignored).  leafbasis_rows 0 and
+ * leafbasis_stages 0 select the defaults; EINVAL for a value outside the
+ * candidates or one whose shared memory does not fit. */
 mra_status mra_set_launch(mra_ctx *ctx, const mra_tune_t *cfg);
 
 /* Select MRA_FP64, MRA_MIXED or MRA_MIXED_FAST for later calls. */

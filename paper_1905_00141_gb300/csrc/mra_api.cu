@@ -273,6 +273,7 @@ struct mra_ctx {
     // (0: 32/48/64, 1: 32/64), side streams for the leaf posterior
     int lb_rows = 0, lb_stages = 0, bucket_set = 0;
     bool concurrent = true;
+    bool gram_tc = false; // mixed modes: leaf Gram on the tensor cores (exact slices)
     BigLeaf *d_big = nullptr;
     int nbig = 0;
     // work items of the tiled large-leaf kernels: [0, n_assemble) assembly
@@ -373,7 +374,7 @@ mra_status dev_upload(mra_ctx *c, T **dst, const T *src, size_t count)
 struct Plan {
     size_t prior = 0, prior_lvl[MRA_MAXM + 1] = {0};
     size_t U = 0, leafw = 0, leafdu = 0, V = 0;
-    size_t Ain = 0, Ainw = 0, Aindu = 0;
+    size_t Ain = 0, Ainw = 0, Aindu = 0, Gexp = 0;
     size_t Atil[MRA_MAXM + 1] = {0}, Atilw[MRA_MAXM + 1] = {0}, Atildu[MRA_MAXM + 1] = {0};
     size_t t_elems = 0, d_elems = 0; // totals
 };
@@ -400,6 +401,7 @@ Plan make_plan(const mra_ctx *c)
         p.Ain = nP * (size_t)(M - 1) * M / 2 * B2;
         p.Ainw = nP * (size_t)(M - 1) * RP;
         p.Aindu = 2 * nP;
+        p.Gexp = nP * (size_t)(M - 1) * RP;
         for (int m = 2; m <= M - 1; m++) {
             const size_t nr = (size_t)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]);
             p.Atil[m] = nr * (size_t)(m - 1) * m / 2 * B2;
@@ -454,6 +456,11 @@ Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
     w.Ainw_stride = p.Ainw;
     w.Ain_du = takeD(p.Aindu);
     w.Aindu_stride = p.Aindu;
+    {
+        w.gexp = (int8_t *)(base + off);
+        off = align256(off + p.Gexp * (size_t)B);
+        w.gexp_stride = p.Gexp;
+    }
     for (int m = 2; m <= c->P.M - 1; m++) {
         w.Atil[m] = takeT8(p.Atil[m]);
         w.Atil_stride[m] = p.Atil[m];
@@ -483,6 +490,7 @@ size_t scratch_bytes_for(const Plan &p, const mra_ctx *c, int B)
     addT(p.Ain);
     addD(p.Ainw);
     addD(p.Aindu);
+    s = align256(s + p.Gexp * (size_t)B);
     for (int m = 2; m <= c->P.M - 1; m++) {
         addT(p.Atil[m]);
         addD(p.Atilw[m]);
@@ -631,7 +639,10 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
         const int chunk = c->ain_chunk > 0 ? c->ain_chunk : nP;
         for (int p0 = 0; p0 < nP; p0 += chunk) {
             const int cnt = std::min(chunk, nP - p0);
-            if ((e = timed_launch(c, K_LEAFGRAM, s, [&] { return launch_leafgram<T, RP>(t, w, p0, cnt, B, s); })))
+            const bool tc = sizeof(T) == 4 && c->gram_tc;
+            if (tc && (e = timed_launch(c, K_LEAFGRAM, s, [&] { return launch_gram_colexp<T, RP>(t, w, p0, cnt, B, s); })))
+                return e;
+            if ((e = timed_launch(c, K_LEAFGRAM, s, [&] { return launch_leafgram<T, RP>(t, w, p0, cnt, B, tc, s); })))
                 return e;
             if ((e = timed_launch(c, K_UP, s, [&] { return launch_up<T, RP>(t, w, M - 1, p0, cnt, B, s); })))
                 return e;
@@ -1479,6 +1490,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         out->leafbasis_stages = stages;
         out->bucket_set = bestc.set;
         out->concurrent = bestc.conc ? 1 : 0;
+        out->gram_tensor_cores = c->gram_tc ? 1 : 0;
         out->ms_default = first;
         out->ms_best = best;
         out->tried = (int)cand.size();
@@ -1512,6 +1524,7 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
     c->lb_stages = stages;
     c->bucket_set = g->bucket_set;
     c->concurrent = g->concurrent != 0;
+    c->gram_tc = g->gram_tensor_cores != 0;
     drop_graphs(c);
     return MRA_OK;
 }

@@ -1,5 +1,6 @@
 // mra_gram_tc.cuh -- the leaf Gram blocks of the mixed mode on the tensor
-// cores (tcgen05, kind::tf32, accumulation in tensor memory).
+// cores (tcgen05, kind::f16 with BF16 operands, accumulation in tensor
+// memory), with sums that are exact in the tensor cores.
 //
 // For a region P of level M-1 the upward pass starts from
 //     A = sum over the leaves c of P of Y_c' Y_c = Y_P' Y_P,
@@ -7,55 +8,115 @@
 // UC = (M-1) RP columns); the packed upper blocks (k <= l) of this UC x UC
 // matrix are the ATilde blocks the leaves pass to their parent (App. B).
 //
-// Tensor-core form: D = T T' with T = Y_P' (UC rows, the region's observations
-// along K).  A CTA of 128 threads computes a 128 x N tile of D: rows
-// [xa0, xa0 + 128) and columns [xb0, xb0 + N), N <= 256, for one region
-// (grid.x), one tile (grid.y) and one theta (grid.z).  Row chunk c of the
-// output owns rows [128 c, 128 c + 128) (the MMA rows start at
-// min(128 c, UC - 128) so that every MMA has M = 128); its columns run from
-// 128 c to UC (the upper triangle), in pieces of at most 256.
+// Exact slices.  The tensor cores accumulate in FP32 and drop the bits below
+// the running sum's last place (toward zero, about once per MMA), which biases
+// a plain FP32 or 3xTF32 Gram: parity of the likelihood drifted to ~6e-6 per
+// observation.  Here every value v of column x of a group of rows is split on
+// a grid fixed per column, 2^e >= max |v| over the group:
+//     v = 2^e (q0 + q1 + q2 + r),  q0 = i0 2^-7, q1 = i1 2^-15, q2 = i2 2^-23,
+// integers |i_k| <= 128 (exact BF16 values) and |r| <= 2^-24, and the
+// products are summed by slice order:
+//     D0 = sum q0 q0,  D1 = sum (q0 q1 + q1 q0),  D2 = sum (q0 q2 + q1 q1 + q2 q0)
+// (all in absolute units; the order-3 and -4 terms and the residual r are
+// dropped: below 2^-23 of 2^(e_a + e_b) per product).  Within one order every
+// product is an integer multiple of one grid step, at most 2^14 steps, so a
+// group of up to 320 rows keeps every partial sum below 2^24 steps and the
+// tensor cores add them exactly, whatever they do with lower bits.  D0 + D1 +
+// D2 is then formed in float pairs and rounded to FP32 once per group; a
+// region of more than 320 rows adds its groups' values in FP32 (one rounding per
+// 320 rows, where the CUDA-core Gram rounds once per 32).
 //
-// Precision: each FP32 value v is split into TF32 parts hi = tf32(v) and
-// lo = tf32(v - hi) (22 significant bits together), and D accumulates
-// hi hi' + hi lo' + lo hi' (the 3xTF32 product: every product exact in the
-// tensor cores, the dropped lo lo' term below 2^-21 of |v1 v2|) in FP32 in
-// tensor memory.
+// Tiles.  A CTA of 128 threads computes a 128 x N tile of A, N <= 64: rows
+// [xa0, xa0 + 128) and columns [xb0, xb0 + N), for one region (grid.x), one tile
+// (grid.y) and one theta (grid.z).  Row chunk c of the output owns rows
+// [128 c, 128 c + 128) (the MMA rows start at min(128 c, UC - 128) so every MMA
+// has M = 128); its columns run from 128 c to UC (the upper triangle) in tiles
+// of 64.  D0, D1, D2 sit at TMEM columns 0, 64, 128.
 //
-// Pipeline per CTA: the region's rows in groups of KC (32, 16 or 8) rows;
-// all 128 threads load a group (plain coalesced loads), split it and store
-// both parts into one of two shared-memory stages in the no-swizzle K-major
-// core-matrix layout (tc_sm100.cuh), then thread 0 issues the MMAs of the
-// group and commits them to the stage's mbarrier, which the threads wait on
-// (bounded) before they refill that stage two groups later.  After the last
-// group the four warps read their 32 TMEM lanes (tile rows) back, 32 columns
-// at a time, and write whole rows of the packed 32 x 32 (or 16 x 16) blocks.
+// Pipeline.  k_gram_colexp first finds each region's column exponents (one
+// pass over Y).  Then per group of rows, in chunks of KC rows: all threads load
+// (eight steps of loads in flight per thread), slice and store the three
+// slices into one of two shared-memory stages in the no-swizzle K-major
+// core-matrix layout (tc_sm100.cuh), thread 0 issues the six MMAs per K = 16
+// step and commits them to the stage's mbarrier, which the threads wait on
+// (bounded) before they refill the stage.  After a group the four warps read
+// their 32 TMEM lanes (tile rows) and add the rounded D0 + D1 + D2 to FP32
+// registers; at the end they write whole rows of the packed blocks.
 #pragma once
 #include "tc_sm100.cuh"
 
 namespace mra {
 
 constexpr int kGramTcThreads = 128;
-constexpr uint32_t kGramTcCols = 256; // TMEM columns per CTA (N <= 256)
-constexpr uint32_t kGramTcPolls = 1u << 24; // mbarrier polls before a wait gives up (~seconds)
+constexpr int kGramTcN = 64;                 // columns per tile
+constexpr uint32_t kGramTcCols = 256;        // TMEM columns per CTA: D0, D1, D2 at 0, 64, 128
+constexpr uint32_t kGramTcPolls = 1u << 24;  // mbarrier polls before a wait gives up (~seconds)
+constexpr int kGramTcGroup = 320;            // rows per exact group
+constexpr int kGramTcMaxTiles = 48;
 enum { ST_ETIMEDOUT = 5 };
 
 // One output tile of the Gram (host-built list, the same for every region).
 struct GramTile {
     int16_t xa0, xb0;  // first row (MMA rows: 128 of them) and first column
-    int16_t n;         // columns (a multiple of 16, <= 256)
+    int16_t n;         // columns (a multiple of 16, <= 64)
     int16_t rowlo;     // rows below this one are owned by an earlier chunk
-    int16_t u0, w;     // staged columns of T: [u0, u0 + w)
-    int16_t kc, pad;   // rows per staged group
+    int16_t u0, w;     // staged columns of Y: [u0, u0 + w), w a multiple of 8
+    int16_t kc, pad;   // rows per staged chunk (a multiple of 16)
 };
-
-constexpr int kGramTcMaxTiles = 12;
 struct GramTiles {
     int n;
     GramTile t[kGramTcMaxTiles];
 };
 
-__host__ __device__ constexpr size_t gram_tc_stage_bytes(int w, int kc) { return (size_t)w * kc * 4; }
-__host__ __device__ constexpr size_t smem_gram_tc_bytes(int w, int kc) { return 4 * gram_tc_stage_bytes(w, kc) + 1024; }
+// one stage: three slices of w x kc BF16 values
+__host__ __device__ constexpr size_t gram_tc_slice_bytes(int w, int kc) { return (size_t)w * kc * 2; }
+__host__ __device__ constexpr size_t smem_gram_tc_bytes(int w, int kc)
+{
+    return 2 * 3 * gram_tc_slice_bytes(w, kc) + (size_t)w * 4 + 1024 + 256;
+}
+
+// 2^-e as a float for the column exponent e (2^e >= max |v|)
+__device__ __forceinline__ float gram_scale(int e) { return __int_as_float((127 - e) << 23); }
+
+// The three slices of v on the grid of exponent e, as BF16 bit patterns (the
+// slice values have at most 8 significant bits, so truncating the FP32 bits
+// is exact).
+__device__ __forceinline__ void gram_slices(float v, int e, uint32_t (&q)[3])
+{
+    const float y = __fmul_rn(v, gram_scale(e)); // |y| <= 1, exact
+    const float q0 = __fmul_rn(rintf(__fmul_rn(y, 128.f)), 0.0078125f);
+    const float r1 = __fsub_rn(y, q0);
+    const float q1 = __fmul_rn(rintf(__fmul_rn(r1, 32768.f)), 3.0517578125e-05f);
+    const float r2 = __fsub_rn(r1, q1);
+    const float q2 = __fmul_rn(rintf(__fmul_rn(r2, 8388608.f)), 1.1920928955078125e-07f);
+    const float up = __int_as_float((127 + e) << 23); // back to absolute units (exact)
+    q[0] = __float_as_uint(__fmul_rn(q0, up)) >> 16;
+    q[1] = __float_as_uint(__fmul_rn(q1, up)) >> 16;
+    q[2] = __float_as_uint(__fmul_rn(q2, up)) >> 16;
+}
+
+// Column exponents of Y below each level-(M-1) region, 2^e > max |Y| over the
+// region's rows (e = 0 for an all-zero column): one CTA per region, threads
+// along the columns (coalesced rows), eight rows in flight per thread.  A grid
+// from the region-wide maximum keeps every group of the Gram exact (the slices
+// stay within +-128 steps).
+template <int RP>
+__global__ void __launch_bounds__(256) k_gram_colexp(DevTree t, Work<float> w, int reg0)
+{
+    const int P = reg0 + blockIdx.x, Pl = blockIdx.x, b = blockIdx.y;
+    const double *th = w.theta + 3 * b;
+    if (!theta_ok(th)) return;
+    const int M = t.M, J = t.J, UC = (M - 1) * RP;
+    const int64_t r0 = t.leaf_off[(int64_t)P * J], r1 = t.leaf_off[(int64_t)P * J + J];
+    const float *Yb = w.U + (size_t)b * w.U_stride;
+    int8_t *ge = w.gexp + (size_t)b * w.gexp_stride + (size_t)Pl * UC;
+    for (int x = threadIdx.x; x < UC; x += blockDim.x) {
+        float m = 0.f;
+#pragma unroll 8
+        for (int64_t r = r0; r < r1; r++) m = fmaxf(m, fabsf(Yb[(size_t)r * UC + x]));
+        ge[x] = (int8_t)(m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xff) - 126 : 0);
+    }
+}
 
 template <int RP>
 __global__ void __launch_bounds__(kGramTcThreads) k_leafgram_tc(DevTree t, Work<float> w, int reg0, GramTiles tiles)
@@ -66,18 +127,17 @@ __global__ void __launch_bounds__(kGramTcThreads) k_leafgram_tc(DevTree t, Work<
     if (!theta_ok(th)) return;
     const GramTile tl = tiles.t[blockIdx.y];
     const int M = t.M, J = t.J, UC = (M - 1) * RP, np = npairs(M - 1);
-    const int KC = tl.kc, W = tl.w, u0 = tl.u0;
-    const uint32_t SBO = (uint32_t)(KC / 4) * 128u, LBO = 128u;
+    const int KC = tl.kc, W = tl.w, u0 = tl.u0, N = tl.n;
+    const uint32_t SBO = (uint32_t)(KC / 8) * 128u, LBO = 128u;
     const int64_t r0 = t.leaf_off[(int64_t)P * J], r1 = t.leaf_off[(int64_t)P * J + J];
     const float *Yb = w.U + (size_t)b * w.U_stride;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // stage s: hi part at 2 s, lo part at 2 s + 1
     unsigned char *stg = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const size_t SB = gram_tc_stage_bytes(W, KC);
+    const size_t SL = gram_tc_slice_bytes(W, KC); // one slice; a stage is 3 SL
+    int *cexp = reinterpret_cast<int *>(stg + 6 * SL); // [W] column exponents
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_bad;
-    // (written only after the last pipeline barrier; read after the next one)
 
     if (warp == 0) {
         tc::tmem_alloc(&s_tmem, kGramTcCols);
@@ -93,58 +153,120 @@ __global__ void __launch_bounds__(kGramTcThreads) k_leafgram_tc(DevTree t, Work<
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    const uint32_t idesc = tc::idesc_tf32(128, tl.n);
-    const int ngroups = (int)((r1 - r0 + KC - 1) / KC);
-    // every exit from the pipeline is uniform: a thread whose bounded wait
-    // gave up says so at the next barrier (__syncthreads_or), and all stop
+    const uint32_t idesc = tc::idesc_bf16(128, N);
+    // sums of this thread's tile row (x = xa0 + tid) over the groups
+    float acc[kGramTcN];
+#pragma unroll
+    for (int q = 0; q < kGramTcN; q++) acc[q] = 0.f;
+
+    // the column exponents of the staged columns (k_gram_colexp, region-wide)
+    {
+        const int8_t *ge = w.gexp + (size_t)b * w.gexp_stride + (size_t)Pl * UC;
+        for (int xx = tid; xx < W; xx += kGramTcThreads) cexp[xx] = (u0 + xx < UC) ? (int)ge[u0 + xx] : 0;
+    }
+    __syncthreads();
     bool bad = false;
-    int last = -1; // the last group whose MMAs were committed
-    for (int g = 0; g < ngroups; g++) {
-        const int s = g & 1;
-        if (g >= 2 && !tc::mbar_wait(&mbar[s], (uint32_t)((g - 2) >> 1) & 1u, kGramTcPolls)) bad = true;
-        unsigned char *hi = stg + (size_t)(2 * s) * SB, *lo = hi + SB;
-        const int64_t rb = r0 + (int64_t)g * KC;
-        // lane (x % 8, r % 4): a warp fills one 128-byte core matrix per step
-        const int ncm = (W / 8) * (KC / 4);
-        if (!bad)
-            for (int cm = warp; cm < ncm; cm += kGramTcThreads / 32) {
-                const int xg = cm / (KC / 4), rg = cm % (KC / 4);
-                const int xx = xg * 8 + (lane >> 2), rr = rg * 4 + (lane & 3);
-                const int x = u0 + xx;
-                const int64_t r = rb + rr;
-                const float v = (r < r1 && x < UC) ? Yb[(size_t)r * UC + x] : 0.f;
-                const float h = tc::to_tf32(v);
-                const float l = tc::to_tf32(__fsub_rn(v, h));
-                const size_t off =
-                    (size_t)xg * SBO + (size_t)rg * LBO + (size_t)(lane >> 2) * 16 + (size_t)(lane & 3) * 4;
-                *reinterpret_cast<float *>(hi + off) = h;
-                *reinterpret_cast<float *>(lo + off) = l;
+    int gc = 0;     // chunks committed so far (all groups)
+    int last = -1;  // index of the last committed chunk
+    for (int64_t g0 = r0; g0 < r1 && !bad; g0 += kGramTcGroup) {
+        const int64_t g1 = min(r1, g0 + (int64_t)kGramTcGroup);
+        // the group's chunks
+        const int nch = (int)((g1 - g0 + KC - 1) / KC);
+        for (int c = 0; c < nch; c++, gc++) {
+            const int s = gc & 1;
+            if (gc >= 2 && !tc::mbar_wait(&mbar[s], (uint32_t)((gc - 2) >> 1) & 1u, kGramTcPolls)) bad = true;
+            unsigned char *st = stg + (size_t)s * 3 * SL;
+            const int64_t rb = g0 + (int64_t)c * KC;
+            // lane (x % 8, pair of rows): a warp fills one 128-byte core matrix of each
+            // slice per step; the loads of CB steps are issued before any is used
+            const int ncm = (W / 8) * (KC / 8);
+            constexpr int CB = 8;
+            if (!bad)
+                for (int cm0 = warp; cm0 < ncm; cm0 += 4 * CB) {
+                    float v0[CB], v1[CB];
+#pragma unroll
+                    for (int k = 0; k < CB; k++) {
+                        const int cm = cm0 + 4 * k;
+                        const int xg = cm / (KC / 8), rg = cm % (KC / 8);
+                        const int x = u0 + xg * 8 + (lane >> 2);
+                        const int64_t r = rb + rg * 8 + (lane & 3) * 2;
+                        const bool ok = cm < ncm && x < UC;
+                        v0[k] = (ok && r < g1) ? Yb[(size_t)r * UC + x] : 0.f;
+                        v1[k] = (ok && r + 1 < g1) ? Yb[(size_t)(r + 1) * UC + x] : 0.f;
+                    }
+#pragma unroll
+                    for (int k = 0; k < CB; k++) {
+                        const int cm = cm0 + 4 * k;
+                        if (cm >= ncm) continue;
+                        const int xg = cm / (KC / 8), rg = cm % (KC / 8);
+                        const int e = cexp[xg * 8 + (lane >> 2)];
+                        uint32_t a[3], bq[3];
+                        gram_slices(v0[k], e, a);
+                        gram_slices(v1[k], e, bq);
+                        const size_t off =
+                            (size_t)xg * SBO + (size_t)rg * LBO + (size_t)(lane >> 2) * 16 + (size_t)(lane & 3) * 4;
+#pragma unroll
+                        for (int q = 0; q < 3; q++)
+                            *reinterpret_cast<uint32_t *>(st + q * SL + off) = a[q] | (bq[q] << 16);
+                    }
+                }
+            tc::fence_proxy_async();
+            if (__syncthreads_or(bad)) {
+                bad = true;
+                break;
             }
-        tc::fence_proxy_async();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                uint32_t as[3], bs[3];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    as[k] = tc::smem_addr(st + k * SL) + (uint32_t)((tl.xa0 - u0) / 8) * SBO;
+                    bs[k] = tc::smem_addr(st + k * SL) + (uint32_t)((tl.xb0 - u0) / 8) * SBO;
+                }
+                for (int ks = 0; ks < KC / 16; ks++) {
+                    const uint32_t ko = (uint32_t)ks * 2u * LBO; // two core matrices along K per step
+                    const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u; // a new group overwrites D
+                    auto mma = [&](int dk, int sa, int sb, uint32_t accum) {
+                        tc::mma_bf16(tmem + 64u * dk, tc::smem_desc(as[sa] + ko, LBO, SBO),
+                                     tc::smem_desc(bs[sb] + ko, LBO, SBO), idesc, accum);
+                    };
+                    mma(0, 0, 0, first);
+                    mma(1, 0, 1, first);
+                    mma(1, 1, 0, 1u);
+                    mma(2, 0, 2, first);
+                    mma(2, 1, 1, 1u);
+                    mma(2, 2, 0, 1u);
+                }
+                tc::mma_commit(&mbar[s]);
+            }
+            last = gc;
+        }
+        if (bad) break;
+        // the group's sums: wait for its last commit, then D0 + D1 + D2 (exact
+        // FP32 values) in float pairs, rounded once, into the running sums
+        bad = !tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, kGramTcPolls);
+        tc::fence_after_sync();
         if (__syncthreads_or(bad)) {
             bad = true;
             break;
         }
-        if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t ah = tc::smem_addr(hi) + (uint32_t)((tl.xa0 - u0) / 8) * SBO;
-            const uint32_t al = tc::smem_addr(lo) + (uint32_t)((tl.xa0 - u0) / 8) * SBO;
-            const uint32_t bh = tc::smem_addr(hi) + (uint32_t)((tl.xb0 - u0) / 8) * SBO;
-            const uint32_t bl = tc::smem_addr(lo) + (uint32_t)((tl.xb0 - u0) / 8) * SBO;
-            for (int ks = 0; ks < KC / 8; ks++) {
-                const uint32_t ko = (uint32_t)ks * 2u * LBO; // two core matrices along K per step
-                tc::mma_tf32(tmem, tc::smem_desc(ah + ko, LBO, SBO), tc::smem_desc(bh + ko, LBO, SBO), idesc,
-                             (g > 0 || ks > 0) ? 1u : 0u);
-                tc::mma_tf32(tmem, tc::smem_desc(ah + ko, LBO, SBO), tc::smem_desc(bl + ko, LBO, SBO), idesc, 1u);
-                tc::mma_tf32(tmem, tc::smem_desc(al + ko, LBO, SBO), tc::smem_desc(bh + ko, LBO, SBO), idesc, 1u);
+#pragma unroll
+        for (int cc = 0; cc < kGramTcN; cc += 16) {
+            float d0[16], d1[16], d2[16];
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cc;
+            tc::tmem_ld16(ta, d0);
+            tc::tmem_ld16(ta + 64u, d1);
+            tc::tmem_ld16(ta + 128u, d2);
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                const ff s = ff_add_f(two_sum(d0[q], d1[q]), d2[q]);
+                acc[cc + q] = __fadd_rn(acc[cc + q], __fadd_rn(s.hi, s.lo));
             }
-            tc::mma_commit(&mbar[s]);
         }
-        last = g;
+        // the next group's first MMAs overwrite D only after every warp has read it
+        tc::fence_before_sync();
+        __syncthreads();
     }
-    // the last commit completes after every MMA of the CTA
-    if (!bad && last >= 0) bad = !tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, kGramTcPolls);
-    tc::fence_after_sync();
     if (__syncthreads_or(bad)) s_bad = 1;
     __syncthreads();
     if (s_bad) {
@@ -155,29 +277,21 @@ __global__ void __launch_bounds__(kGramTcThreads) k_leafgram_tc(DevTree t, Work<
             if (last >= 0) (void)tc::mbar_wait(&mbar[last & 1], (uint32_t)(last >> 1) & 1u, kGramTcPolls);
         }
     } else {
-        // tile row i = 32 warp + lane, output row x = xa0 + i
+        // tile row i = tid, output row x = xa0 + i: whole rows of the packed blocks
         float *out = w.Ain + (size_t)b * w.Ain_stride + (size_t)Pl * np * RP * RP;
-        const int i = 32 * warp + lane, x = tl.xa0 + i;
-        const bool mine = x >= tl.rowlo && x < UC;
-        const int k = x / RP, ii = x % RP;
-        for (int cc = 0; cc < tl.n; cc += 32) {
-            float v[32];
-            if (ngroups > 0) {
-                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cc, v);
-            } else {
+        const int x = tl.xa0 + tid;
+        if (x >= tl.rowlo && x < UC) {
+            const int k = x / RP, ii = x % RP;
 #pragma unroll
-                for (int q = 0; q < 32; q++) v[q] = 0.f;
-            }
-            if (!mine) continue;
-#pragma unroll
-            for (int part = 0; part < 32 / RP; part++) {
-                const int xb = tl.xb0 + cc + part * RP, l = xb / RP;
-                if (xb >= UC || k > l) continue;
+            for (int part = 0; part < kGramTcN / RP; part++) {
+                const int xb = tl.xb0 + part * RP, l = xb / RP;
+                if (part * RP >= N || xb >= UC || k > l) continue;
                 float4 *dst = reinterpret_cast<float4 *>(out + (size_t)pidx(k + 1, l + 1) * RP * RP + (size_t)ii * RP);
 #pragma unroll
-                for (int q = 0; q < RP / 4; q++)
-                    dst[q] = make_float4(v[part * RP + 4 * q], v[part * RP + 4 * q + 1], v[part * RP + 4 * q + 2],
-                                         v[part * RP + 4 * q + 3]);
+                for (int q = 0; q < RP / 4; q++) {
+                    const int c = part * RP + 4 * q;
+                    dst[q] = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+                }
             }
         }
     }
@@ -214,26 +328,26 @@ __global__ void __launch_bounds__(kGramTcThreads) k_leafgram_tc(DevTree t, Work<
 }
 
 // The tile list of a Gram of UC columns (host side): row chunks of 128, each
-// with its columns [128 c, UC) in pieces of at most 256; the staged range and
-// the rows per group chosen so that two stages of both parts fit twice per SM.
+// with its columns [128 c, UC) in tiles of 64; the staged range and the rows
+// per chunk chosen so that the two stages stay under ~100 KB (two CTAs per SM).
 __host__ inline int gram_tc_tiles(int UC, GramTile *out, int cap)
 {
     int n = 0;
     for (int c = 0; 128 * c < UC; c++) {
         const int rowlo = 128 * c;
         const int xa0 = UC >= 128 ? (rowlo < UC - 128 ? rowlo : UC - 128) : 0;
-        for (int xb0 = rowlo; xb0 < UC; xb0 += 256) {
+        for (int xb0 = rowlo; xb0 < UC; xb0 += kGramTcN) {
             GramTile g;
             g.xa0 = (int16_t)xa0;
             g.xb0 = (int16_t)xb0;
-            g.n = (int16_t)(UC - xb0 < 256 ? UC - xb0 : 256);
+            g.n = (int16_t)(UC - xb0 < kGramTcN ? UC - xb0 : kGramTcN);
             g.rowlo = (int16_t)rowlo;
             const int lo = xa0 < xb0 ? xa0 : xb0;
             const int hi = (xa0 + 128 > xb0 + g.n) ? xa0 + 128 : xb0 + g.n;
             g.u0 = (int16_t)lo;
             g.w = (int16_t)(hi - lo);
             int kc = 32;
-            while (kc > 8 && smem_gram_tc_bytes(g.w, kc) > (size_t)112 * 1024) kc /= 2;
+            while (kc > 16 && smem_gram_tc_bytes(g.w, kc) > (size_t)100 * 1024) kc /= 2;
             g.kc = (int16_t)kc;
             g.pad = 0;
             if (n < cap) out[n] = g;

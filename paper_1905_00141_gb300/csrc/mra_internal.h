@@ -20,6 +20,8 @@
 //              Holds one chunk of consecutive regions when the whole level
 //              does not fit (the leaf Gram and the level M-1 upward step then
 //              run chunk by chunk).
+//   gexp       level M-1 regions (same chunking as Ain): int8 column exponents of
+//              Y for the exact tensor-core Gram (mixed mode).
 //   Atil[m]    level m regions (2 <= m <= M-1): ATilde after the region's
 //              step, blocks (k <= l <= m-1), same packing, plus w (FP64) and (d, u).
 #pragma once
@@ -66,6 +68,8 @@ struct Work {
     double *Ain_w;  // [nP][(M-1) RP]
     double *Ain_du; // [nP][2]
     size_t Ain_stride, Ainw_stride, Aindu_stride;
+    int8_t *gexp;   // [nP][(M-1) RP]: per column of Y below each region, e with 2^e > max |Y| (mixed mode)
+    size_t gexp_stride;
     T *Atil[MRA_MAXM + 1];
     double *Atil_w[MRA_MAXM + 1];
     double *Atil_du[MRA_MAXM + 1];
@@ -172,7 +176,9 @@ template <typename T, int RP>
 int launch_big(const DevTree &t, const Work<T> &w, int phase, const BigLeaf *leaves, const BigTile *items,
                int nitems, int k, int B, void *stream);
 template <typename T, int RP>
-int launch_leafgram(const DevTree &t, const Work<T> &w, int reg0, int nP, int B, void *stream);
+int launch_leafgram(const DevTree &t, const Work<T> &w, int reg0, int nP, int B, bool tensor_cores, void *stream);
+template <typename T, int RP>
+int launch_gram_colexp(const DevTree &t, const Work<T> &w, int reg0, int nP, int B, void *stream);
 template <typename T, int RP>
 int launch_up(const DevTree &t, const Work<T> &w, int m, int reg0, int nreg, int B, void *stream);
 template <typename T, int RP>

@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "mra_kernels.cuh"
+#include "mra_gram_tc.cuh"
 
 namespace mra {
 
@@ -133,16 +134,48 @@ int launch_big(const DevTree &t, const Work<T> &w, int phase, const BigLeaf *lea
     return (int)cudaGetLastError();
 }
 
+// tensor_cores (mixed modes): the exact tensor-core Gram (after launch_gram_colexp)
 template <typename T, int RP>
-int launch_leafgram(const DevTree &t, const Work<T> &w, int reg0, int nP, int B, void *stream)
+int launch_leafgram(const DevTree &t, const Work<T> &w, int reg0, int nP, int B, bool tensor_cores, void *stream)
 {
-    static size_t done = 0;
-    const size_t sm = smem_leafgram_bytes<T, RP>(t.M);
-    if (int e = set_smem(k_leafgram<T, RP>, sm, &done)) return e;
-    const int nt = ((t.M - 1) * RP + kGramTile - 1) / kGramTile;
-    dim3 grid((unsigned)nP, (unsigned)(nt * (nt + 1) / 2), (unsigned)B);
-    k_leafgram<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, reg0);
-    return (int)cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {
+      if (tensor_cores) {
+        // mixed mode: tensor cores, exact BF16-slice sums (mra_gram_tc.cuh)
+        static size_t done_tc = 0;
+        GramTiles tl;
+        memset(&tl, 0, sizeof(tl));
+        tl.n = gram_tc_tiles((t.M - 1) * RP, tl.t, kGramTcMaxTiles);
+        if (tl.n > kGramTcMaxTiles) return (int)cudaErrorInvalidConfiguration;
+        size_t sm = (size_t)80 * 1024; // at most two CTAs per SM: their TMEM (2 x 256 columns) always fits
+        for (int k = 0; k < tl.n; k++) sm = std::max(sm, smem_gram_tc_bytes(tl.t[k].w, tl.t[k].kc));
+        if (int e = set_smem(k_leafgram_tc<RP>, sm, &done_tc)) return e;
+        dim3 grid((unsigned)nP, (unsigned)tl.n, (unsigned)B);
+        k_leafgram_tc<RP><<<grid, kGramTcThreads, sm, (cudaStream_t)stream>>>(t, w, reg0, tl);
+        return (int)cudaGetLastError();
+      }
+    }
+    {
+        static size_t done = 0;
+        const size_t sm = smem_leafgram_bytes<T, RP>(t.M);
+        if (int e = set_smem(k_leafgram<T, RP>, sm, &done)) return e;
+        const int nt = ((t.M - 1) * RP + kGramTile - 1) / kGramTile;
+        dim3 grid((unsigned)nP, (unsigned)(nt * (nt + 1) / 2), (unsigned)B);
+        k_leafgram<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, reg0);
+        return (int)cudaGetLastError();
+    }
+}
+
+// mixed mode: column exponents of Y per level-(M-1) region for the exact Gram
+template <typename T, int RP>
+int launch_gram_colexp(const DevTree &t, const Work<T> &w, int reg0, int nP, int B, void *stream)
+{
+    if constexpr (sizeof(T) == 4) {
+        dim3 grid((unsigned)nP, (unsigned)B);
+        k_gram_colexp<RP><<<grid, 256, 0, (cudaStream_t)stream>>>(t, w, reg0);
+        return (int)cudaGetLastError();
+    } else {
+        return 0;
+    }
 }
 
 // regions reg0 .. reg0 + nreg - 1 of level m (nreg < 0: the whole level)
@@ -204,7 +237,8 @@ int launch_predict(const DevTree &t, const Work<T> &w, const PredArgs &q, void *
     template size_t smem_big<T, RP>(int);                                                                   \
     template int launch_big<T, RP>(const DevTree &, const Work<T> &, int, const BigLeaf *, const BigTile *, \
                                    int, int, int, void *);                                                  \
-    template int launch_leafgram<T, RP>(const DevTree &, const Work<T> &, int, int, int, void *);           \
+    template int launch_leafgram<T, RP>(const DevTree &, const Work<T> &, int, int, int, bool, void *);     \
+    template int launch_gram_colexp<T, RP>(const DevTree &, const Work<T> &, int, int, int, void *);        \
     template int launch_up<T, RP>(const DevTree &, const Work<T> &, int, int, int, int, void *);            \
     template int launch_root_single<T, RP>(const DevTree &, const Work<T> &, int, void *);                   \
     template int launch_predict<T, RP>(const DevTree &, const Work<T> &, const PredArgs &, void *);

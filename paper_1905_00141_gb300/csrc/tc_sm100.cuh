@@ -6,11 +6,11 @@
 // commit to an mbarrier, bounded mbarrier waits and 32-lane TMEM loads.
 //
 // Shared-memory operand layout (no swizzle, K-major): the operand is split
-// into "core matrices" of 8 rows (M or N) x 16 bytes (4 FP32/TF32 values along
-// K), each stored as 128 contiguous bytes (row-major inside).  Core matrices
-// adjacent along K are `lbo` bytes apart, 8-row groups adjacent along M/N are
-// `sbo` bytes apart.  One MMA with K = 8 (TF32) reads two core matrices along
-// K per 8-row group.
+// into "core matrices" of 8 rows (M or N) x 16 bytes (4 TF32 or 8 BF16 values
+// along K), each stored as 128 contiguous bytes (row-major inside).  Core
+// matrices adjacent along K are `lbo` bytes apart, 8-row groups adjacent along
+// M/N are `sbo` bytes apart.  One MMA step (K = 8 for TF32, K = 16 for BF16:
+// 32 bytes) reads two core matrices along K per 8-row group.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,6 +40,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
 {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of kind::f16 with BF16 operands and FP32
+// accumulation, both K-major: D format F32 (bits 4-5 = 1), A and B format BF16
+// (bits 7-9 and 10-12 = 1), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // TMEM allocation by one whole warp: ncols (a power of two >= 32) columns of
@@ -73,6 +81,19 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
                  ".reg .pred p;\n"
                  "setp.ne.b32 p, %4, 0;\n"
                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+                 "}\n" ::"r"(dtmem),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+
+// D[tmem] (+)= A * B' for one K = 16 step of BF16 operands.
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile("{\n"
+                 ".reg .pred p;\n"
+                 "setp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
                  "}\n" ::"r"(dtmem),
                  "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
                  : "memory");
@@ -131,6 +152,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane, then the wait.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
 // FP32 -> TF32 rounded to nearest (ties away), kept in a 32-bit container.

@@ -291,3 +291,58 @@ def test_parity_deep_binary_trees(n, M, r, seed):
 def test_fast_mixed_mode_on_small_trees():
     x, y, z = synth.uniform(3000, 25)
     _parity(x, y, z, 5, 4, 32, precisions=("mixed_fast",))
+
+
+# The leaf Gram on the tensor cores (tcgen05 BF16 MMAs of exact fixed-grid slices;
+# mra_tune_t.gram_tensor_cores = 1): the same likelihood as the CUDA-core Gram up to
+# its last bits, held to the mixed tolerance against the oracle.  The trees cover
+# Gram widths from 16 to 272 columns (one to three row chunks of the tile list,
+# pieces narrower than the 64-column tile), empty subtrees, and a region of more
+# than 320 observations (several exact groups added in FP32).
+@pytest.mark.parametrize("n,M,J,r,seed", [
+    (600, 2, 4, 16, 2),
+    (3000, 4, 2, 30, 4),
+    (3000, 5, 4, 32, 5),
+    (4000, 6, 2, 16, 6),
+    (20000, 14, 2, 16, 41),
+    (30000, 18, 2, 9, 42),
+])
+def test_tensor_core_gram_parity(n, M, J, r, seed):
+    x, y, z = synth.uniform(n, seed, exact=n <= 6000)
+    th = THETAS[:2]
+    ref, st = oracle.loglik(x, y, z, M, J, r, th)
+    assert st == 0
+    with mra.MRA(x, y, z, M, J, r, precision="mixed") as g:
+        nu = g.stats()["n_used"]
+        cuda_core = g.loglik(th)
+        g.set_launch(gram_tensor_cores=True)
+        assert g.autotune(th[0], reps=1)["gram_tensor_cores"] == 1
+        tensor = g.loglik(th)
+        again = g.loglik(th)
+    assert np.array_equal(tensor, again)
+    assert not np.array_equal(tensor, cuda_core)
+    err = np.abs(tensor - ref) / nu
+    print("tensor-core Gram M=%d |dl|/n:" % M, err, "CUDA-core:", np.abs(cuda_core - ref) / nu)
+    assert np.all(err <= TOLMIX), err
+
+
+def test_tensor_core_gram_ragged_and_grid_workload():
+    # a 400-point cluster: a level-(M-1) region of more than 320 rows (several groups)
+    x, y, z = synth.uniform(3000, 11)
+    rng = np.random.default_rng(5)
+    x = np.concatenate([x, 0.8 + 0.01 * rng.standard_normal(400)])
+    y = np.concatenate([y, 0.8 + 0.01 * rng.standard_normal(400)])
+    z = np.concatenate([z, rng.standard_normal(400)])
+    d = synth.grid()
+    for (xx, yy, zz, M, J, r, th) in [(x, y, z, 4, 4, 16, THETAS),
+                                      (d["x"], d["y"], d["z"], d["M"], d["J"], d["r"],
+                                       np.array([[1.0, 0.05, 0.01], [1.3, 0.08, 0.02]]))]:
+        ref, st = oracle.loglik(xx, yy, zz, M, J, r, th)
+        assert st == 0
+        with mra.MRA(xx, yy, zz, M, J, r, precision="mixed") as g:
+            nu = g.stats()["n_used"]
+            g.set_launch(gram_tensor_cores=True)
+            got = g.loglik(th)
+        err = np.abs(got - ref) / nu
+        print("tensor-core Gram n=%d |dl|/n:" % nu, err)
+        assert np.all(err <= TOLMIX), err
