@@ -73,9 +73,9 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-clustered", action="store_true",
                    help="skip the clustered 64-theta object of the default grid line")
-    p.add_argument("--launch", default=None, metavar="ROWS,STAGES,BUCKETS,CONCURRENT",
+    p.add_argument("--launch", default=None, metavar="ROWS,STAGES,BUCKETS,CONCURRENT[,QUEUE]",
                    help="pin the launch configuration (mra_set_launch) instead of running the autotuner, "
-                        "e.g. 64,1,0,1")
+                        "e.g. 64,1,0,1 (QUEUE 1: leaf buckets as persistent work queues)")
     p.add_argument("--workload", default="grid", choices=["grid", "clustered", "massive"],
                    help="grid: n=131,072, 1 theta per call (default); clustered: n=2,097,152 with 64 theta per "
                         "call; massive: n=47,185,920, 1 theta per call")
@@ -356,7 +356,7 @@ def run_ours(args):
     # launch configuration chosen by the library's autotuner (outside the timed region), or pinned
     def choose_launch():
         if args.launch:
-            keys = ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent")
+            keys = ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent", "leaf_queue")
             cfg = dict(zip(keys, (int(v) for v in args.launch.split(","))))
             g.set_launch(**cfg)
             return dict(cfg, pinned=True)
@@ -467,7 +467,8 @@ def run_ours(args):
     # the same steps with the leaf Gram on the tensor cores (exact BF16 slices)
     gram_tc = None
     if name == "grid" and args.precision == "mixed":
-        cfg = {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent") if k in tune}
+        cfg = {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent", "leaf_queue")
+               if k in tune}
         g.set_launch(**cfg, gram_tensor_cores=True)
         ms_t, _, prof_t, ll_t = measure_precision(g, torch, args.precision, args, thetas, stream, flush, local)
         g.set_launch(**cfg, gram_tensor_cores=False)
@@ -502,7 +503,7 @@ def run_ours(args):
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "flops_per_eval": st["flops_per_theta"],
         "launch_config": {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent",
-                                                "gram_tensor_cores", "pinned") if k in tune},
+                                                "gram_tensor_cores", "leaf_queue", "pinned") if k in tune},
         "gram_tensor_cores": gram_tc,
         "predict": pred,
         "clustered": clus,
@@ -567,6 +568,12 @@ def clustered_line(torch, stream, flush, local, precision="mixed", calls=2, warm
             timed_steps(g, torch, th_dev, out_dev, flush, stream, 1)
         ms = timed_steps(g, torch, th_dev, out_dev, flush, stream, calls)
         ll = out_dev.cpu().numpy()[0]
+        # the leaf buckets as persistent work queues (largest leaf first), same calls
+        g.set_launch(64, 1, 0, True, leaf_queue=True)
+        timed_steps(g, torch, th_dev, out_dev, flush, stream, 1)
+        ms_q = timed_steps(g, torch, th_dev, out_dev, flush, stream, calls)
+        same_q = bool(np.array_equal(out_dev.cpu().numpy()[0], ll))
+        g.set_launch(64, 1, 0, True)
         g.profile(True)
         g.profile_read()
         timed_steps(g, torch, th_dev, out_dev, flush, stream, 1)
@@ -601,6 +608,8 @@ def clustered_line(torch, stream, flush, local, precision="mixed", calls=2, warm
                 "launch_config": {"leafbasis_rows": 64, "leafbasis_stages": 1, "bucket_set": 0, "concurrent": 1,
                                   "pinned": True},
                 "fp64_ms_per_theta": fp64_per_theta_ms, "mixed_vs_fp64": fp64_per_theta_ms / per_theta_ms,
+                "leaf_queue": {"ms_per_theta": sum(ms_q) / (calls * 64), "same_loglik_bits": same_q,
+                               "note": "the same calls with each leaf bucket as a persistent work-queue kernel"},
                 "accuracy_abs_dl_per_n": acc,
                 "kernels_ms_per_step": {k: v[1] for k, v in prof.items()},
                 "l2": "flushed between calls (256 MB write, outside the timed events)"}

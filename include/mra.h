@@ -139,8 +139,9 @@ mra_status mra_loglik_device(mra_ctx *ctx, const double *theta_dev, int batch, d
  * precision by timing it on this tree.  Candidates: observation rows per
  * leaf-basis CTA (32 or, in the mixed mode, 64), one or two shared-memory
  * stages of ancestor blocks, the leaf-size buckets of the leaf posterior
- * ({<=32, <=48, <=64} or {<=32, <=64}), and running those buckets on side
- * streams or one after another.  Every candidate computes the same loglik,
+ * ({<=32, <=48, <=64} or {<=32, <=64}), running those buckets on side
+ * streams or one after another, and each bucket as one CTA per leaf or as a
+ * persistent work queue.  Every candidate computes the same loglik,
  * bit for bit; only the time differs.  Each candidate runs 2 untimed and
  * `reps` timed passes of one theta (theta: host, 3 doubles) on a stream of
  * the library; the fastest is kept for later calls (mra_set_precision resets
@@ -158,12 +159,15 @@ typedef struct {
                               sums of 32-row chunks); 1 on the tensor cores (tcgen05 BF16 MMAs of exact
                               fixed-grid slices, exact sums, rounded once per 320 rows).  The two differ in the
                               last bits, so the autotuner does not switch it: it reports the setting in force. */
+    int leaf_queue;       /* 1: each leaf-size bucket runs as a persistent work-queue kernel (CTAs resident at
+                             once take the leaves, largest first, through an atomic counter) instead of one CTA
+                             per leaf; the same results bit for bit, so the autotuner tries both */
 } mra_tune_t;
 
 mra_status mra_autotune(mra_ctx *ctx, const double *theta, int reps, mra_tune_t *out);
 
 /* Set the launch configuration directly (the four configuration fields of
- * cfg and gram_tensor_cores; the times are ignored).  leafbasis_rows 0 and
+ * cfg, gram_tensor_cores and leaf_queue; the times are ignored).  leafbasis_rows 0 and
  * leafbasis_stages 0 select the defaults; EINVAL for a value outside the
  * candidates or one whose shared memory does not fit. */
 mra_status mra_set_launch(mra_ctx *ctx, const mra_tune_t *cfg);

@@ -274,6 +274,8 @@ struct mra_ctx {
     int lb_rows = 0, lb_stages = 0, bucket_set = 0;
     bool concurrent = true;
     bool gram_tc = false; // mixed modes: leaf Gram on the tensor cores (exact slices)
+    bool leaf_queue = false; // shared-memory leaf buckets as persistent work-queue kernels
+    unsigned *d_qcnt = nullptr; // their counters: kLeafBuckets x status_cap
     BigLeaf *d_big = nullptr;
     int nbig = 0;
     // work items of the tiled large-leaf kernels: [0, n_assemble) assembly
@@ -605,8 +607,9 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
                 cudaStreamWaitEvent(q, c->fork_ev, 0);
             }
             s_taken = true;
+            unsigned *qc = c->leaf_queue ? c->d_qcnt + (size_t)k * c->status_cap : nullptr;
             if ((e = timed_launch(c, K_LEAFPOST, q, [&] {
-                     return launch_leafpost_small<T, RP>(t, w, lists[k], counts[k], caps[k], B, q);
+                     return launch_leafpost_small<T, RP>(t, w, lists[k], counts[k], caps[k], B, qc, q);
                  })))
                 return e;
         }
@@ -766,6 +769,11 @@ mra_status ensure_capacity(mra_ctx *c, int B)
         return MRA_ENOMEM;
     }
     e = cudaMalloc((void **)&c->d_status, sizeof(int) * (size_t)B);
+    if (e == cudaSuccess) {
+        if (c->d_qcnt) cudaFree(c->d_qcnt);
+        c->d_qcnt = nullptr;
+        e = cudaMalloc((void **)&c->d_qcnt, sizeof(unsigned) * (size_t)kLeafBuckets * (size_t)B);
+    }
     if (e != cudaSuccess) {
         cudaFree(c->d_scratch);
         c->d_scratch = nullptr;
@@ -1410,7 +1418,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy theta");
     struct Cfg {
         int rows, stages, set;
-        bool conc;
+        bool conc, queue;
     };
     const bool mixed = c->precision != MRA_FP64;
     const int RP = c->RP, M = c->P.M;
@@ -1423,7 +1431,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         return b <= 227 * 1024;
     };
     std::vector<Cfg> cand;
-    const Cfg start{c->lb_rows, c->lb_stages, c->bucket_set, c->concurrent};
+    const Cfg start{c->lb_rows, c->lb_stages, c->bucket_set, c->concurrent, c->leaf_queue};
     cand.push_back(start);
     for (int rows : {64, 32}) {
         if (rows == 64 && !mixed) continue;
@@ -1431,7 +1439,8 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
             if (!smem_ok(rows, stages)) continue;
             for (int set : {0, 1}) {
                 if (set == 1 && c->nmax_small < 64) continue;
-                for (bool conc : {true, false}) cand.push_back(Cfg{rows, stages, set, conc});
+                for (bool conc : {true, false})
+                    for (bool queue : {false, true}) cand.push_back(Cfg{rows, stages, set, conc, queue});
             }
         }
     }
@@ -1448,6 +1457,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         c->lb_stages = g.stages;
         c->bucket_set = g.set;
         c->concurrent = g.conc;
+        c->leaf_queue = g.queue;
         drop_graphs(c); // the pass changes
     };
     double best = 1e300, first = 0.0;
@@ -1491,6 +1501,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         out->bucket_set = bestc.set;
         out->concurrent = bestc.conc ? 1 : 0;
         out->gram_tensor_cores = c->gram_tc ? 1 : 0;
+        out->leaf_queue = bestc.queue ? 1 : 0;
         out->ms_default = first;
         out->ms_best = best;
         out->tried = (int)cand.size();
@@ -1525,6 +1536,7 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
     c->bucket_set = g->bucket_set;
     c->concurrent = g->concurrent != 0;
     c->gram_tc = g->gram_tensor_cores != 0;
+    c->leaf_queue = g->leaf_queue != 0;
     drop_graphs(c);
     return MRA_OK;
 }
@@ -1540,6 +1552,7 @@ mra_status mra_set_precision(mra_ctx *c, int precision)
     c->precision = precision;
     c->lb_rows = c->lb_stages = c->bucket_set = 0; // tuned for the other precision
     c->concurrent = true;
+    c->leaf_queue = false;
     if (c->d_sx) {
         // the scratch layout and the theta per pass depend on the storage type
         const int mb = max_batch_for(c, c->hbm_budget);
@@ -1804,7 +1817,7 @@ void mra_free(mra_ctx *c)
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
                     c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_leaves_m, c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
-                    c->d_reg_du, c->d_reg_lw, c->pred.pt, c->pred.tree};
+                    c->d_reg_du, c->d_reg_lw, c->pred.pt, c->pred.tree, c->d_qcnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);

@@ -169,7 +169,7 @@ int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, in
                      int B, void *stream);
 template <typename T, int RP>
 int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves,
-                          int nmax, int B, void *stream);
+                          int nmax, int B, unsigned *queue, void *stream);
 // Tiled large-leaf posterior: one launch per phase; items of that phase.
 enum BigPhase { BIG_ASSEMBLE = 0, BIG_POTRF = 1, BIG_TRSM = 2, BIG_UPDATE = 3, BIG_FINISH = 4 };
 template <typename T, int RP>

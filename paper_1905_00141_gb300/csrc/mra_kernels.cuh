@@ -1287,15 +1287,16 @@ __device__ void gram_vec(const T *Y, int ldy, int UC, const F *y, int n, double 
     }
 }
 
+// The posterior terms of leaf c at theta b by the whole CTA (the body of the
+// shared-memory leaf kernels below); theta b is valid.  Ends with every thread
+// past its last shared-memory access of the leaf.
 template <typename T, int RP, int NMAX>
-__global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, const int64_t *leaves)
+__device__ __forceinline__ void leafpost_small_leaf(const DevTree &t, const Work<T> &w, int64_t c, int b)
 {
     constexpr int nmax = NMAX;
     using F = typename FacT<T>::type;
-    const int64_t c = leaves[blockIdx.x];
-    const int b = blockIdx.y, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
-    if (!theta_ok(th)) return;
     const double tau2 = th[2];
     __shared__ double s_ib; // 1/beta, one FP64 division per CTA
     const int M = t.M;
@@ -1444,6 +1445,39 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
             r[1] = uv;
         }
         if (flag[0]) w.status[b] = ST_ENOTPD;
+    }
+}
+
+// One CTA per leaf of the list (grid.x), theta grid.y.
+template <typename T, int RP, int NMAX>
+__global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, const int64_t *leaves)
+{
+    const int b = blockIdx.y;
+    if (!theta_ok(w.theta + 3 * b)) return;
+    leafpost_small_leaf<T, RP, NMAX>(t, w, leaves[blockIdx.x], b);
+}
+
+// The same leaves as a work queue: a persistent grid (CTAs resident at once)
+// takes the leaves of the list in order through an atomic counter per theta
+// (counter[b], zero at launch), the list being ordered by decreasing size --
+// the paper's dynamic scheduling by the cost of a leaf (Sec. 4.1) as greedy
+// longest-first list scheduling on the GPU.  No CTA waits for another; each
+// leaf is computed by the same code as above, so the results are the same bit
+// for bit.
+template <typename T, int RP, int NMAX>
+__global__ void __launch_bounds__(NT) k_leafpost_queue(DevTree t, Work<T> w, const int64_t *leaves, int nleaves,
+                                                       unsigned *counter)
+{
+    const int b = blockIdx.y;
+    if (!theta_ok(w.theta + 3 * b)) return;
+    __shared__ int s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = (int)atomicAdd(&counter[b], 1u);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads(); // every thread has read s_idx (and left the last leaf's shared memory)
+        if (idx >= nleaves) break;
+        leafpost_small_leaf<T, RP, NMAX>(t, w, leaves[idx], b);
     }
 }
 

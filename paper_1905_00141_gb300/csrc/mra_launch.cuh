@@ -76,25 +76,48 @@ int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, in
 
 template <typename T, int RP, int NMAX>
 static int launch_leafpost_n(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves, int B,
-                             void *stream)
+                             unsigned *queue, void *stream)
 {
-    static size_t done = 0;
     const size_t sm = smem_leafpost_bytes<T, RP>(t.M, NMAX);
-    if (int e = set_smem(k_leafpost_small<T, RP, NMAX>, sm, &done)) return e;
-    dim3 grid((unsigned)nleaves, (unsigned)B);
-    k_leafpost_small<T, RP, NMAX><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, leaves);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!queue) {
+        static size_t done = 0;
+        if (int e = set_smem(k_leafpost_small<T, RP, NMAX>, sm, &done)) return e;
+        dim3 grid((unsigned)nleaves, (unsigned)B);
+        k_leafpost_small<T, RP, NMAX><<<grid, NT, sm, s>>>(t, w, leaves);
+        return (int)cudaGetLastError();
+    }
+    // persistent grid: the CTAs that fit on the GPU at once (per theta), at
+    // most one per leaf
+    static size_t done_q = 0;
+    static int per_sm = 0, sms = 0;
+    if (int e = set_smem(k_leafpost_queue<T, RP, NMAX>, sm, &done_q)) return e;
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leafpost_queue<T, RP, NMAX>, NT, sm);
+        if (per_sm < 1) per_sm = 1;
+    }
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned) * (size_t)B, s);
+    if (e != cudaSuccess) return (int)e;
+    const int per_theta = std::max(1, std::min(nleaves, sms * per_sm / std::max(B, 1)));
+    dim3 grid((unsigned)per_theta, (unsigned)B);
+    k_leafpost_queue<T, RP, NMAX><<<grid, NT, sm, s>>>(t, w, leaves, nleaves, queue);
     return (int)cudaGetLastError();
 }
 
-// nmax: a bucket cap (32, 48 or 64); the leaves of the list have at most nmax observations
+// nmax: a bucket cap (32, 48 or 64); the leaves of the list have at most nmax
+// observations.  queue: null for one CTA per leaf, else B zeroed counters for
+// the persistent work-queue kernel.
 template <typename T, int RP>
 int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves, int nmax,
-                          int B, void *stream)
+                          int B, unsigned *queue, void *stream)
 {
     if (nleaves == 0) return 0;
-    if (nmax <= 32) return launch_leafpost_n<T, RP, 32>(t, w, leaves, nleaves, B, stream);
-    if (nmax <= 48) return launch_leafpost_n<T, RP, 48>(t, w, leaves, nleaves, B, stream);
-    return launch_leafpost_n<T, RP, 64>(t, w, leaves, nleaves, B, stream);
+    if (nmax <= 32) return launch_leafpost_n<T, RP, 32>(t, w, leaves, nleaves, B, queue, stream);
+    if (nmax <= 48) return launch_leafpost_n<T, RP, 48>(t, w, leaves, nleaves, B, queue, stream);
+    return launch_leafpost_n<T, RP, 64>(t, w, leaves, nleaves, B, queue, stream);
 }
 
 template <typename T, int RP>
@@ -233,7 +256,7 @@ int launch_predict(const DevTree &t, const Work<T> &w, const PredArgs &q, void *
     template int launch_leafbasis<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, int, int, \
                                          void *);                                                           \
     template int launch_leafpost_small<T, RP>(const DevTree &, const Work<T> &, const int64_t *, int, int,   \
-                                              int, void *);                                                 \
+                                              int, unsigned *, void *);                                     \
     template size_t smem_big<T, RP>(int);                                                                   \
     template int launch_big<T, RP>(const DevTree &, const Work<T> &, int, const BigLeaf *, const BigTile *, \
                                    int, int, int, void *);                                                  \

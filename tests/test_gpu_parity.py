@@ -264,8 +264,9 @@ def test_launch_configurations_agree_bit_for_bit(precision):
             for stages in (1, 2):
                 for bset in (0, 1):
                     for conc in (True, False):
-                        g.set_launch(r, stages, bset, conc)
-                        assert np.array_equal(g.loglik(THETAS), ref), (r, stages, bset, conc)
+                        for queue in (False, True):
+                            g.set_launch(r, stages, bset, conc, leaf_queue=queue)
+                            assert np.array_equal(g.loglik(THETAS), ref), (r, stages, bset, conc, queue)
         rep = g.autotune(THETAS[0], reps=2)
         assert rep["tried"] >= 2 and rep["ms_best"] <= rep["ms_default"]
         assert np.array_equal(g.loglik(THETAS), ref)
