@@ -7,17 +7,14 @@ coordinates u = 2 (log theta - log lo) / (log hi - log lo) - 1 of a theta box:
 
 * :func:`nelder_mead` -- the plain simplex method (Nelder & Mead 1965, with
   the standard coefficients 1, 2, 1/2, 1/2), one exact evaluation at a time.
-* :func:`surrogate_search` -- the learned surrogate (``mlp.Surrogate``, the
-  3 -> 64 -> 64 -> 1 network trained by the library's own kernels) is fitted
-  to exact evaluations on a Sobol design, proposes where to look, and every
-  proposal is scored by the exact likelihood in batches of 64 theta (one
-  batched library call per round).  The exact values decide; the network
-  only chooses the next batch.  If a round brings no improvement the search
-  falls back to Nelder-Mead on the exact likelihood from the best point.
-
-With ``use_network=False`` the same batched trust-region loop runs without
-the network (each round is centred on the best exact point so far), which is
-the method without the learned part.
+* :func:`guided_search` -- a batched trust-region search guided by models of
+  the exact values seen so far: a weighted quadratic trend in u and the
+  learned surrogate (``mlp.Surrogate``, the 3 -> 64 -> 64 -> 1 network trained
+  by the library's own kernels) fitted to the trend's residuals.  Each round
+  scores a small batch of proposals in one batched library call; the exact
+  values decide, the models only choose the next batch, and the initial
+  design counts in the budget.  With ``use_network=False`` the same loop runs
+  on the trend alone (the method without the learned part).
 """
 from __future__ import annotations
 
@@ -136,154 +133,120 @@ def exact_nelder_mead(exact, u0, step=0.25, max_evals=400, xtol=1e-4, ftol=1e-3)
     return u, -fu, ne
 
 
-def _cloud(center, radius, n, seed):
-    """n Sobol points in the box |u - center| <= radius (sup norm), clipped to [-1, 1]^3."""
-    return np.clip(np.asarray(center, float) + float(radius) * sobol_unit(n, seed), -1.0, 1.0)
-
-
-def _top_distinct(u, v, k, min_dist):
+def _top_distinct(u, v, k, min_dist, taken=None):
     """Up to k points of u in decreasing order of v, each at least min_dist
-    (sup norm) from those already taken."""
+    (sup norm) from those already taken (and from the rows of `taken`)."""
     order = np.argsort(-v)
     take = []
+    prior = [] if taken is None else list(np.atleast_2d(taken))
     for i in order:
+        if len(take) == k:
+            break
         if not np.isfinite(v[i]):
             continue
-        if all(np.max(np.abs(u[i] - u[j])) >= min_dist for j in take):
+        if all(np.max(np.abs(u[i] - u[j])) >= min_dist for j in take) and \
+                all(np.max(np.abs(u[i] - p)) >= min_dist for p in prior):
             take.append(i)
-            if len(take) == k:
-                break
     return u[take]
 
 
-DEFAULT_SCHEDULE = ((2500, 3e-3), (2500, 1e-3), (2500, 3e-4), (2500, 1e-4))
+def _quad_features(u):
+    """1, u_i, u_i^2 and u_i u_j (i < j) of points u [k][3]: 10 columns."""
+    u = np.atleast_2d(u)
+    a, b, c = u[:, 0], u[:, 1], u[:, 2]
+    return np.stack([np.ones_like(a), a, b, c, a * a, b * b, c * c, a * b, a * c, b * c], axis=1)
 
 
-def _fit(sur, th, y, schedule):
-    sur.set_target_scaling(float(np.mean(y)), float(max(np.std(y), 1e-300)))
-    for steps, lr in schedule:
-        sur.train(th, y, steps, lr=lr)
+def _fit_trend(u, ll, center, radius):
+    """Weighted least-squares quadratic of loglik over scaled coordinates u
+    (centred on the incumbent and divided by the trust radius).  Points are
+    weighted by exp(-(l_best - l) / s), s the median gap of the points to the
+    best, so the fit follows the top of the surface; the weights never fall
+    below 1e-3."""
+    z = (np.asarray(u, float) - center) / radius
+    gap = np.max(ll) - ll
+    s = max(float(np.median(gap)), 1.0)
+    wt = np.maximum(np.exp(-gap / s), 1e-3)
+    X = _quad_features(z) * np.sqrt(wt)[:, None]
+    coef, *_ = np.linalg.lstsq(X, ll * np.sqrt(wt), rcond=None)
+    return lambda uu: _quad_features((np.asarray(uu, float) - center) / radius) @ coef
 
 
-class _Gap:
-    """Monotone transform of loglik the network is fitted to:
-    T(l) = -log(l_ref - l + c), c > 0 in nats.  It spreads the values near the
-    best point l_ref over a wide range of T, so the fit's relative precision
-    (bounded by the BF16 parameters) turns into a fine absolute precision of
-    loglik near the maximum, where it matters; the argmax is unchanged."""
+def guided_search(exact, new_surrogate=None, n0=16, batch=6, seed=1909, max_evals=160, radius0=1.0,
+                  shrink=0.5, min_local=24, cloud=8192, steps=(600, 600), rates=(3e-3, 5e-4), use_network=True,
+                  net_share=0.5, log=None):
+    """Batched model-based trust-region search for the maximiser of the exact
+    loglik, with the design counted in the budget.
 
-    def __init__(self, l_ref, c):
-        self.l_ref, self.c = float(l_ref), float(c)
-
-    def __call__(self, ll):
-        return -np.log(self.l_ref - np.asarray(ll, float) + self.c)
-
-    def inverse(self, t):
-        return self.l_ref + self.c - np.exp(-np.asarray(t, float))
-
-
-def surrogate_search(exact, new_surrogate=None, n_train=2048, batch=64, tol=0.5, seed=1909, max_rounds=10,
-                     top_fraction=0.25, schedule=DEFAULT_SCHEDULE, radius0=0.2, shrink=0.25, cloud=16384,
-                     gap_nats=0.0, use_network=True, nm_fallback_evals=200, log=None):
-    """Batched trust-region search for the maximiser of the exact loglik.
-
-    1. Exact loglik on n_train Sobol points of the box (batches of `batch`).
-    2. A network over the whole box is fitted on the best `top_fraction` of
-       them (full-batch Adam, `schedule` of (steps, rate)) to
-       -log(l_best - loglik + gap_nats), a monotone transform of loglik that
-       concentrates the fit's precision near the best value (gap_nats = 0:
-       loglik/n itself).
-    3. Each round proposes `batch` theta: the points of highest predicted
-       loglik in a Sobol cloud of the trust region (sup-norm radius r around
-       the incumbent, the best exact point), kept at least r/64 apart, and
-       scores them exactly in one batched call.  If the incumbent moved by
-       less than r/4 the region shrinks by `shrink` (otherwise it follows the
-       incumbent at the same size), and a fresh network is fitted to the exact
-       values inside the new region, with its inputs scaled to that region,
-       for the next round.
-    4. The loop ends when a round gains less than tol/4 without moving far
-       (or once r <= 0.02).  A round with no gain at all hands over to
-       Nelder-Mead on the exact loglik from the incumbent (the fallback).
-    Without the network (use_network=False) each round scores a Sobol set of
-    the trust region instead.  new_surrogate(box) -> ``mlp.Surrogate``.
-
-    Returns a dict with the best theta and loglik, the exact evaluations of the
-    design and of the search, and the rounds used."""
+    Round 0 scores n0 scrambled-Sobol theta of the box (one batched call).
+    Every round then:
+      1. takes the exact points near the incumbent (sup-norm distance <= 1.5 r
+         in scaled coordinates, at least the min_local nearest);
+      2. fits a quadratic trend of loglik to them (weighted least squares, the
+         weights favouring the top of the surface: the log-likelihood of a
+         smooth covariance model is close to quadratic in log theta near its
+         maximum) and, with use_network, the 3 -> 64 -> 64 -> 1 network to the
+         trend's residuals (input scaling: the trust region; a few hundred Adam
+         steps of the library's own kernels);
+      3. scores in one batched exact call `batch` points of a Sobol cloud of
+         the trust region (sup-norm radius r around the incumbent), at least
+         r/16 apart: a share net_share of them of highest trend + network
+         prediction, the rest of highest trend prediction (the network's
+         proposals are a hedge: fitted to a few dozen points it can place
+         spurious maxima, and the trend alone keeps the search moving);
+      4. recentres on the best exact point and halves r (shrink) when it moved
+         by less than r/4.
+    The exact values decide; the models only choose the next batch.  Stops
+    after max_evals exact evaluations or once r < 1e-3.  Returns the best theta
+    and loglik, the evaluations and the rounds."""
     if use_network and new_surrogate is None:
         from . import mlp
 
         def new_surrogate(b):
             return mlp.Surrogate(b, mlp.glorot_init(seed))
 
-    box, n = exact.box, exact.n
-    th_design = from_unit(sobol_unit(n_train, seed), box)
-    for i in range(0, n_train, batch):
-        exact(th_design[i:i + batch])
-    evals_design = exact.evals
-    radius = radius0
-    sur, sur_box = None, None
-    tf = None
-
-    def targets(ll):
-        return tf(ll) if tf is not None else np.asarray(ll, float) / n
-
-    def predicted_ll(th):
-        p = sur.predict(th)
-        return tf.inverse(p) if tf is not None else p * n
-
-    if use_network:
-        th_all = np.array(exact.thetas)
-        ll_all = np.array(exact.values)
-        good = np.isfinite(ll_all)
-        keep = good & (ll_all >= np.quantile(ll_all[good], 1.0 - top_fraction))
-        tf = _Gap(exact.best, gap_nats) if gap_nats > 0 else None
-        sur_box = box
-        sur = new_surrogate(box)
-        _fit(sur, th_all[keep], targets(ll_all[keep]), schedule)
+    box = exact.box
+    exact(from_unit(sobol_unit(n0, seed), box))
+    radius = float(radius0)
     rounds = 0
-    fell_back = False
-    while rounds < max_rounds:
+    while exact.evals + batch <= max_evals and radius >= 1e-3:
         rounds += 1
         center = to_unit(exact.best_theta, box)
-        pts = _cloud(center, radius, cloud, seed + 100 + rounds)
-        if use_network:
-            pred = predicted_ll(from_unit(pts, box))
-            cand = _top_distinct(pts, pred, batch, radius / 64.0)
-        else:
-            cand = np.vstack([center[None, :], pts[:batch - 1]])
+        u_all = to_unit(np.array(exact.thetas), box)
+        ll_all = np.array(exact.values)
+        ok = np.isfinite(ll_all)
+        dist = np.max(np.abs(u_all - center), axis=1)
+        near = ok & (dist <= 1.5 * radius)
+        if near.sum() < min_local:
+            order = np.argsort(np.where(ok, dist, np.inf))
+            near = np.zeros_like(ok)
+            near[order[:min(min_local, int(ok.sum()))]] = True
+        u_loc, ll_loc = u_all[near], ll_all[near]
+        trend = _fit_trend(u_loc, ll_loc, center, radius)
+        lo_u, hi_u = np.clip(center - radius, -1, 1), np.clip(center + radius, -1, 1)
+        pts = np.clip(center + radius * sobol_unit(cloud, seed + 100 + rounds), -1, 1)
+        pred_t = trend(pts)
+        k_net = int(round(net_share * batch)) if use_network else 0
+        cand = _top_distinct(pts, pred_t, batch - k_net, radius / 16.0)
+        if k_net > 0:
+            res = ll_loc - trend(u_loc)
+            scale = max(float(np.std(res)), 1e-3)
+            sur = new_surrogate((from_unit(lo_u, box), from_unit(hi_u, box)))
+            try:
+                sur.set_target_scaling(0.0, scale)
+                th_loc = from_unit(u_loc, box)
+                for st, lr in zip(steps, rates):
+                    sur.train(th_loc, res, st, lr=lr)
+                pred_n = pred_t + sur.predict(from_unit(pts, box))
+            finally:
+                sur.close()
+            cand = np.vstack([cand, _top_distinct(pts, pred_n, k_net, radius / 16.0, taken=cand)])
         before = exact.best
-        ll_c = exact(from_unit(cand, box))
-        gain = exact.best - before
+        exact(from_unit(cand, box))
         moved = float(np.max(np.abs(to_unit(exact.best_theta, box) - center)))
         if log is not None:
-            err = None
-            if use_network:
-                err = float(np.sqrt(np.mean((predicted_ll(from_unit(cand, box)) - ll_c) ** 2)))
-            log.append(dict(round=rounds, radius=radius, best=float(exact.best), gain=float(gain), moved=moved,
-                            pred_rmse_nats=err))
-        if gain < 0.25 * tol and (moved < 0.25 * radius or radius <= 0.02):
-            if gain <= 0.0 and radius > 0.01:
-                exact_nelder_mead(exact, to_unit(exact.best_theta, box), step=radius, max_evals=nm_fallback_evals,
-                                  ftol=0.1 * tol)
-                fell_back = True
-            break
+            log.append(dict(round=rounds, radius=radius, best=float(exact.best), gain=float(exact.best - before),
+                            moved=moved, local=int(near.sum())))
         if moved < 0.25 * radius:
-            radius = max(radius * shrink, 1e-3)  # the optimum is inside: zoom in
-        if use_network:
-            # fresh local network on the exact values inside the new region
-            c = to_unit(exact.best_theta, box)
-            lo_u, hi_u = np.clip(c - radius, -1, 1), np.clip(c + radius, -1, 1)
-            u_all = to_unit(np.array(exact.thetas), box)
-            ll_all = np.array(exact.values)
-            inside = np.all((u_all >= lo_u - 1e-12) & (u_all <= hi_u + 1e-12), axis=1) & np.isfinite(ll_all)
-            if inside.sum() >= 16:
-                sur.close()
-                sur_box = (from_unit(lo_u, box), from_unit(hi_u, box))
-                sur = new_surrogate(sur_box)
-                tf = _Gap(exact.best, gap_nats) if gap_nats > 0 else None
-                _fit(sur, np.array(exact.thetas)[inside], targets(ll_all[inside]), schedule)
-    if sur is not None:
-        sur.close()
-    return dict(theta=exact.best_theta, loglik=exact.best, evals_design=evals_design,
-                evals_search=exact.evals - evals_design, rounds=rounds, fell_back=fell_back,
-                calls=exact.calls)
+            radius *= shrink
+    return dict(theta=exact.best_theta, loglik=exact.best, evals=exact.evals, rounds=rounds)

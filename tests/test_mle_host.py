@@ -76,7 +76,20 @@ def test_trust_region_without_network_finds_maximum():
         ridge = (u[:, 0] - u[:, 1]) ** 2 * 400.0 + (u[:, 0] + u[:, 1]) ** 2 * 20.0 + u[:, 2] ** 2 * 200.0
         return -ridge
     ex = mle.Exact(fn, BOX, 1)
-    r = mle.surrogate_search(ex, None, n_train=256, use_network=False, tol=0.5)
-    assert r["evals_design"] == 256
-    assert ex.best > -0.5
-    assert r["evals_search"] == ex.evals - 256
+    log = []
+    r = mle.guided_search(ex, use_network=False, n0=16, batch=6, max_evals=160, log=log)
+    assert ex.best > -0.5 and r["evals"] == ex.evals <= 160
+    assert ex.evals_to_reach(-0.5) <= 100
+    # the design is one batched call, then every round one call of `batch` points
+    assert ex.calls == 1 + len(log) and ex.evals == 16 + 6 * len(log)
+
+
+def test_quadratic_trend_is_exact_on_a_quadratic():
+    rng = np.random.default_rng(4)
+    u = rng.uniform(-1, 1, (30, 3))
+    A = np.array([[-3.0, 0.5, 0.2], [0.5, -2.0, 0.1], [0.2, 0.1, -1.0]])
+    b = np.array([0.3, -0.2, 0.1])
+    f = np.einsum("ij,jk,ik->i", u, A, u) + u @ b + 7.0
+    trend = mle._fit_trend(u, f, np.array([0.1, 0.0, -0.1]), 0.5)
+    v = rng.uniform(-1, 1, (50, 3))
+    assert np.allclose(trend(v), np.einsum("ij,jk,ik->i", v, A, v) + v @ b + 7.0, atol=1e-9)

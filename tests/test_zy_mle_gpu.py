@@ -2,12 +2,14 @@
 M=7, J=4, r=32, mixed precision) against plain Nelder-Mead on the exact
 loglik, and against the same batched search without the network.
 
-The reference optimum l* is the best exact value any of the three searches
-found, polished by a tight Nelder-Mead.  Checked: the surrogate-guided search
-ends within 0.5 nats of l*, and its first batch of 64 network proposals
-gains more over the design's best point than a batch of 64 points of the same
-trust region chosen without the network.  The evaluation counts are printed
-(one line, prefixed MLE:)."""
+The reference optimum l* is the best exact value any search found, polished
+by a tight Nelder-Mead.  The measure is the number of exact evaluations (the
+initial design included) until the best value first comes within 0.5 nats of
+l*.  The guided search is deterministic (seeded Sobol points, deterministic
+training kernels), so three seeds give three fixed counts per method.
+Checked: with the network the search beats Nelder-Mead on every seed, and its
+mean count is below that of the same loop on the quadratic trend alone (what
+the trained network gains).  The counts are printed (one line, prefixed MLE:)."""
 import json
 import time
 
@@ -17,6 +19,8 @@ import pytest
 from paper_1905_00141_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+SEEDS = (1909, 1910, 1911)
 
 
 @pytest.fixture(scope="module")
@@ -41,35 +45,32 @@ def test_surrogate_guided_mle(problem):
         return g.loglik(th, check=False)
 
     out = {}
-    t0 = time.time()
     ex_nm = mle.Exact(fn, box, n)
     mle.exact_nelder_mead(ex_nm, np.zeros(3), step=0.25, max_evals=600, xtol=1e-5, ftol=1e-3)
-    out["nm"] = dict(evals=ex_nm.evals, best=ex_nm.best, sec=time.time() - t0)
     runs = {}
     for use in (True, False):
-        t0 = time.time()
-        ex = mle.Exact(fn, box, n)
-        log = []
-        r = mle.surrogate_search(ex, None, use_network=use, log=log)
-        runs[use] = (ex, r, log)
-        out["network" if use else "no_network"] = dict(evals_design=r["evals_design"],
-                                                       evals_search=r["evals_search"], rounds=r["rounds"],
-                                                       fell_back=r["fell_back"], best=r["loglik"],
-                                                       first_batch_gain=log[0]["gain"], sec=time.time() - t0)
-    best = max(ex_nm.best, runs[True][0].best, runs[False][0].best)
-    cands = [ex_nm, runs[True][0], runs[False][0]]
-    start = max(cands, key=lambda e: e.best).best_theta
+        for seed in SEEDS:
+            t0 = time.time()
+            ex = mle.Exact(fn, box, n)
+            r = mle.guided_search(ex, seed=seed, use_network=use)
+            runs[(use, seed)] = (ex, r, time.time() - t0)
+    allex = [ex_nm] + [v[0] for v in runs.values()]
+    start = max(allex, key=lambda e: e.best).best_theta
     ex_ref = mle.Exact(fn, box, n)
     mle.exact_nelder_mead(ex_ref, mle.to_unit(start, box), step=0.01, max_evals=300, xtol=1e-7, ftol=1e-4)
-    lstar = max(best, ex_ref.best)
+    lstar = max(max(e.best for e in allex), ex_ref.best)
+    nm = ex_nm.evals_to_reach(lstar - 0.5)
     out["l_star"] = lstar
-    out["nm"]["evals_to_0.5"] = ex_nm.evals_to_reach(lstar - 0.5)
+    out["nelder_mead"] = dict(evals_to_0_5=nm, evals=ex_nm.evals)
     for use in (True, False):
-        ex, r, _ = runs[use]
-        e = ex.evals_to_reach(lstar - 0.5)
-        k = "network" if use else "no_network"
-        out[k]["search_evals_to_0.5"] = None if e is None else e - r["evals_design"]
-        out[k]["gap"] = lstar - r["loglik"]
+        k = "network" if use else "trend_only"
+        cnt = [runs[(use, s)][0].evals_to_reach(lstar - 0.5) for s in SEEDS]
+        out[k] = dict(evals_to_0_5=cnt, gap=[lstar - runs[(use, s)][1]["loglik"] for s in SEEDS],
+                      sec=[round(runs[(use, s)][2], 2) for s in SEEDS])
     print("MLE:", json.dumps(out, default=float))
-    assert lstar - runs[True][1]["loglik"] <= 0.5
-    assert out["network"]["first_batch_gain"] > out["no_network"]["first_batch_gain"] + 5.0
+    net = out["network"]["evals_to_0_5"]
+    trend = out["trend_only"]["evals_to_0_5"]
+    assert nm is not None and all(c is not None for c in net + trend)
+    assert all(c < nm for c in net), (net, nm)
+    assert np.mean(net) < np.mean(trend), (net, trend)
+    assert all(lstar - runs[(True, s)][1]["loglik"] <= 0.5 for s in SEEDS)
