@@ -76,9 +76,10 @@ def parse():
     p.add_argument("--launch", default=None, metavar="ROWS,STAGES,BUCKETS,CONCURRENT[,QUEUE]",
                    help="pin the launch configuration (mra_set_launch) instead of running the autotuner, "
                         "e.g. 64,1,0,1 (QUEUE 1: leaf buckets as persistent work queues)")
-    p.add_argument("--workload", default="grid", choices=["grid", "clustered", "massive"],
+    p.add_argument("--workload", default="grid", choices=["grid", "clustered", "massive", "swaths"],
                    help="grid: n=131,072, 1 theta per call (default); clustered: n=2,097,152 with 64 theta per "
-                        "call; massive: n=47,185,920, 1 theta per call")
+                        "call; massive: n=47,185,920, 1 theta per call; swaths: n=2,439,827, J=2, M=14, "
+                        "r=49, 1 theta per call")
     return p.parse_args()
 
 
@@ -116,6 +117,10 @@ WORKLOAD_INFO = {
     "massive": dict(desc="massive n=47185920 M=12 J=4 r=16, 1 theta per call", per_call=1,
                     data="synthetic: n=47185920 uniform on [0,1]^2 minus 200 discs (5% of the area); z from an "
                          "exponential GP (sigma2=1, beta=0.02, tau2=0.01) by circulant embedding, seed 1911"),
+    "swaths": dict(desc="swaths n=2439827 M=14 J=2 r=49 (27 device levels), 1 theta per call", per_call=1,
+                   data="synthetic: n=2439827 uniform on [0,1]^2 in slanted bands (80% coverage, straight gaps); "
+                        "z from an exponential GP (sigma2=1, beta=0.05, tau2=0.01) by circulant embedding, "
+                        "seed 1912"),
 }
 
 
@@ -137,7 +142,8 @@ def step_thetas(name):
 def config(precision, name="grid", d=None):
     info = WORKLOAD_INFO[name]
     c = {"workload": info["desc"], "n": int(len(d["x"])) if d is not None else None,
-         "M": d["M"] if d is not None else None, "J": 4, "r": d["r"] if d is not None else None,
+         "M": d["M"] if d is not None else None, "J": d["J"] if d is not None else None,
+         "r": d["r"] if d is not None else None,
          "theta_per_call": info["per_call"], "precision": precision,
          "l2": "flushed between steps (256 MB write, outside the timed events)"}
     return c
@@ -254,6 +260,11 @@ def run_reference(args):
     if args.workload == "massive":
         print(json.dumps({"impl": "reference", "unavailable": "the FP64 CPU oracle is not run on the 47M-observation "
                           "tree (about 5 TFLOP and tens of GB of host memory per evaluation)"}), flush=True)
+        return 0
+    if args.workload == "swaths":
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 CPU oracle takes minutes per evaluation of "
+                          "the r=49 swaths tree; its stored values are checked in tests/test_zv_swaths_gpu.py"}),
+              flush=True)
         return 0
     d = workload(args.workload)
     thetas = step_thetas(args.workload).reshape(-1, 3)
@@ -377,7 +388,7 @@ def run_ours(args):
     # the other precision on the same theta, for the mixed-vs-FP64 comparison
     other = "fp64" if args.precision != "fp64" else "mixed"
     other_line, ll_o = None, None
-    if name != "massive":
+    if name not in ("massive", "swaths"):
         oargs = argparse.Namespace(**vars(args))
         if name != "grid":
             oargs.steps, oargs.warmup = min(args.steps, 2), 1
@@ -429,6 +440,9 @@ def run_ours(args):
             acc["mixed_fast"] = float(np.max(np.abs(ll_f - ref)) / n)
     elif ll_o is not None:
         acc = {"against": "FP64 GPU path", args.precision: float(np.max(np.abs(ll - ll_o)) / n)}
+    elif name == "swaths":
+        acc = {"against": None, "note": "the FP64 kernels do not fit this depth (27 device levels); the stored "
+                                        "oracle values are checked in tests/test_zv_swaths_gpu.py"}
     else:
         acc = {"against": None, "note": "FP64 does not fit one theta of this tree; sampled leaves against the "
                                         "oracle in tests/test_zx_massive_gpu.py"}

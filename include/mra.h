@@ -82,6 +82,8 @@ typedef struct {
     int launches_per_pass;      /* kernels launched by the last device pass (one batch chunk) */
     double flops_by_kernel[8];  /* flops_per_theta split by kernel family, in the order
                                    prior, leafbasis, leafpost, leafpost_big, leafgram, up, root */
+    int device_levels;          /* levels the kernels run: M, or 2 (M - 1) + 1 when r_hat > 32
+                                   (each non-leaf level enters its knots in two halves) */
 } mra_stats_t;
 
 typedef struct {
@@ -98,7 +100,12 @@ void mra_default_opts(mra_opts *opt);
  *   lon, lat, z : host arrays of n doubles (locations and values).  A NaN value
  *                 marks a prediction site and is dropped; non-finite locations
  *                 give MRA_EINVAL.
- *   M >= 1 levels, J in {2, 4}, r >= 1 knots requested (r_hat placed).
+ *   M >= 1 levels, J in {2, 4}, r >= 1 knots requested (r_hat placed,
+ *   r_hat <= 64).  With r_hat > 32 every non-leaf level is run as two device
+ *   levels of the same regions, the first ceil(r_hat/2) knots and then the
+ *   rest (Sec. 1.1: the remainder after projecting on the two halves in turn
+ *   is the remainder after projecting on all of them, so the likelihood is the
+ *   same); 2 (M - 1) + 1 device levels must not exceed 35.
  *   The domain is the bounding box with its top and right edges pushed out by
  *   1% of the extent; regions are half-open [x0,x1) x [y0,y1); J = 4 halves both
  *   sides, J = 2 halves the longer side (ties: x).  Observations that sit exactly
@@ -107,7 +114,8 @@ void mra_default_opts(mra_opts *opt);
  *   and of the used observations in leaf order; on failure *out is NULL and
  *   mra_last_error(NULL) gives the reason.
  *   Errors: MRA_EINVAL (sizes, J, r, M, offset outside [0, 0.5), degenerate
- *   domain), MRA_EEMPTY (nothing left), MRA_ENOMEM, MRA_ECUDA.
+ *   domain, r_hat > 64, a tree too deep for the shared-memory kernels in the
+ *   requested precision), MRA_EEMPTY (nothing left), MRA_ENOMEM, MRA_ECUDA.
  */
 mra_status mra_build(const double *lon, const double *lat, const double *z, int64_t n, int M,
                      int J, int r, const mra_opts *opt, mra_ctx **out);

@@ -247,11 +247,90 @@ mra_status build_partition(const double *x, const double *y, const double *z, in
     return MRA_OK;
 }
 
+// The levels the kernels run on (DevTree).  With r_hat <= 32 they are the
+// partition's levels.  With 32 < r_hat <= 64 every non-leaf level l enters its
+// knots in two device levels of the same regions: 2l - 1 holds the first
+// ceil(r_hat/2) knots and has one child (itself at 2l), 2l holds the rest and
+// has the J children of level l.  The remainder recursion of Sec. 1.1 after
+// projecting on Q1 and then on Q2 equals the one after projecting on
+// Q1 u Q2 (the Schur complement of the knot covariance), so Sigma_MRA, the
+// likelihood and the predictive distribution are unchanged, and every region
+// still fits one warp's lanes.
+struct Levels {
+    int M = 0, split = 1, RP = 0;
+    std::vector<int64_t> lvl_off; // [M+2]
+    std::vector<int> Rl, Jl;      // [M+1]: knots and children of a level-m region
+    std::vector<int> real;        // [M+1]: partition level of device level m
+    std::vector<double> kx, ky;   // [nnonleaf * RP], padded with zeros
+    std::vector<double> cx, cy;   // [nnonleaf] lower-left corner of the region
+    int64_t nreg() const { return lvl_off[(size_t)M + 1]; }
+    int64_t nnonleaf() const { return lvl_off[(size_t)M]; }
+    int64_t nleaf() const { return nreg() - nnonleaf(); }
+    int lgJ(int m) const { return Jl[(size_t)m] == 4 ? 2 : (Jl[(size_t)m] == 2 ? 1 : 0); }
+};
+
+// Largest r_hat the two-level split serves.
+constexpr int kMaxRhat = 64;
+
+mra_status make_levels(const Partition &P, Levels &G, std::string &err)
+{
+    if (P.R > kMaxRhat) {
+        err = "r_hat > 64 is not supported";
+        return MRA_EINVAL;
+    }
+    G.split = P.R > 32 ? 2 : 1;
+    const int Mr = P.M;
+    G.M = G.split == 1 ? Mr : 2 * (Mr - 1) + 1;
+    if (G.M > MRA_MAXM - 1) {
+        err = "M too large for r_hat > 32 (device levels 2 (M - 1) + 1 exceed the limit)";
+        return MRA_EINVAL;
+    }
+    const int R1 = G.split == 1 ? P.R : (P.R + 1) / 2;
+    G.lvl_off.assign((size_t)G.M + 2, 0);
+    G.Rl.assign((size_t)G.M + 1, 0);
+    G.Jl.assign((size_t)G.M + 1, 0);
+    G.real.assign((size_t)G.M + 1, 0);
+    for (int m = 1; m <= G.M; m++) {
+        const int l = G.split == 1 ? m : (m + 1) / 2; // partition level
+        const int h = G.split == 1 ? 0 : (m - 1) % 2; // which half of its knots
+        G.real[(size_t)m] = l;
+        const int64_t cnt = P.lvl_off[(size_t)l + 1] - P.lvl_off[(size_t)l];
+        G.lvl_off[(size_t)m + 1] = G.lvl_off[(size_t)m] + cnt;
+        if (m < G.M) {
+            G.Rl[(size_t)m] = h == 0 ? R1 : P.R - R1;
+            G.Jl[(size_t)m] = (G.split == 2 && h == 0) ? 1 : P.J;
+        }
+    }
+    int rmax = 0;
+    for (int m = 1; m < G.M; m++) rmax = std::max(rmax, G.Rl[(size_t)m]);
+    G.RP = rmax <= 16 ? 16 : 32;
+    const int64_t NK = G.nnonleaf();
+    G.kx.assign((size_t)(NK * G.RP), 0.0);
+    G.ky.assign((size_t)(NK * G.RP), 0.0);
+    G.cx.assign((size_t)std::max<int64_t>(NK, 1), 0.0);
+    G.cy.assign(G.cx.size(), 0.0);
+    for (int m = 1; m < G.M; m++) {
+        const int l = G.real[(size_t)m];
+        const int first = (G.split == 2 && (m - 1) % 2 == 1) ? R1 : 0;
+        for (int64_t i = 0; i < G.lvl_off[(size_t)m + 1] - G.lvl_off[(size_t)m]; i++) {
+            const int64_t g = G.lvl_off[(size_t)m] + i, pg = P.lvl_off[(size_t)l] + i;
+            for (int j = 0; j < G.Rl[(size_t)m]; j++) {
+                G.kx[(size_t)(g * G.RP + j)] = P.kx[(size_t)(pg * P.R + first + j)];
+                G.ky[(size_t)(g * G.RP + j)] = P.ky[(size_t)(pg * P.R + first + j)];
+            }
+            G.cx[(size_t)g] = P.bx0[(size_t)pg];
+            G.cy[(size_t)g] = P.by0[(size_t)pg];
+        }
+    }
+    return MRA_OK;
+}
+
 } // namespace
 
 // --------------------------------------------------------------- context --
 struct mra_ctx {
-    Partition P;
+    Partition P; // the partition of Sec. 1.2 (what the user sees)
+    Levels G;    // the levels the kernels run on
     int RP = 0, lgJ = 0, precision = MRA_FP64, device = 0;
     std::string err;
     // device tree
@@ -265,6 +344,8 @@ struct mra_ctx {
     int64_t *d_leaves[kLeafBuckets] = {nullptr, nullptr, nullptr};
     int nl[kLeafBuckets] = {0, 0, 0};
     int nmax_small = 64; // largest bucket cap whose shared memory fits
+    bool lb64_fits = true; // mixed modes: 64-row leaf-basis chunks fit in shared memory
+    bool fp64_fits = true; // the FP64 kernels fit in shared memory on this tree
     // the 48- and 64-observation buckets as one list (bucket set 1)
     int64_t *d_leaves_m = nullptr;
     int nl_m = 0;
@@ -383,8 +464,8 @@ struct Plan {
 
 Plan make_plan(const mra_ctx *c)
 {
-    const Partition &P = c->P;
-    const int M = P.M, J = P.J, RP = c->RP;
+    const Levels &P = c->G;
+    const int M = P.M, RP = c->RP;
     const size_t B2 = (size_t)RP * RP;
     Plan p;
     size_t acc = 0;
@@ -393,7 +474,7 @@ Plan make_plan(const mra_ctx *c)
         acc += (size_t)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]) * m * B2;
     }
     p.prior = acc;
-    p.U = (size_t)P.n_used * (size_t)(M - 1) * RP;
+    p.U = (size_t)c->P.n_used * (size_t)(M - 1) * RP;
     p.leafw = (size_t)P.nleaf() * (size_t)(M - 1) * RP;
     p.leafdu = 2 * (size_t)P.nleaf();
     p.V = (size_t)c->vbig_elems;
@@ -411,7 +492,6 @@ Plan make_plan(const mra_ctx *c)
             p.Atildu[m] = 2 * nr;
         }
     }
-    (void)J;
     p.t_elems = p.prior + p.U + p.leafw + p.Ain;
     for (int m = 2; m <= M - 1; m++) p.t_elems += p.Atil[m];
     p.d_elems = p.leafdu + p.V + p.Ainw + p.Aindu;
@@ -463,7 +543,7 @@ Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
         off = align256(off + p.Gexp * (size_t)B);
         w.gexp_stride = p.Gexp;
     }
-    for (int m = 2; m <= c->P.M - 1; m++) {
+    for (int m = 2; m <= c->G.M - 1; m++) {
         w.Atil[m] = takeT8(p.Atil[m]);
         w.Atil_stride[m] = p.Atil[m];
         w.Atil_w[m] = takeD(p.Atilw[m]);
@@ -493,7 +573,7 @@ size_t scratch_bytes_for(const Plan &p, const mra_ctx *c, int B)
     addD(p.Ainw);
     addD(p.Aindu);
     s = align256(s + p.Gexp * (size_t)B);
-    for (int m = 2; m <= c->P.M - 1; m++) {
+    for (int m = 2; m <= c->G.M - 1; m++) {
         addT(p.Atil[m]);
         addD(p.Atilw[m]);
         addD(p.Atildu[m]);
@@ -505,10 +585,8 @@ DevTree dev_tree(const mra_ctx *c)
 {
     DevTree t;
     memset(&t, 0, sizeof(t));
-    t.M = c->P.M;
-    t.J = c->P.J;
-    t.lgJ = c->lgJ;
-    t.R = c->P.R;
+    const Levels &G = c->G;
+    t.M = G.M;
     t.RP = c->RP;
     t.n_used = c->P.n_used;
     t.kx = c->d_kx;
@@ -519,7 +597,15 @@ DevTree dev_tree(const mra_ctx *c)
     t.sy = c->d_sy;
     t.sz = c->d_sz;
     t.leaf_off = c->d_leaf_off;
-    for (int m = 0; m <= c->P.M + 1; m++) t.lvl_off[m] = c->P.lvl_off[(size_t)m];
+    for (int m = 0; m <= G.M + 1; m++) t.lvl_off[m] = G.lvl_off[(size_t)m];
+    t.sh[1] = 0;
+    for (int m = 1; m <= G.M; m++) {
+        if (m < G.M) {
+            t.Rl[m] = G.Rl[(size_t)m];
+            t.Jl[m] = G.Jl[(size_t)m];
+        }
+        t.sh[m + 1] = t.sh[m] + (m < G.M ? G.lgJ(m) : 0);
+    }
     return t;
 }
 
@@ -555,12 +641,13 @@ template <typename T, int RP>
 int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
 {
     const DevTree t = dev_tree(c);
-    const int M = c->P.M;
+    const int M = c->G.M;
     int e;
     c->launches_last = 0;
     for (int m = 1; m < M; m++)
         if ((e = timed_launch(c, K_PRIOR, s, [&] { return launch_prior<T, RP>(t, w, m, B, s); }))) return e;
-    const int rows = (sizeof(T) == 4 && c->lb_rows == 32) ? 32 : chunk_rows<T>();
+    int rows = (sizeof(T) == 4 && c->lb_rows == 32) ? 32 : chunk_rows<T>();
+    if (rows == 64 && !c->lb64_fits) rows = 32; // deep trees: 64-row chunks exceed shared memory
     const Chunk *chunks = rows == 64 ? c->d_chunks64 : c->d_chunks32;
     const int nchunks = rows == 64 ? c->nchunks64 : c->nchunks32;
     if (M > 1 && nchunks > 0)
@@ -638,7 +725,7 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
         cudaStreamWaitEvent(s, c->join_ev[a], 0);
     }
     if (M > 1) {
-        const int nP = (int)(c->P.lvl_off[(size_t)M] - c->P.lvl_off[(size_t)M - 1]);
+        const int nP = (int)(c->G.lvl_off[(size_t)M] - c->G.lvl_off[(size_t)M - 1]);
         const int chunk = c->ain_chunk > 0 ? c->ain_chunk : nP;
         for (int p0 = 0; p0 < nP; p0 += chunk) {
             const int cnt = std::min(chunk, nP - p0);
@@ -666,34 +753,32 @@ int dispatch_rp(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     return run_pass<T, 32>(c, w, B, s);
 }
 
-size_t max_smem_needed(const mra_ctx *c, int nmax)
+// The largest dynamic shared memory one pass's kernels ask for with storage
+// type T: leaf-basis chunks of 32 rows in one stage (the smallest
+// configuration), the prior in two stages where they fit, leaf buckets up to
+// nmax observations.
+template <typename T, int RP>
+size_t smem_need(int M, int nmax)
 {
-    const int M = c->P.M;
     size_t mx = 0;
     auto upd = [&](size_t v) { mx = std::max(mx, v); };
     for (int m = 1; m < M; m++) {
-        if (c->RP == 16) {
-            upd(smem_prior<double, 16>(m));
-            upd(smem_up<double, 16>(m));
-        } else {
-            upd(smem_prior<double, 32>(m));
-            upd(smem_up<double, 32>(m));
-        }
+        upd(smem_prior<T, RP>(m));
+        upd(smem_up<T, RP>(m));
     }
-    if (c->RP == 16) {
-        upd(smem_big<double, 16>(M));
-        upd(smem_leafgram<double, 16>(M));
-        upd(smem_leafbasis<double, 16>(M));
-        upd(smem_leafpost_small<double, 16>(M, 32));
-        if (nmax > 0) upd(smem_leafpost_small<double, 16>(M, nmax));
-    } else {
-        upd(smem_big<double, 32>(M));
-        upd(smem_leafgram<double, 32>(M));
-        upd(smem_leafbasis<double, 32>(M));
-        upd(smem_leafpost_small<double, 32>(M, 32));
-        if (nmax > 0) upd(smem_leafpost_small<double, 32>(M, nmax));
-    }
+    upd(smem_big<T, RP>(M));
+    upd(smem_leafgram<T, RP>(M));
+    upd(smem_leafbasis_cfg<T, RP>(M, 32, 1));
+    upd(smem_leafpost_small<T, RP>(M, 32));
+    if (nmax > 0) upd(smem_leafpost_small<T, RP>(M, nmax));
     return mx;
+}
+
+size_t max_smem_needed(const mra_ctx *c, int nmax, bool fp64)
+{
+    const int M = c->G.M;
+    if (fp64) return c->RP == 16 ? smem_need<double, 16>(M, nmax) : smem_need<double, 32>(M, nmax);
+    return c->RP == 16 ? smem_need<float, 16>(M, nmax) : smem_need<float, 32>(M, nmax);
 }
 
 // Algorithmic FP operations of one evaluation per kernel family (r_hat, not
@@ -701,35 +786,58 @@ size_t max_smem_needed(const mra_ctx *c, int nmax)
 // evaluations.
 void count_work(mra_ctx *c)
 {
+    // on the device levels: Rk[m] knots of a level-m region, S[m] the knots of
+    // its ancestors (levels 1..m-1)
+    const Levels &G = c->G;
     const Partition &P = c->P;
-    const double R = P.R;
-    const int M = P.M, J = P.J;
+    const int M = G.M, J = P.J;
+    std::vector<double> Rk((size_t)M + 1, 0.0), S((size_t)M + 1, 0.0);
+    for (int m = 1; m <= M; m++) {
+        if (m < M) Rk[(size_t)m] = G.Rl[(size_t)m];
+        S[(size_t)m] = m > 1 ? S[(size_t)m - 1] + Rk[(size_t)m - 1] : 0.0;
+    }
     double f[K_COUNT] = {0};
     double cv = 0.0;
     for (int m = 1; m < M; m++) {
-        const double nr = (double)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]);
+        const double nr = (double)(G.lvl_off[(size_t)m + 1] - G.lvl_off[(size_t)m]);
+        const double R = Rk[(size_t)m], Sm = S[(size_t)m];
         double per = 0.0;
-        for (int l = 1; l < m; l++) per += 2.0 * (l - 1) * R * R * R + R * R * R; // W^l and W^l Linv'
-        per += (m - 1) * R * R * (R + 1) + 2.0 * R * R * R / 3.0;                 // self block, chol, inverse
+        for (int l = 1; l < m; l++) {
+            const double Rl = Rk[(size_t)l];
+            per += 2.0 * S[(size_t)l] * R * Rl + R * Rl * Rl; // W^l and W^l Linv'
+            cv += nr * R * Rl;
+        }
+        per += Sm * R * (R + 1) + 2.0 * R * R * R / 3.0; // self block, chol, inverse
         f[K_PRIOR] += nr * per;
-        cv += nr * ((m - 1) * R * R + R * (R + 1) / 2);
-        f[K_UP] += nr * (R * R * R / 3.0 + (m - 1) * R * R * R + R * R + (m - 1) * (m - 2) * R * R * R +
-                         (m - 1) * R * R * (R + 1) + 2.0 * (m - 1) * R * R);
+        cv += nr * R * (R + 1) / 2;
+        double upd = 0.0; // ATilde^{k,l} = A^{k,l} - Z_k' Z_l, k <= l < m
+        for (int l = 1; l < m; l++) {
+            upd += Rk[(size_t)l] * (Rk[(size_t)l] + 1) * R;
+            for (int k = 1; k < l; k++) upd += 2.0 * Rk[(size_t)k] * Rk[(size_t)l] * R;
+        }
+        f[K_UP] += nr * (R * R * R / 3.0 + Sm * R * R + R * R + upd + 2.0 * Sm * R);
     }
     if (M > 1) {
-        double perrow = 0.0;
-        for (int l = 1; l < M; l++) perrow += 2.0 * (l - 1) * R * R + R * R;
+        double perrow = 0.0, gram = 0.0;
+        for (int l = 1; l < M; l++) {
+            const double Rl = Rk[(size_t)l];
+            perrow += 2.0 * S[(size_t)l] * Rl + Rl * Rl;
+            gram += Rl * (Rl + 1);
+            for (int k = 1; k < l; k++) gram += 2.0 * Rk[(size_t)k] * Rl;
+        }
+        const double SM = S[(size_t)M];
         f[K_LEAFBASIS] += (double)P.n_used * perrow;
-        cv += (double)P.n_used * (M - 1) * R;
-        const int64_t nP = P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1];
+        cv += (double)P.n_used * SM;
+        const int64_t nP = G.lvl_off[(size_t)M] - G.lvl_off[(size_t)M - 1];
         for (int64_t p = 0; p < nP; p++) {
             const double N = (double)(P.leaf_off[(size_t)((p + 1) * J)] - P.leaf_off[(size_t)(p * J)]);
-            f[K_LEAFGRAM] += N * R * R * (M - 1) * (M - 2) + N * R * (R + 1) * (M - 1) + 2.0 * N * (M - 1) * R;
+            f[K_LEAFGRAM] += N * gram + 2.0 * N * SM;
         }
     }
+    const double SM = S[(size_t)M];
     for (int64_t l = 0; l < P.nleaf(); l++) {
         const double n = (double)(P.leaf_off[(size_t)l + 1] - P.leaf_off[(size_t)l]);
-        const double fl = (M - 1) * R * n * (n + 1) + n * n * n / 3.0 + (M - 1) * R * n * n + n * n;
+        const double fl = SM * n * (n + 1) + n * n * n / 3.0 + SM * n * n + n * n;
         if (n <= c->nmax_small || c->d_sx == nullptr)
             f[K_LEAFPOST] += fl;
         else
@@ -803,9 +911,9 @@ int max_batch_for(mra_ctx *c, size_t budget)
     c->ain_chunk = 0;
     Plan p = make_plan(c);
     size_t per = scratch_bytes_for(p, c, 1) + 4096;
-    const int M = c->P.M;
+    const int M = c->G.M;
     if (per > budget && M >= 2 && p.Ain > 0) {
-        const int64_t nP = c->P.lvl_off[(size_t)M] - c->P.lvl_off[(size_t)M - 1];
+        const int64_t nP = c->G.lvl_off[(size_t)M] - c->G.lvl_off[(size_t)M - 1];
         const size_t full_ain = scratch_bytes_for(p, c, 1);
         c->ain_chunk = 1;
         const size_t base = scratch_bytes_for(make_plan(c), c, 1);
@@ -1030,9 +1138,9 @@ mra_status predict_impl(mra_ctx *c, const double *theta, const std::vector<doubl
                         const std::vector<double> &sy, const std::vector<int64_t> &sl, double *mean_out,
                         double *var_out)
 {
-    const Partition &P = c->P;
-    const int M = P.M;
-    const int64_t np = (int64_t)sx.size(), NK = P.nnonleaf(), NL = P.nleaf();
+    const Levels &G = c->G;
+    const int M = G.M;
+    const int64_t np = (int64_t)sx.size(), NK = G.nnonleaf(), NL = G.nleaf();
     const int UC = (M - 1) * RP;
     const size_t stride = keep_up_doubles(M, RP);
     KeepGuard guard{c};
@@ -1060,7 +1168,7 @@ mra_status predict_impl(mra_ctx *c, const double *theta, const std::vector<doubl
     double *d_xi = (double *)(c->pred.tree + o_xi);
     int32_t *d_bigidx = (int32_t *)(c->pred.tree + o_bi);
     // per-point buffers
-    const int rows = chunk_rows<T>();
+    const int rows = (chunk_rows<T>() == 64 && !c->lb64_fits) ? 32 : chunk_rows<T>();
     std::vector<Chunk> chunks;
     if (M > 1)
         for (int64_t k = 0; k < np; k++) {
@@ -1243,12 +1351,12 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     mra_status st = build_partition(lon, lat, z, n, M, J, r, f, opt.dedup, c->P, c->err);
     if (st != MRA_OK) return st;
     const Partition &P = c->P;
-    if (P.R > 32) {
-        c->err = "r_hat > 32 is not supported by this build";
+    st = make_levels(P, c->G, c->err);
+    if (st != MRA_OK) {
         *out = c;
-        return MRA_EINVAL;
+        return st;
     }
-    c->RP = P.R <= 16 ? 16 : 32;
+    c->RP = c->G.RP;
     c->lgJ = J == 4 ? 2 : 1;
     if (opt.device < 0) { // host-only partition: stats and tree queries, no likelihood
         for (int64_t l = 0; l < P.nleaf(); l++) {
@@ -1279,14 +1387,25 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
             }
         }
     }
+    // The leaf buckets are sized where the FP64 kernels fit (they take twice
+    // the bytes); on trees too deep for them only the mixed modes run.
+    c->fp64_fits = max_smem_needed(c, kLeafCap[0], true) <= kSmemMax;
+    const bool f64 = c->fp64_fits;
     int nmax_small = kLeafCap[kLeafBuckets - 1];
-    while (nmax_small > kLeafCap[0] && max_smem_needed(c, nmax_small) > 227 * 1024) nmax_small -= 16;
-    if (max_smem_needed(c, nmax_small) > 227 * 1024) {
+    while (nmax_small > kLeafCap[0] && max_smem_needed(c, nmax_small, f64) > kSmemMax) nmax_small -= 16;
+    if (max_smem_needed(c, nmax_small, f64) > kSmemMax) {
         c->err = "M too large for the shared-memory kernels at this r";
         *out = c;
         return MRA_EINVAL;
     }
+    if (!f64 && c->precision == MRA_FP64) {
+        c->err = "tree too deep for the FP64 shared-memory kernels at this r; build in a mixed precision";
+        *out = c;
+        return MRA_EINVAL;
+    }
     c->nmax_small = nmax_small;
+    c->lb64_fits = (c->RP == 16 ? smem_leafbasis_cfg<float, 16>(c->G.M, 64, 1)
+                                : smem_leafbasis_cfg<float, 32>(c->G.M, 64, 1)) <= kSmemMax;
     std::vector<int64_t> lb[kLeafBuckets];
     std::vector<BigLeaf> big;
     int64_t voff = 0;
@@ -1356,20 +1475,10 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
             c->big_steps.push_back(st);
         }
     }
-    // device tree, knots padded to RP
-    std::vector<double> kxp((size_t)(P.nnonleaf() * c->RP), 0.0), kyp((size_t)(P.nnonleaf() * c->RP), 0.0);
-    for (int64_t g = 0; g < P.nnonleaf(); g++)
-        for (int j = 0; j < P.R; j++) {
-            kxp[(size_t)(g * c->RP + j)] = P.kx[(size_t)(g * P.R + j)];
-            kyp[(size_t)(g * c->RP + j)] = P.ky[(size_t)(g * P.R + j)];
-        }
-    std::vector<double> cxv((size_t)std::max<int64_t>(P.nnonleaf(), 1), 0.0), cyv(cxv.size(), 0.0);
-    for (int64_t g = 0; g < P.nnonleaf(); g++) {
-        cxv[(size_t)g] = P.bx0[(size_t)g];
-        cyv[(size_t)g] = P.by0[(size_t)g];
-    }
-    if ((st = dev_upload(c, &c->d_kx, kxp.data(), kxp.size())) || (st = dev_upload(c, &c->d_ky, kyp.data(), kyp.size())) ||
-        (st = dev_upload(c, &c->d_cx, cxv.data(), cxv.size())) || (st = dev_upload(c, &c->d_cy, cyv.data(), cyv.size())) ||
+    // device levels: knots padded to RP, region corners
+    const Levels &G = c->G;
+    if ((st = dev_upload(c, &c->d_kx, G.kx.data(), G.kx.size())) || (st = dev_upload(c, &c->d_ky, G.ky.data(), G.ky.size())) ||
+        (st = dev_upload(c, &c->d_cx, G.cx.data(), G.cx.size())) || (st = dev_upload(c, &c->d_cy, G.cy.data(), G.cy.size())) ||
         (st = dev_upload(c, &c->d_sx, P.sx.data(), P.sx.size())) || (st = dev_upload(c, &c->d_sy, P.sy.data(), P.sy.size())) ||
         (st = dev_upload(c, &c->d_sz, P.sz.data(), P.sz.size())) ||
         (st = dev_upload(c, &c->d_leaf_off, P.leaf_off.data(), P.leaf_off.size())) ||
@@ -1421,14 +1530,14 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         bool conc, queue;
     };
     const bool mixed = c->precision != MRA_FP64;
-    const int RP = c->RP, M = c->P.M;
+    const int RP = c->RP, M = c->G.M;
     auto smem_ok = [&](int rows, int stages) {
         size_t b;
         if (mixed)
             b = RP == 16 ? smem_leafbasis_cfg<float, 16>(M, rows, stages) : smem_leafbasis_cfg<float, 32>(M, rows, stages);
         else
             b = RP == 16 ? smem_leafbasis_cfg<double, 16>(M, rows, stages) : smem_leafbasis_cfg<double, 32>(M, rows, stages);
-        return b <= 227 * 1024;
+        return b <= kSmemMax;
     };
     std::vector<Cfg> cand;
     const Cfg start{c->lb_rows, c->lb_stages, c->bucket_set, c->concurrent, c->leaf_queue};
@@ -1489,7 +1598,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
     cudaStreamDestroy(st);
     if (rs != MRA_OK) return rs;
     if (out) {
-        out->leafbasis_rows = bestc.rows > 0 ? bestc.rows : (mixed ? 64 : 32);
+        out->leafbasis_rows = bestc.rows > 0 ? bestc.rows : ((mixed && c->lb64_fits) ? 64 : 32);
         int stages = bestc.stages;
         if (stages == 0) { // the automatic rule of the launcher
             const int r = out->leafbasis_rows;
@@ -1520,13 +1629,13 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
         return MRA_EINVAL;
     }
     if (stages > 0) {
-        const int r = rows > 0 ? rows : (mixed ? 64 : 32), RP = c->RP, M = c->P.M;
+        const int r = rows > 0 ? rows : (mixed ? 64 : 32), RP = c->RP, M = c->G.M;
         size_t b;
         if (mixed)
             b = RP == 16 ? smem_leafbasis_cfg<float, 16>(M, r, stages) : smem_leafbasis_cfg<float, 32>(M, r, stages);
         else
             b = RP == 16 ? smem_leafbasis_cfg<double, 16>(M, r, stages) : smem_leafbasis_cfg<double, 32>(M, r, stages);
-        if (b > 227 * 1024) {
+        if (b > kSmemMax) {
             c->err = "leaf-basis stages do not fit in shared memory";
             return MRA_EINVAL;
         }
@@ -1549,6 +1658,10 @@ mra_status mra_set_precision(mra_ctx *c, int precision)
         return MRA_EINVAL;
     }
     if (precision == c->precision) return MRA_OK;
+    if (precision == MRA_FP64 && !c->fp64_fits) {
+        c->err = "tree too deep for the FP64 shared-memory kernels at this r";
+        return MRA_EINVAL;
+    }
     c->precision = precision;
     c->lb_rows = c->lb_stages = c->bucket_set = 0; // tuned for the other precision
     c->concurrent = true;
@@ -1626,7 +1739,8 @@ mra_status mra_region_terms(mra_ctx *c, const double *theta, double *d, double *
     }
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    const int64_t NR = c->P.nreg(), NK = c->P.nnonleaf();
+    // the kernels record per device region; the output is per partition region
+    const int64_t NR = c->G.nreg(), NK = c->G.nnonleaf();
     if (!c->d_reg_du) {
         if (cudaMalloc((void **)&c->d_reg_du, sizeof(double) * 2 * (size_t)NR) != cudaSuccess ||
             cudaMalloc((void **)&c->d_reg_lw, sizeof(double) * (size_t)std::max<int64_t>(NK, 1)) != cudaSuccess) {
@@ -1653,10 +1767,27 @@ mra_status mra_region_terms(mra_ctx *c, const double *theta, double *d, double *
     if (e == cudaSuccess) e = cudaMemcpy(&ll, c->d_ll_stage, sizeof(double), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(&hs, d_st, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "region readback");
-    for (int64_t g = 0; g < NR; g++) {
-        if (d) d[g] = du[(size_t)(2 * g)];
-        if (u) u[g] = du[(size_t)(2 * g + 1)];
-        if (logdetW) logdetW[g] = g < NK ? lw[(size_t)g] : std::nan("");
+    // Partition region (level l, index i): d and u of its first device level
+    // (the terms of levels l..M, both halves of level l included); log|W| of
+    // its knots = log|W of the first half| + log|W of the second half given
+    // the first| (Schur complement).
+    const Partition &P = c->P;
+    const Levels &G = c->G;
+    for (int l = 1; l <= P.M; l++) {
+        const int m1 = l == P.M ? G.M : (G.split == 1 ? l : 2 * l - 1);
+        for (int64_t i = 0; i < P.lvl_off[(size_t)l + 1] - P.lvl_off[(size_t)l]; i++) {
+            const int64_t gr = P.lvl_off[(size_t)l] + i, gd = G.lvl_off[(size_t)m1] + i;
+            if (d) d[gr] = du[(size_t)(2 * gd)];
+            if (u) u[gr] = du[(size_t)(2 * gd + 1)];
+            if (logdetW) {
+                double v = std::nan("");
+                if (l < P.M) {
+                    v = lw[(size_t)gd];
+                    if (G.split == 2) v += lw[(size_t)(G.lvl_off[(size_t)m1 + 1] + i)];
+                }
+                logdetW[gr] = v;
+            }
+        }
     }
     if (loglik) *loglik = ll;
     return (mra_status)hs;
@@ -1742,6 +1873,7 @@ mra_status mra_stats(const mra_ctx *c, mra_stats_t *o)
     o->device_bytes = c->bytes_held;
     o->launches_per_pass = c->launches_last;
     for (int k = 0; k < 8; k++) o->flops_by_kernel[k] = c->flops_k[k];
+    o->device_levels = c->G.M;
     return MRA_OK;
 }
 

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
         }
         cp_async_commit();
     }
-    const int64_t gp = M > 1 ? t.lvl_off[M - 1] + (v.c >> t.lgJ) : -1;
+    const int64_t gp = M > 1 ? t.lvl_off[M - 1] + anc_index(t, v.c, M, M - 1) : -1;
     const double ox = gp >= 0 ? t.cx[gp] : t.sx[v.o0], oy = gp >= 0 ? t.cy[gp] : t.sy[v.o0];
     // coordinates once per point (mixed mode: as float pairs, one conversion a
     // thread; FP64 conversions are slow on this GPU)

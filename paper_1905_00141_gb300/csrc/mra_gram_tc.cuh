@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) k_gram_colexp(DevTree t, Work<float> w, i
     const int P = reg0 + blockIdx.x, Pl = blockIdx.x, b = blockIdx.y;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const int M = t.M, J = t.J, UC = (M - 1) * RP;
+    const int M = t.M, J = t.Jl[M - 1], UC = (M - 1) * RP;
     const int64_t r0 = t.leaf_off[(int64_t)P * J], r1 = t.leaf_off[(int64_t)P * J + J];
     const float *Yb = w.U + (size_t)b * w.U_stride;
     int8_t *ge = w.gexp + (size_t)b * w.gexp_stride + (size_t)Pl * UC;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kGramTcThreads) k_leafgram_tc(DevTree t, Work<
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
     const GramTile tl = tiles.t[blockIdx.y];
-    const int M = t.M, J = t.J, UC = (M - 1) * RP, np = npairs(M - 1);
+    const int M = t.M, J = t.Jl[M - 1], UC = (M - 1) * RP, np = npairs(M - 1);
     const int KC = tl.kc, W = tl.w, u0 = tl.u0, N = tl.n;
     const uint32_t SBO = (uint32_t)(KC / 8) * 128u, LBO = 128u;
     const int64_t r0 = t.leaf_off[(int64_t)P * J], r1 = t.leaf_off[(int64_t)P * J + J];

@@ -33,20 +33,38 @@
 #define __device__
 #endif
 
-#define MRA_MAXM 24
+#define MRA_MAXM 36
 #define MRA_NT 256
 
 namespace mra {
 
+// The tree the kernels run on.  Its levels are the partition's levels, except
+// that a region with more knots than one warp holds (33..64) enters its knots
+// in two successive levels of the same region: the first ceil(r/2) knots,
+// then the rest, with a single child between the two (Sec. 1.1 recursion: the
+// remainder after projecting on Q1 and then on Q2 is the remainder after
+// projecting on Q1 u Q2, so Sigma_MRA is unchanged).  Rl[m] is the number of
+// knots of a level-m region (the rest of the RP slots is inert padding), Jl[m]
+// the children of a level-m region, and region i of level m has the ancestor
+// i >> (sh[m] - sh[l]) at level l.
 struct DevTree {
-    int M, J, lgJ, R, RP;
+    int M, RP;
     int64_t n_used;
     const double *kx, *ky;
     const double *cx, *cy;
     const double *sx, *sy, *sz;
     const int64_t *leaf_off;
     int64_t lvl_off[MRA_MAXM + 2]; // first global region id of level m (1-based)
+    int Rl[MRA_MAXM + 1];
+    int Jl[MRA_MAXM + 1];
+    int sh[MRA_MAXM + 2];
 };
+
+// Index of the level-l ancestor of region i (index within its level) of level m.
+__host__ __device__ inline int64_t anc_index(const DevTree &t, int64_t i, int m, int l)
+{
+    return i >> (t.sh[m] - t.sh[l]);
+}
 
 template <typename T>
 struct Work {
@@ -87,6 +105,9 @@ struct Work {
     T *keep_li;
     double *keep_y;
 };
+
+// Dynamic shared memory one CTA may ask for on this GPU (227 KB).
+constexpr size_t kSmemMax = (size_t)227 * 1024;
 
 // Leading dimension of a kept leaf factor: the largest shared-memory bucket.
 constexpr int kKeepLd = 64;

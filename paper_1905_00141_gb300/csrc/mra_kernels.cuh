@@ -962,17 +962,25 @@ __device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, i
 // ------------------------------------------------------------------ prior --
 // Region i of level m (1 <= m <= M-1): What^1..What^{m-1} against its
 // ancestors, then W^m = C(Q,Q) - sum_k What^k What^k', its Cholesky factor L,
-// log|W^m| and Linv = L^{-1}.
+// log|W^m| and Linv = L^{-1}.  The ancestors' blocks are staged level by
+// level: in two buffers (the next level prefetched while this one is
+// computed), or in one on deep trees where two do not fit.
 template <typename T, int RP>
-__host__ __device__ constexpr size_t smem_prior_bytes(int m)
+__host__ __device__ constexpr size_t smem_prior_bytes(int m, int stages = 2)
 {
     return (size_t)RP * (RP + 1) * 8 + (RP + 2) * 8 + 8 * 8 + (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 +
-           4 * RP * sizeof(T) + (size_t)((m - 1) + 2 * (m > 1 ? m - 1 : 1) + 1) * RP * RP * sizeof(T) +
+           4 * RP * sizeof(T) + (size_t)((m - 1) + stages * (m > 1 ? m - 1 : 1) + 1) * RP * RP * sizeof(T) +
            RP * sizeof(T) + 64;
 }
 
 template <typename T, int RP>
-__global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
+__host__ __device__ constexpr int prior_stages(int m)
+{
+    return smem_prior_bytes<T, RP>(m, 2) <= kSmemMax ? 2 : 1;
+}
+
+template <typename T, int RP>
+__global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m, int stages)
 {
     using TL = Tile<RP, RP>;
     using F = typename FacT<T>::type;
@@ -993,28 +1001,35 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     T *sq = (T *)(flag + 16);               // own knots relative to the current origin: 2 RP
     T *sa = sq + 2 * RP;                    // ancestor knots: 2 RP
     T *sU = sa + 2 * RP;                    // (m-1) blocks k-major [t][row]
-    T *sB0 = sU + (size_t)(m - 1) * RP * RP; // 2 stages of up to m-1 ancestor blocks (column-major)
-    T *sW = sB0 + (size_t)2 * (m > 1 ? m - 1 : 1) * RP * RP; // RP x RP k-major
+    T *sB0 = sU + (size_t)(m - 1) * RP * RP; // `stages` stages of up to m-1 ancestor blocks (column-major)
+    T *sW = sB0 + (size_t)stages * (m > 1 ? m - 1 : 1) * RP * RP; // RP x RP k-major
 
-    const int R = t.R;
+    const int Rm = t.Rl[m]; // own knots
     const int64_t g = t.lvl_off[m] + i;
     if (tid == 0) flag[0] = 0;
     T *pb = w.prior + (size_t)b * w.prior_stride;
     const int r0 = TL::r0(), c0 = TL::c0();
-    // the level-l ancestor's blocks go to stage l & 1; level l + 1 is fetched
-    // with cp.async while level l is computed
+    // two stages: the level-l ancestor's blocks go to stage l & 1 and level
+    // l + 1 is fetched with cp.async while level l is computed; one stage:
+    // each level is fetched after the previous one's last read (the barrier
+    // that ends every level)
     const size_t stage = (size_t)(m > 1 ? m - 1 : 1) * RP * RP;
+    auto slot = [&](int l) { return sB0 + (size_t)(stages == 2 ? (l & 1) : 0) * stage; };
     auto fetch = [&](int l) {
-        const int64_t ia = (int64_t)i >> (t.lgJ * (m - l));
-        copy_g2s_async(sB0 + (size_t)(l & 1) * stage, pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP, l * RP * RP);
+        const int64_t ia = anc_index(t, i, m, l);
+        copy_g2s_async(slot(l), pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP, l * RP * RP);
         cp_async_commit();
     };
-    if (m > 1) fetch(1);
+    if (m > 1 && stages == 2) fetch(1);
     for (int l = 1; l < m; l++) {
-        const int64_t ia = (int64_t)i >> (t.lgJ * (m - l));
+        const int64_t ia = anc_index(t, i, m, l);
         const int64_t ga = t.lvl_off[l] + ia;
-        T *sB = sB0 + (size_t)(l & 1) * stage;
-        if (l + 1 < m) {
+        const int Ra = t.Rl[l]; // the ancestor's knots
+        T *sB = slot(l);
+        if (stages != 2) {
+            fetch(l);
+            cp_async_wait<0>();
+        } else if (l + 1 < m) {
             fetch(l + 1);
             cp_async_wait<1>();
         } else {
@@ -1032,7 +1047,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
         bool done = false;
         if constexpr (sizeof(T) == 4) {
             if (w.exact_rem) {
-                remainder_ff<RP, RP>(acc, sU, RP, sB, (l - 1) * RP, sq, RP, R, sa, R, s_par[0], s_par[1], s_cq);
+                remainder_ff<RP, RP>(acc, sU, RP, sB, (l - 1) * RP, sq, RP, Rm, sa, Ra, s_par[0], s_par[1], s_cq);
 #pragma unroll
                 for (int r = 0; r < TL::RT; r++)
 #pragma unroll
@@ -1048,7 +1063,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
 #pragma unroll
                 for (int c = 0; c < TL::CT; c++) {
                     const int a = r0 + r, j = c0 + c;
-                    const T cv = (a < R && j < R) ? cov_d(CovP<T>(th[0], s_ib), sq[a] - sa[j], sq[RP + a] - sa[RP + j]) : T(0);
+                    const T cv = (a < Rm && j < Ra) ? cov_d(CovP<T>(th[0], s_ib), sq[a] - sa[j], sq[RP + a] - sa[RP + j]) : T(0);
                     sW[j * RP + a] = cv - acc[r][c];
                 }
         }
@@ -1082,7 +1097,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
                 for (int c = 0; c < TL::CT; c++) {
                     const int a = r0 + r, j = c0 + c;
                     F v;
-                    if (a < R && j < R)
+                    if (a < Rm && j < Rm)
                         v = ff_sub_sloppy(ff_cov_exp(s2f, ibf, sq[a], sq[RP + a], sq[j], sq[RP + j]),
                                    ff{fa[r][c].hi, fa[r][c].lo});
                     else
@@ -1102,7 +1117,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
             for (int c = 0; c < TL::CT; c++) {
                 const int a = r0 + r, j = c0 + c;
                 F v;
-                if (a < R && j < R)
+                if (a < Rm && j < Rm)
                     v = f_of_T(cov_d(CovP<T>(th[0], s_ib), sq[a] - sq[j], sq[RP + a] - sq[RP + j]) - acc[r][c]);
                 else
                     v = f_of<F>(a == j ? 1.0 : 0.0);
@@ -1114,9 +1129,6 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m)
     // mixed mode calls such a factor singular at 1e-6 of the largest diagonal.
     if constexpr (sizeof(T) == 4)
         chol_blocked<RP>(sL, RP + 1, RP, srs, flag, 1e-6, red);
-    else
-        if constexpr (sizeof(T) == 4)
-        chol_blocked<RP>(sL, RP + 1, RP, srs, flag, MRA_SINGULAR, red);
     else
         chol_small<F, (tri_count(RP) + NT - 1) / NT>(sL, RP + 1, RP, srs, sr2, flag, MRA_SINGULAR);
     const double ld = logdet_small(sL, RP + 1, RP, red);
@@ -1163,7 +1175,7 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
     const float s_cq = grid_constant(th[0]);
     set_cov_params<T>(th, &s_ib, s_par);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = t.M, R = t.R, P = ch.parent, nr = ch.n;
+    const int M = t.M, P = ch.parent, nr = ch.n;
     T *sp = (T *)smem_raw;                  // 2 CH rows relative to the ancestor corner
     T *sa = sp + 2 * CH;                    // 2 RP
     T *sU = sa + 2 * RP;                     // (M-1) blocks k-major [t][row], stride LDC
@@ -1174,15 +1186,16 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
     // the ancestor's blocks of level l go to stage l & 1 (two stages: level
     // l + 1 is fetched with cp.async while level l is computed)
     auto fetch = [&](int l) {
-        const int64_t ia = (int64_t)P >> (t.lgJ * (M - 1 - l));
+        const int64_t ia = anc_index(t, P, M - 1, l);
         copy_g2s_async(sB0 + (size_t)((l & 1) * (stages - 1)) * (M - 1) * RP * RP,
                        pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP, l * RP * RP);
         cp_async_commit();
     };
     fetch(1);
     for (int l = 1; l <= M - 1; l++) {
-        const int64_t ia = (int64_t)P >> (t.lgJ * (M - 1 - l));
+        const int64_t ia = anc_index(t, P, M - 1, l);
         const int64_t ga = t.lvl_off[l] + ia;
+        const int R = t.Rl[l]; // the ancestor's knots
         T *sB = sB0 + (size_t)((l & 1) * (stages - 1)) * (M - 1) * RP * RP;
         if (stages == 2) {
             if (l + 1 <= M - 1) {
@@ -1326,7 +1339,7 @@ __device__ __forceinline__ void leafpost_small_leaf(const DevTree &t, const Work
         cp_async_commit();
     }
     // coordinates relative to the parent region's corner (level M-1)
-    const int64_t gp = M > 1 ? t.lvl_off[M - 1] + (c >> t.lgJ) : -1;
+    const int64_t gp = M > 1 ? t.lvl_off[M - 1] + anc_index(t, c, M, M - 1) : -1;
     const double ox = gp >= 0 ? t.cx[gp] : t.sx[o0], oy = gp >= 0 ? t.cy[gp] : t.sy[o0];
     for (int a = tid; a < n; a += NT) {
         if constexpr (sizeof(T) == 4) {
@@ -1568,7 +1581,7 @@ __global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w, int reg0)
     const int P = reg0 + blockIdx.x, Pl = blockIdx.x, b = blockIdx.z, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
-    const int M = t.M, J = t.J, D = M - 1, UC = D * RP;
+    const int M = t.M, J = t.Jl[M - 1], D = M - 1, UC = D * RP;
     const int np = npairs(D);
     // upper-triangle tile (ti <= tj) from the linear index
     const int nt = (UC + TS - 1) / TS;
@@ -1708,7 +1721,7 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
         }
         return;
     }
-    const int M = t.M, J = t.J;
+    const int M = t.M, J = t.Jl[m];
     const bool direct = (m == M - 1);
     const int nsrc = direct ? 1 : J;
     const int np = npairs(m), npo = npairs(m - 1);

@@ -20,7 +20,7 @@ static int set_smem(K kernel, size_t bytes, size_t *done)
     return 0;
 }
 
-template <typename T, int RP> size_t smem_prior(int m) { return smem_prior_bytes<T, RP>(m); }
+template <typename T, int RP> size_t smem_prior(int m) { return smem_prior_bytes<T, RP>(m, prior_stages<T, RP>(m)); }
 template <typename T, int RP> size_t smem_leafbasis_cfg(int M, int rows, int stages)
 {
     return smem_leafbasis_bytes<T, RP>(M, stages, rows);
@@ -42,10 +42,11 @@ template <typename T, int RP>
 int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream)
 {
     static size_t done = 0;
-    const size_t sm = smem_prior_bytes<T, RP>(m);
+    const int stages = prior_stages<T, RP>(m);
+    const size_t sm = smem_prior_bytes<T, RP>(m, stages);
     if (int e = set_smem(k_prior<T, RP>, sm, &done)) return e;
     dim3 grid((unsigned)(t.lvl_off[m + 1] - t.lvl_off[m]), (unsigned)B);
-    k_prior<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m);
+    k_prior<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, stages);
     return (int)cudaGetLastError();
 }
 

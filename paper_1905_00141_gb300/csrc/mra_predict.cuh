@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(32) k_down(DevTree t, const double *keep, size
     const double *Lt = kp, *rinv = kp + RP * RP, *v = rinv + RP, *Z = v + RP;
     double acc = lane < RP ? v[lane] : 0.0;
     for (int k = 1; k < m; k++) {
-        const int64_t anc = t.lvl_off[k] + (i >> (t.lgJ * (m - k)));
+        const int64_t anc = t.lvl_off[k] + anc_index(t, i, m, k);
         const double *xa = xi + (size_t)anc * RP;
         if (lane < RP)
             for (int bc = 0; bc < RP; bc++) acc -= Z[(size_t)lane * ldk + (k - 1) * RP + bc] * xa[bc];
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_predict(DevTree t, Work<T> w, PredArgs 
     for (int j = lane; j < UC; j += 32) {
         sa[j] = (double)Ua[j];
         const int l = j / RP + 1;
-        const int64_t anc = t.lvl_off[l] + (c >> (t.lgJ * (M - l)));
+        const int64_t anc = t.lvl_off[l] + anc_index(t, c, M, l);
         sxi[j] = q.xi[(size_t)anc * RP + (j % RP)];
     }
     const double x0 = q.px[p], y0 = q.py[p];
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_predict(DevTree t, Work<T> w, PredArgs 
     double qf = 0.0;
     const int ldk = (M - 2) * RP;
     for (int m = M - 1; m >= 1; m--) {
-        const int64_t anc = t.lvl_off[m] + (c >> (t.lgJ * (M - m)));
+        const int64_t anc = t.lvl_off[m] + anc_index(t, c, M, m);
         const double *kp = q.keep_up + (size_t)anc * q.keep_stride;
         const double *Lt = kp, *rinv = kp + RP * RP, *Z = kp + RP * RP + 2 * RP;
         double wa = lane < RP ? sg[(m - 1) * RP + lane] : 0.0;

@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("r_hat", ctypes.c_int), ("max_leaf", ctypes.c_int64), ("empty_leaves", ctypes.c_int64),
                 ("max_batch", ctypes.c_int), ("flops_per_theta", ctypes.c_double),
                 ("cov_evals_per_theta", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("launches_per_pass", ctypes.c_int), ("flops_by_kernel", ctypes.c_double * 8)]
+                ("launches_per_pass", ctypes.c_int), ("flops_by_kernel", ctypes.c_double * 8),
+                ("device_levels", ctypes.c_int)]
 
 KERNEL_FAMILIES = ["prior", "leafbasis", "leafpost", "leafpost_big", "leafgram", "up", "root"]
 

@@ -26,6 +26,12 @@ Workloads (sizes follow the configurations the library is measured on):
                the area); GP by circulant embedding on a 4096^2 grid
                (sigma2=1, beta=0.02, tau2=0.01); M=12, J=4, r=16.  Stand-in
                for the large MODIS scene (gaps where clouds mask pixels).
+* ``swaths``   n=2,439,827 uniform on [0,1]^2 inside parallel slanted bands
+               (a band of width 0.1 every 0.125 across the direction
+               (1, 0.35): 80% coverage, straight gaps between passes); GP by
+               circulant embedding on a 2048^2 grid (sigma2=1, beta=0.05,
+               tau2=0.01); M=14, J=2, r=49.  Stand-in for the AMSR scene of
+               the paper (satellite passes with gaps, its r = 49 binary tree).
 """
 from __future__ import annotations
 
@@ -38,6 +44,7 @@ WORKLOADS = {
     "grid": dict(n=131072, M=7, J=4, r=32, theta=(1.0, 0.05, 0.01)),
     "clustered": dict(n=2097152, M=9, J=4, r=32, theta=(1.0, 0.05, 0.01)),
     "massive": dict(n=47185920, M=12, J=4, r=16, theta=(1.0, 0.02, 0.01)),
+    "swaths": dict(n=2439827, M=14, J=2, r=49, theta=(1.0, 0.05, 0.01)),
 }
 
 SEED_BASE = 1905
@@ -193,6 +200,36 @@ def massive(seed: int = SEED_BASE + 6, n: int = 47185920, grid_n: int = 4096, n_
     return dict(x=x, y=y, z=z, M=12, J=4, r=16, theta=np.array([[s2, b, t2]]))
 
 
+def swaths(seed: int = SEED_BASE + 7, n: int = 2439827, grid_n: int = 2048, period: float = 0.125,
+           width: float = 0.1, slant: float = 0.35):
+    """n points uniform on [0,1]^2 kept where frac((x + slant y) / period) <
+    width / period (parallel slanted bands, the rest a gap), an oversample
+    trimmed to n; z from an exponential GP (sigma2=1, beta=0.05, tau2=0.01)
+    by circulant embedding on a grid_n^2 grid, nearest-cell value plus the
+    nugget; M=14, J=2, r=49."""
+    rng = np.random.default_rng(seed)
+    cover = width / period
+    m = int(n / cover * 1.05) + 1024
+    x = rng.random(m)
+    y = rng.random(m)
+    keep = np.mod((x + slant * y) / period, 1.0) < cover
+    idx = np.flatnonzero(keep)
+    if len(idx) < n:
+        raise ValueError("oversample too small")
+    idx = np.sort(rng.permutation(idx)[:n])
+    x, y = x[idx], y[idx]
+    perm = rng.permutation(n)
+    x, y = x[perm], y[perm]
+    s2, b, t2 = WORKLOADS["swaths"]["theta"]
+    h = 1.0 / (grid_n - 1)
+    field = gp_grid(grid_n, grid_n, h, h, s2, b, rng)
+    ix = np.clip(np.rint(x / h).astype(np.int64), 0, grid_n - 1)
+    iy = np.clip(np.rint(y / h).astype(np.int64), 0, grid_n - 1)
+    z = field[ix, iy] + math.sqrt(t2) * rng.standard_normal(n)
+    w = WORKLOADS["swaths"]
+    return dict(x=x, y=y, z=z, M=w["M"], J=w["J"], r=w["r"], theta=np.array([[s2, b, t2]]))
+
+
 def uniform(n: int, seed: int, sigma2=1.0, beta=0.1, tau2=0.05, exact=True):
     """Small uniform draw for tests (exact GP values when exact=True)."""
     rng = np.random.default_rng(seed)
@@ -206,4 +243,4 @@ def uniform(n: int, seed: int, sigma2=1.0, beta=0.1, tau2=0.05, exact=True):
 
 
 def make(name: str, **kw):
-    return {"small": small, "grid": grid, "clustered": clustered, "massive": massive}[name](**kw)
+    return {"small": small, "grid": grid, "clustered": clustered, "massive": massive, "swaths": swaths}[name](**kw)

@@ -8,10 +8,12 @@ line also records a fingerprint of the generated data (n, sums of the
 coordinates and of the values) so that a test can tell whether its own draw of
 the same workload is the one the stored value belongs to.
 
-    python tests/golden/make_full_size_oracle.py [clustered] [massive]
+    python tests/golden/make_full_size_oracle.py [clustered] [massive] [swaths]
 
 The clustered workload (n = 2,097,152, M = 9) takes about 80 s per theta on 8
-cores; the 47M-observation tree (M = 12) about 10 minutes for its one theta.
+cores; the 47M-observation tree (M = 12) about 10 minutes for its one theta;
+the swaths workload (n = 2,439,827, J = 2, M = 14, r = 49) is checked at two
+theta.
 """
 import os
 import sys
@@ -31,8 +33,10 @@ OUT = os.path.join(HERE, "full_size_oracle.txt")
 
 # theta rows checked per workload: the clustered ones are entries 0, 21, 42 and
 # 60 of the 4x4x4 log grid (60 is the corner sigma2 = 2, beta = 0.2,
-# tau2 = 0.005); the 47M tree is checked at its generating theta
-PICKS = {"clustered": [0, 21, 42, 60], "massive": None}
+# tau2 = 0.005); the 47M tree is checked at its generating theta; the swaths
+# tree at its generating theta and at a longer range with a smaller nugget
+PICKS = {"clustered": [0, 21, 42, 60], "massive": None, "swaths": None}
+SWATHS_EXTRA = [1.5, 0.15, 0.005]
 
 
 def fingerprint(d):
@@ -43,6 +47,8 @@ def fingerprint(d):
 def thetas_of(name, d):
     if name == "clustered":
         return synth.theta_grid_4x4x4()[PICKS[name]]
+    if name == "swaths":
+        return np.vstack([np.atleast_2d(d["theta"])[:1], [SWATHS_EXTRA]])
     return np.atleast_2d(d["theta"])[:1]
 
 

@@ -55,11 +55,36 @@ def _same_tree(x, y, z, M, J, r, offset=np.e / 100, dedup=False):
     o.close()
 
 
-@pytest.mark.parametrize("M,J,r", [(1, 4, 16), (3, 4, 16), (5, 2, 9), (4, 4, 32), (6, 2, 30), (3, 4, 2)])
+@pytest.mark.parametrize("M,J,r", [(1, 4, 16), (3, 4, 16), (5, 2, 9), (4, 4, 32), (6, 2, 30), (3, 4, 2),
+                                   (6, 2, 49), (3, 4, 64)])
 def test_host_partition_matches_oracle(M, J, r):
     x, y, z = synth.uniform(3000, 100 + M * 10 + J, exact=False)
     x = x * 2.3 - 0.4
     _same_tree(x, y, z, M, J, r)
+
+
+@pytest.mark.parametrize("M,J,r,levels", [(6, 2, 30, 6), (6, 2, 49, 11), (14, 2, 49, 27), (3, 4, 64, 5),
+                                          (1, 4, 49, 1)])
+def test_device_levels_of_wide_regions(M, J, r, levels):
+    """r_hat > 32: every non-leaf level runs as two device levels (Sec. 1.1
+    recursion entered in two halves of the knots); the partition the user sees
+    (stats, export) stays the paper's."""
+    x, y, z = synth.uniform(2000, 5, exact=False)
+    g = mra.MRA(x, y, z, M, J, r, device=-1)
+    s = g.stats()
+    assert s["M"] == M and s["device_levels"] == levels
+    assert s["n_regions"] == sum(J ** m for m in range(M))
+    g.close()
+
+
+def test_rhat_above_64_is_refused():
+    x, y, z = synth.uniform(500, 6, exact=False)
+    with pytest.raises(mra.MRAError) as e:
+        mra.MRA(x, y, z, 3, 4, 81, device=-1)  # r_hat = 9 x 9
+    assert e.value.status == mra.EINVAL and "64" in str(e.value)
+    with pytest.raises(mra.MRAError) as e:
+        mra.MRA(x, y, z, 19, 2, 49, device=-1)
+    assert e.value.status == mra.EINVAL and "device levels" in str(e.value)
 
 
 def test_host_partition_grid_workload():

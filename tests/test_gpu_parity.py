@@ -26,11 +26,11 @@ def _built():
     oracle.build()
 
 
-def _parity(x, y, z, M, J, r, thetas=THETAS, precisions=("fp64", "mixed"), **kw):
+def _parity(x, y, z, M, J, r, thetas=THETAS, precisions=("fp64", "mixed"), build_precision="fp64", **kw):
     ref, st = oracle.loglik(x, y, z, M, J, r, thetas, **kw)
     assert st == 0
     out = {}
-    with mra.MRA(x, y, z, M, J, r, **kw) as g:
+    with mra.MRA(x, y, z, M, J, r, precision=build_precision, **kw) as g:
         n = g.stats()["n_used"]
         for p in precisions:
             g.set_precision(p)
@@ -108,13 +108,17 @@ TOL_REGION_MIX = 1e-5
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_region_terms_match_oracle(precision):
+@pytest.mark.parametrize("M,J,r", [(4, 4, 16), (4, 2, 49)])
+def test_region_terms_match_oracle(precision, M, J, r):
+    # r = 49: the GPU runs every level as two device levels of the same
+    # regions; its records are mapped back to the partition's regions (d, u of
+    # the first half-level, log|W| summed over the halves)
     x, y, z = synth.uniform(3000, 21)
     th = np.array([1.2, 0.15, 0.03])
-    t = oracle.Tree(x, y, z, 4, 4, 16)
+    t = oracle.Tree(x, y, z, M, J, r)
     ro = t.region_terms(th)
     nr = _region_counts(t).astype(np.float64)
-    with mra.MRA(x, y, z, 4, 4, 16, precision=precision) as g:
+    with mra.MRA(x, y, z, M, J, r, precision=precision) as g:
         rg = g.region_terms(th)
     assert rg["status"] == 0 and ro["status"] == 0
     k = np.isfinite(ro["logdetW"])
@@ -135,6 +139,46 @@ def test_region_terms_match_oracle(precision):
     assert np.all(err_sum <= TOL_REGION_MIX), err_sum.max()
     assert np.all(err_d <= 1e-5) and np.all(err_u <= 1e-5), (err_d.max(), err_u.max())
     assert abs(rg["loglik"] - ro["loglik"]) <= TOLMIX * t.n_used
+
+
+# r_hat > 32: the kernels enter each region's knots in two device levels (the
+# first ceil(r_hat/2), then the rest: Sec. 1.1 recursion in two steps); the
+# oracle evaluates the paper's tree with all r_hat knots of a region at once.
+@pytest.mark.parametrize("n,M,J,r,seed", [
+    (3000, 3, 2, 49, 51),   # the paper's r = 49 on a binary tree
+    (4000, 4, 2, 49, 52),
+    (3000, 3, 4, 49, 53),
+    (2500, 2, 4, 64, 54),   # r_hat = 64: two halves of 32
+    (3000, 5, 2, 36, 55),   # r_hat = 36: 18 + 18, padded to 32 each
+    (600, 1, 4, 49, 56),    # M = 1: no knots, one leaf
+    (6000, 7, 2, 49, 57),   # 13 device levels: the deepest r = 49 tree the FP64 kernels fit
+])
+def test_parity_wide_regions(n, M, J, r, seed):
+    x, y, z = synth.uniform(n, seed)
+    with mra.MRA(x, y, z, M, J, r, device=-1) as h:
+        assert h.stats()["device_levels"] == (2 * (M - 1) + 1 if M > 1 else 1)
+    err = _parity(x, y, z, M, J, r)
+    print("r=%d M=%d J=%d |dl|/n" % (r, M, J), {k: float(v.max()) for k, v in err.items()})
+
+
+@pytest.mark.parametrize("n,M,seed", [(60000, 10, 61), (60000, 14, 62)])
+def test_parity_deep_binary_trees_r49(n, M, seed):
+    """The paper's AMSR tree shape (J = 2, r = 49) at depth 10 and 14: 19 and
+    27 device levels, on the swaths generator's data (slanted passes with
+    gaps, a GP field) at 60,000 points.  Only the mixed modes fit the
+    shared-memory kernels this deep; the FP64 mode is refused with EINVAL."""
+    d = synth.swaths(seed=seed, n=n, grid_n=512)
+    x, y, z = d["x"], d["y"], d["z"]
+    th = np.array([[1.0, 0.05, 0.01], [1.5, 0.15, 0.005]])
+    err = _parity(x, y, z, M, 2, 49, th, precisions=("mixed",), build_precision="mixed")
+    print("deep r=49 M=%d |dl|/n" % M, float(err["mixed"].max()))
+    with mra.MRA(x, y, z, M, 2, 49, precision="mixed") as g:
+        with pytest.raises(mra.MRAError) as e:
+            g.set_precision("fp64")
+        assert e.value.status == mra.EINVAL
+    with pytest.raises(mra.MRAError) as e:
+        mra.MRA(x, y, z, M, 2, 49, precision="fp64")
+    assert e.value.status == mra.EINVAL
 
 
 def test_batch_with_invalid_theta():

@@ -82,6 +82,17 @@ def test_predict_binary_tree_deeper():
     _check(x, y, z, 6, 2, 9, px, py)
 
 
+def test_predict_wide_regions_r49():
+    """r = 49 (J = 2, M = 4; J = 4, M = 3): the kernels run each level's
+    knots as two device levels; the predictive distribution is the paper's
+    (dense kriging with all 49 knots of a region at once)."""
+    rng = np.random.default_rng(8)
+    for M, J, seed in [(4, 2, 13), (3, 4, 14)]:
+        x, y, z = synth.uniform(1200, seed)
+        px, py = _points(rng, 30)
+        _check(x, y, z, M, J, 49, px, py)
+
+
 def test_predict_empty_leaf_and_large_leaf():
     """A tight cluster makes a leaf of more than 64 observations (the tiled
     large-leaf path) and a hole leaves leaves empty; points land in both."""

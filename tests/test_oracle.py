@@ -121,6 +121,7 @@ def test_m1_is_exact_dense_gaussian():
 CASES = [
     (90, 2, 4, 9, 1), (150, 3, 4, 9, 2), (200, 3, 4, 16, 3), (120, 3, 2, 4, 4),
     (200, 4, 2, 9, 5), (160, 4, 4, 4, 6), (100, 5, 2, 6, 7), (180, 2, 2, 30, 8),
+    (260, 3, 2, 49, 9), (220, 2, 4, 64, 10),
 ]
 
 
