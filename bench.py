@@ -73,9 +73,10 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-clustered", action="store_true",
                    help="skip the clustered 64-theta object of the default grid line")
-    p.add_argument("--launch", default=None, metavar="ROWS,STAGES,BUCKETS,CONCURRENT[,QUEUE]",
+    p.add_argument("--launch", default=None, metavar="ROWS,STAGES,BUCKETS,CONCURRENT[,QUEUE[,PRIOR]]",
                    help="pin the launch configuration (mra_set_launch) instead of running the autotuner, "
-                        "e.g. 64,1,0,1 (QUEUE 1: leaf buckets as persistent work queues)")
+                        "e.g. 64,1,0,1 (QUEUE 1: leaf buckets as persistent work queues; PRIOR 0/1/2: the "
+                        "prior's ancestor blocks in one or two buffers by occupancy, one, two)")
     p.add_argument("--workload", default="grid", choices=["grid", "clustered", "massive", "swaths"],
                    help="grid: n=131,072, 1 theta per call (default); clustered: n=2,097,152 with 64 theta per "
                         "call; massive: n=47,185,920, 1 theta per call; swaths: n=2,439,827, J=2, M=14, "
@@ -367,7 +368,7 @@ def run_ours(args):
     # launch configuration chosen by the library's autotuner (outside the timed region), or pinned
     def choose_launch():
         if args.launch:
-            keys = ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent", "leaf_queue")
+            keys = ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent", "leaf_queue", "prior_stages")
             cfg = dict(zip(keys, (int(v) for v in args.launch.split(","))))
             g.set_launch(**cfg)
             return dict(cfg, pinned=True)
@@ -481,8 +482,8 @@ def run_ours(args):
     # the same steps with the leaf Gram on the tensor cores (exact BF16 slices)
     gram_tc = None
     if name == "grid" and args.precision == "mixed":
-        cfg = {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent", "leaf_queue")
-               if k in tune}
+        cfg = {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent", "leaf_queue",
+                                    "prior_stages") if k in tune}
         g.set_launch(**cfg, gram_tensor_cores=True)
         ms_t, _, prof_t, ll_t = measure_precision(g, torch, args.precision, args, thetas, stream, flush, local)
         g.set_launch(**cfg, gram_tensor_cores=False)
@@ -517,7 +518,8 @@ def run_ours(args):
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "flops_per_eval": st["flops_per_theta"],
         "launch_config": {k: tune[k] for k in ("leafbasis_rows", "leafbasis_stages", "bucket_set", "concurrent",
-                                                "gram_tensor_cores", "leaf_queue", "pinned") if k in tune},
+                                                "gram_tensor_cores", "leaf_queue", "prior_stages", "pinned")
+                          if k in tune},
         "gram_tensor_cores": gram_tc,
         "predict": pred,
         "clustered": clus,

@@ -170,12 +170,15 @@ typedef struct {
     int leaf_queue;       /* 1: each leaf-size bucket runs as a persistent work-queue kernel (CTAs resident at
                              once take the leaves, largest first, through an atomic counter) instead of one CTA
                              per leaf; the same results bit for bit, so the autotuner tries both */
+    int prior_stages;     /* ancestor blocks of the prior staged in 0: one or two buffers per level by occupancy
+                             (one where it fits more CTAs per SM and saves a wave), 1: one buffer, 2: two
+                             where they fit (the next level prefetched); the same results bit for bit */
 } mra_tune_t;
 
 mra_status mra_autotune(mra_ctx *ctx, const double *theta, int reps, mra_tune_t *out);
 
 /* Set the launch configuration directly (the four configuration fields of
- * cfg, gram_tensor_cores and leaf_queue; the times are ignored).  leafbasis_rows 0 and
+ * cfg, gram_tensor_cores, leaf_queue and prior_stages; the times are ignored).  leafbasis_rows 0 and
  * leafbasis_stages 0 select the defaults; EINVAL for a value outside the
  * candidates or one whose shared memory does not fit. */
 mra_status mra_set_launch(mra_ctx *ctx, const mra_tune_t *cfg);

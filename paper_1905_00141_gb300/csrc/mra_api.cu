@@ -356,6 +356,7 @@ struct mra_ctx {
     bool concurrent = true;
     bool gram_tc = false; // mixed modes: leaf Gram on the tensor cores (exact slices)
     bool leaf_queue = false; // shared-memory leaf buckets as persistent work-queue kernels
+    int prior_st = 0;        // prior: 0 one or two stages by occupancy, 1 one stage, 2 two where they fit
     unsigned *d_qcnt = nullptr; // their counters: kLeafBuckets x status_cap
     BigLeaf *d_big = nullptr;
     int nbig = 0;
@@ -645,7 +646,8 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     int e;
     c->launches_last = 0;
     for (int m = 1; m < M; m++)
-        if ((e = timed_launch(c, K_PRIOR, s, [&] { return launch_prior<T, RP>(t, w, m, B, s); }))) return e;
+        if ((e = timed_launch(c, K_PRIOR, s, [&] { return launch_prior<T, RP>(t, w, m, B, c->prior_st, s); })))
+            return e;
     int rows = (sizeof(T) == 4 && c->lb_rows == 32) ? 32 : chunk_rows<T>();
     if (rows == 64 && !c->lb64_fits) rows = 32; // deep trees: 64-row chunks exceed shared memory
     const Chunk *chunks = rows == 64 ? c->d_chunks64 : c->d_chunks32;
@@ -1528,6 +1530,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
     struct Cfg {
         int rows, stages, set;
         bool conc, queue;
+        int prior;
     };
     const bool mixed = c->precision != MRA_FP64;
     const int RP = c->RP, M = c->G.M;
@@ -1540,7 +1543,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         return b <= kSmemMax;
     };
     std::vector<Cfg> cand;
-    const Cfg start{c->lb_rows, c->lb_stages, c->bucket_set, c->concurrent, c->leaf_queue};
+    const Cfg start{c->lb_rows, c->lb_stages, c->bucket_set, c->concurrent, c->leaf_queue, c->prior_st};
     cand.push_back(start);
     for (int rows : {64, 32}) {
         if (rows == 64 && !mixed) continue;
@@ -1549,7 +1552,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
             for (int set : {0, 1}) {
                 if (set == 1 && c->nmax_small < 64) continue;
                 for (bool conc : {true, false})
-                    for (bool queue : {false, true}) cand.push_back(Cfg{rows, stages, set, conc, queue});
+                    for (bool queue : {false, true}) cand.push_back(Cfg{rows, stages, set, conc, queue, start.prior});
             }
         }
     }
@@ -1567,29 +1570,52 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         c->bucket_set = g.set;
         c->concurrent = g.conc;
         c->leaf_queue = g.queue;
+        c->prior_st = g.prior;
         drop_graphs(c); // the pass changes
     };
     double best = 1e300, first = 0.0;
     Cfg bestc = start;
     mra_status rs = MRA_OK;
-    for (size_t q = 0; q < cand.size() && rs == MRA_OK; q++) {
-        apply(cand[q]);
+    int tried = 0;
+    // mean pass time of one candidate (2 untimed passes, then reps timed)
+    auto time_one = [&](const Cfg &g, double &per) {
+        apply(g);
         for (int w = 0; w < 2 && rs == MRA_OK; w++)
             rs = enqueue(c, c->d_theta_stage, 1, c->d_ll_stage, nullptr, st, false);
-        if (rs != MRA_OK) break;
+        if (rs != MRA_OK) return false;
         cudaEventRecord(e0, st);
         for (int r = 0; r < reps && rs == MRA_OK; r++)
             rs = enqueue(c, c->d_theta_stage, 1, c->d_ll_stage, nullptr, st, false);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) rs = cuda_fail(c, cudaGetLastError(), "autotune timing");
-        if (rs != MRA_OK) break;
+        if (rs != MRA_OK) return false;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double per = (double)ms / reps;
+        per = (double)ms / reps;
+        tried++;
+        return true;
+    };
+    // the leaf-side candidates, then the prior's staging (a kernel of its
+    // own) on the best of them
+    for (size_t q = 0; q < cand.size(); q++) {
+        double per = 0.0;
+        if (!time_one(cand[q], per)) break;
         if (q == 0) first = per;
         if (per < best) {
             best = per;
             bestc = cand[q];
+        }
+    }
+    const Cfg lead = bestc;
+    for (int ps : {0, 1, 2}) {
+        if (rs != MRA_OK || ps == lead.prior) continue;
+        Cfg g = lead;
+        g.prior = ps;
+        double per = 0.0;
+        if (!time_one(g, per)) break;
+        if (per < best) {
+            best = per;
+            bestc = g;
         }
     }
     apply(rs == MRA_OK ? bestc : start);
@@ -1611,9 +1637,10 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         out->concurrent = bestc.conc ? 1 : 0;
         out->gram_tensor_cores = c->gram_tc ? 1 : 0;
         out->leaf_queue = bestc.queue ? 1 : 0;
+        out->prior_stages = bestc.prior;
         out->ms_default = first;
         out->ms_best = best;
-        out->tried = (int)cand.size();
+        out->tried = tried;
     }
     return MRA_OK;
 }
@@ -1624,7 +1651,8 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
     const bool mixed = c->precision != MRA_FP64;
     const int rows = g->leafbasis_rows, stages = g->leafbasis_stages;
     if (!(rows == 0 || rows == 32 || (rows == 64 && mixed)) || stages < 0 || stages > 2 || g->bucket_set < 0 ||
-        g->bucket_set > 1 || (g->bucket_set == 1 && c->nmax_small < 64)) {
+        g->bucket_set > 1 || (g->bucket_set == 1 && c->nmax_small < 64) || g->prior_stages < 0 ||
+        g->prior_stages > 2) {
         c->err = "launch configuration outside the candidates";
         return MRA_EINVAL;
     }
@@ -1646,6 +1674,7 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
     c->concurrent = g->concurrent != 0;
     c->gram_tc = g->gram_tensor_cores != 0;
     c->leaf_queue = g->leaf_queue != 0;
+    c->prior_st = g->prior_stages;
     drop_graphs(c);
     return MRA_OK;
 }
@@ -1666,6 +1695,7 @@ mra_status mra_set_precision(mra_ctx *c, int precision)
     c->lb_rows = c->lb_stages = c->bucket_set = 0; // tuned for the other precision
     c->concurrent = true;
     c->leaf_queue = false;
+    c->prior_st = 0;
     if (c->d_sx) {
         // the scratch layout and the theta per pass depend on the storage type
         const int mb = max_batch_for(c, c->hbm_budget);

@@ -180,7 +180,7 @@ template <typename T> __host__ __device__ constexpr int chunk_rows() { return si
 
 // Launchers (one instantiation per precision T and padding RP).
 template <typename T, int RP>
-int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream);
+int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, int stages_req, void *stream);
 template <int RP>
 int launch_down(const DevTree &t, const double *keep, size_t stride, double *xi, int m, void *stream);
 template <typename T, int RP>

@@ -959,6 +959,14 @@ __device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, i
     __syncthreads();
 }
 
+// Bytes of the per-column Cholesky's scratch (chol_small, the FP64 kernels);
+// the mixed kernels' blocked Cholesky needs none.
+template <typename T, int N>
+__host__ __device__ constexpr size_t chol_scratch_bytes()
+{
+    return sizeof(T) == 8 ? (size_t)((tri_count(N) * 2 + 15) & ~15) : 0;
+}
+
 // ------------------------------------------------------------------ prior --
 // Region i of level m (1 <= m <= M-1): What^1..What^{m-1} against its
 // ancestors, then W^m = C(Q,Q) - sum_k What^k What^k', its Cholesky factor L,
@@ -968,7 +976,7 @@ __device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, i
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_prior_bytes(int m, int stages = 2)
 {
-    return (size_t)RP * (RP + 1) * 8 + (RP + 2) * 8 + 8 * 8 + (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 +
+    return (size_t)RP * (RP + 1) * 8 + (RP + 2) * 8 + 8 * 8 + chol_scratch_bytes<T, RP>() + 64 +
            4 * RP * sizeof(T) + (size_t)((m - 1) + stages * (m > 1 ? m - 1 : 1) + 1) * RP * RP * sizeof(T) +
            RP * sizeof(T) + 64;
 }
@@ -996,8 +1004,8 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m, int s
     F *sL = (F *)smem_raw;                  // RP x (RP+1)
     F *srs = sL + RP * (RP + 1);            // RP + 2
     double *red = (double *)(srs + RP + 2); // 8
-    F *sr2 = (F *)(red + 8);                // RP + 1 (squared reciprocal pivots)
-    int *flag = (int *)((unsigned char *)sr2 + ((tri_count(RP) * 2 + 15) & ~15));
+    F *sr2 = (F *)(red + 8);                // RP + 1 (squared reciprocal pivots; FP64 only)
+    int *flag = (int *)((unsigned char *)sr2 + chol_scratch_bytes<T, RP>());
     T *sq = (T *)(flag + 16);               // own knots relative to the current origin: 2 RP
     T *sa = sq + 2 * RP;                    // ancestor knots: 2 RP
     T *sU = sa + 2 * RP;                    // (m-1) blocks k-major [t][row]
@@ -1701,7 +1709,7 @@ template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_up_bytes(int m)
 {
     return (size_t)RP * (RP + 1) * 8 + (size_t)(m * RP) * 8 + (size_t)(RP + RP + 2 + 8) * 8 +
-           (size_t)((tri_count(RP) * 2 + 15) & ~15) + 64 + (size_t)(2 * m - 1) * RP * RP * sizeof(T) +
+           chol_scratch_bytes<T, RP>() + 64 + (size_t)(2 * m - 1) * RP * RP * sizeof(T) +
            (size_t)4 * RP * sizeof(T) + 64;
 }
 
@@ -1731,8 +1739,8 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
     F *sz = (F *)(sw + m * RP);                  // RP
     F *srs = sz + RP;                            // RP + 2
     double *red = (double *)(srs + RP + 2);      // 8
-    F *sr2 = (F *)(red + 8);                     // RP + 1
-    int *flag = (int *)((unsigned char *)sr2 + ((tri_count(RP) * 2 + 15) & ~15));
+    F *sr2 = (F *)(red + 8);                     // RP + 1 (FP64 only)
+    int *flag = (int *)((unsigned char *)sr2 + chol_scratch_bytes<T, RP>());
     T *sC = (T *)(flag + 16);                    // m blocks A^{k,m}, row-major
     T *sZ = sC + (size_t)m * B2;                 // RP x ((m-1) RP + 4)
     const T *blk[4];

@@ -38,14 +38,50 @@ template <typename T, int RP> size_t smem_big(int M)
     return a > p ? a : p;
 }
 
+// Stages of ancestor blocks for level m of the prior: stages_req 1 or 2
+// forces one (two where they fit); 0 takes one stage where that fits more
+// CTAs per SM and saves a wave of the level's CTAs (the prefetch of the
+// second stage then buys less than the extra CTAs hide), else two where
+// they fit.
 template <typename T, int RP>
-int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, void *stream)
+static int prior_stages_for(int m, long long ctas, int stages_req, size_t *done)
+{
+    const int fit = prior_stages<T, RP>(m);
+    if (stages_req == 1 || fit == 1) return 1;
+    if (stages_req == 2) return fit;
+    // decided once per (level, CTA count): the first pass runs uncaptured, so
+    // the queries below stay out of graph capture
+    static long long seen_ctas[MRA_MAXM + 1] = {0};
+    static int seen_stages[MRA_MAXM + 1] = {0};
+    if (seen_ctas[m] == ctas && seen_stages[m] > 0) return seen_stages[m];
+    if (set_smem(k_prior<T, RP>, smem_prior_bytes<T, RP>(m, 2), done)) return fit;
+    int dev = 0, sms = 0, o1 = 0, o2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_prior<T, RP>, NT, smem_prior_bytes<T, RP>(m, 1)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_prior<T, RP>, NT, smem_prior_bytes<T, RP>(m, 2)) !=
+            cudaSuccess ||
+        sms <= 0 || o1 <= 0 || o2 <= 0) {
+        cudaGetLastError();
+        return fit;
+    }
+    const long long w1 = (ctas + (long long)sms * o1 - 1) / ((long long)sms * o1);
+    const long long w2 = (ctas + (long long)sms * o2 - 1) / ((long long)sms * o2);
+    seen_ctas[m] = ctas;
+    seen_stages[m] = w1 < w2 ? 1 : 2;
+    return seen_stages[m];
+}
+
+template <typename T, int RP>
+int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, int stages_req, void *stream)
 {
     static size_t done = 0;
-    const int stages = prior_stages<T, RP>(m);
+    const long long nreg = (long long)(t.lvl_off[m + 1] - t.lvl_off[m]);
+    const int stages = prior_stages_for<T, RP>(m, nreg * B, stages_req, &done);
     const size_t sm = smem_prior_bytes<T, RP>(m, stages);
     if (int e = set_smem(k_prior<T, RP>, sm, &done)) return e;
-    dim3 grid((unsigned)(t.lvl_off[m + 1] - t.lvl_off[m]), (unsigned)B);
+    dim3 grid((unsigned)nreg, (unsigned)B);
     k_prior<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, stages);
     return (int)cudaGetLastError();
 }
@@ -253,7 +289,7 @@ int launch_predict(const DevTree &t, const Work<T> &w, const PredArgs &q, void *
     template size_t smem_leafpost_small<T, RP>(int, int);                                                   \
     template size_t smem_up<T, RP>(int);                                                                    \
     template size_t smem_leafgram<T, RP>(int);                                                              \
-    template int launch_prior<T, RP>(const DevTree &, const Work<T> &, int, int, void *);                   \
+    template int launch_prior<T, RP>(const DevTree &, const Work<T> &, int, int, int, void *);              \
     template int launch_leafbasis<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, int, int, \
                                          void *);                                                           \
     template int launch_leafpost_small<T, RP>(const DevTree &, const Work<T> &, const int64_t *, int, int,   \

@@ -311,6 +311,12 @@ def test_launch_configurations_agree_bit_for_bit(precision):
                         for queue in (False, True):
                             g.set_launch(r, stages, bset, conc, leaf_queue=queue)
                             assert np.array_equal(g.loglik(THETAS), ref), (r, stages, bset, conc, queue)
+        # the prior's ancestor blocks in one buffer, in two, or by occupancy
+        for ps in (1, 2, 0):
+            g.set_launch(prior_stages=ps)
+            assert np.array_equal(g.loglik(THETAS), ref), ps
+        with pytest.raises(mra.MRAError):
+            g.set_launch(prior_stages=3)
         rep = g.autotune(THETAS[0], reps=2)
         assert rep["tried"] >= 2 and rep["ms_best"] <= rep["ms_default"]
         assert np.array_equal(g.loglik(THETAS), ref)
