@@ -198,7 +198,7 @@ def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
     for f in ("mra_kernels.cuh", "mra_launch.cuh", "mra_bigleaf.cuh", "mra_predict.cuh", "mra_gram_tc.cuh",
-              "tc_sm100.cuh", "ff_math.h", "mra_internal.h"):
+              "mra_leafbasis_tc.cuh", "tc_sm100.cuh", "ff_math.h", "mra_internal.h"):
         with open(os.path.join(ROOT, "paper_1905_00141_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -493,6 +493,22 @@ def run_ours(args):
                    "accuracy_abs_dl_per_n": float(np.max(np.abs(ll_t - ref)) / n),
                    "note": "the same timed steps with mra_tune_t.gram_tensor_cores = 1 (tcgen05 BF16 MMAs of exact "
                            "fixed-grid slices; column exponents by k_gram_colexp); accuracy against the FP64 CPU oracle"}
+    # the same steps with the leaf basis's remainder products on the tensor cores
+    lb_tc = None
+    if name == "grid" and args.precision == "mixed":
+        g.set_launch(**cfg, leafbasis_tensor_cores=True)
+        ms_l, _, prof_l, ll_l = measure_precision(g, torch, args.precision, args, thetas, stream, flush, local)
+        g.set_launch(**cfg, leafbasis_tensor_cores=False)
+        lb_launches, lb_ms = prof_l.get("leafbasis", (0, 0.0))
+        lb_tc = {"ms_per_step": sum(ms_l) / args.steps, "value": whole_job_rate(n, per_call, args.steps,
+                                                                               sum(ms_l) / 1e3, 1),
+                 "leafbasis_ms_per_step": lb_ms / args.steps,
+                 "leafbasis_alu_tflops": (st["flops_by_kernel"]["leafbasis"] * per_call * args.steps / lb_ms / 1e9
+                                          if lb_ms > 0 else None),
+                 "accuracy_abs_dl_per_n": float(np.max(np.abs(ll_l - ref)) / n),
+                 "note": "the same timed steps with mra_tune_t.leafbasis_tensor_cores = 1 (remainder products as "
+                         "tcgen05 BF16 MMAs of five exact fixed-grid slices per value, 128 rows per CTA); accuracy "
+                         "against the FP64 CPU oracle"}
     pred = prediction_line(g, d, args.precision) if name == "grid" else None
     clus = None
     if name == "grid" and args.precision == "mixed" and not args.no_clustered:
@@ -521,6 +537,7 @@ def run_ours(args):
                                                 "gram_tensor_cores", "leaf_queue", "prior_stages", "pinned")
                           if k in tune},
         "gram_tensor_cores": gram_tc,
+        "leafbasis_tensor_cores": lb_tc,
         "predict": pred,
         "clustered": clus,
     }

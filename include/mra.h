@@ -173,12 +173,18 @@ typedef struct {
     int prior_stages;     /* ancestor blocks of the prior staged in 0: one or two buffers per level by occupancy
                              (one where it fits more CTAs per SM and saves a wave), 1: one buffer, 2: two
                              where they fit (the next level prefetched); the same results bit for bit */
+    int leafbasis_tensor_cores; /* MRA_MIXED: 1 runs the leaf basis's remainder products on the tensor cores
+                                   (tcgen05 BF16 MMAs of five exact fixed-grid slices per value, sums exact in
+                                   tensor memory, 128 rows per CTA); trees with (M - 2) x padded r_hat up to 192
+                                   (EINVAL beyond).  It differs from the CUDA-core kernel in the last bits, so
+                                   the autotuner reports it but does not switch it. */
 } mra_tune_t;
 
 mra_status mra_autotune(mra_ctx *ctx, const double *theta, int reps, mra_tune_t *out);
 
 /* Set the launch configuration directly (the four configuration fields of
- * cfg, gram_tensor_cores, leaf_queue and prior_stages; the times are ignored).  leafbasis_rows 0 and
+ * cfg, gram_tensor_cores, leaf_queue, prior_stages and leafbasis_tensor_cores;
+ * the times are ignored).  leafbasis_rows 0 and
  * leafbasis_stages 0 select the defaults; EINVAL for a value outside the
  * candidates or one whose shared memory does not fit. */
 mra_status mra_set_launch(mra_ctx *ctx, const mra_tune_t *cfg);

@@ -12,6 +12,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmra.so")
 SOURCES = ["mra_api.cu", "k_f64.cu", "k_f32.cu", "mra_noalloc.cu", "mra_mlp.cu"]
 HEADERS = ["mra_internal.h", "mra_kernels.cuh", "mra_launch.cuh", "mra_bigleaf.cuh", "mra_predict.cuh", "mra_gram_tc.cuh",
+           "mra_leafbasis_tc.cuh",
            "tc_sm100.cuh", "ff_math.h", "ff_tables.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -339,6 +339,8 @@ struct mra_ctx {
     int64_t *d_leaf_off = nullptr;
     Chunk *d_chunks32 = nullptr, *d_chunks64 = nullptr; // leaf-basis chunks of 32 / 64 rows
     int nchunks32 = 0, nchunks64 = 0;
+    Chunk *d_chunks128 = nullptr; // 128-row chunks of the tensor-core leaf basis
+    int nchunks128 = 0;
     // leaves with 1..kLeafCap[k] observations (and more than the previous cap),
     // one CTA each; larger leaves take the global-memory path
     int64_t *d_leaves[kLeafBuckets] = {nullptr, nullptr, nullptr};
@@ -355,6 +357,7 @@ struct mra_ctx {
     int lb_rows = 0, lb_stages = 0, bucket_set = 0;
     bool concurrent = true;
     bool gram_tc = false; // mixed modes: leaf Gram on the tensor cores (exact slices)
+    bool lb_tc = false;   // MRA_MIXED: leaf basis with its remainder products on the tensor cores
     bool leaf_queue = false; // shared-memory leaf buckets as persistent work-queue kernels
     int prior_st = 0;        // prior: 0 one or two stages by occupancy, 1 one stage, 2 two where they fit
     unsigned *d_qcnt = nullptr; // their counters: kLeafBuckets x status_cap
@@ -652,9 +655,11 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     if (rows == 64 && !c->lb64_fits) rows = 32; // deep trees: 64-row chunks exceed shared memory
     const Chunk *chunks = rows == 64 ? c->d_chunks64 : c->d_chunks32;
     const int nchunks = rows == 64 ? c->nchunks64 : c->nchunks32;
+    const bool lbtc = sizeof(T) == 4 && c->lb_tc && c->precision == MRA_MIXED;
     if (M > 1 && nchunks > 0)
         if ((e = timed_launch(c, K_LEAFBASIS, s, [&] {
-                 return launch_leafbasis<T, RP>(t, w, chunks, nchunks, rows, c->lb_stages, B, s);
+                 return lbtc ? launch_leafbasis_tc<T, RP>(t, w, c->d_chunks128, c->nchunks128, B, s)
+                             : launch_leafbasis<T, RP>(t, w, chunks, nchunks, rows, c->lb_stages, B, s);
              })))
             return e;
     // leaf posterior: the size buckets and the large-leaf pipeline touch
@@ -1372,13 +1377,13 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     cudaError_t e = cudaSetDevice(opt.device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     // work lists
-    std::vector<Chunk> chunks32, chunks64;
+    std::vector<Chunk> chunks32, chunks64, chunks128;
     if (M > 1) {
         const int64_t nP = P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1];
         for (int64_t p = 0; p < nP; p++) {
             const int64_t r0 = P.leaf_off[(size_t)(p * J)], r1 = P.leaf_off[(size_t)((p + 1) * J)];
-            for (int rows : {32, 64}) {
-                std::vector<Chunk> &dst = rows == 32 ? chunks32 : chunks64;
+            for (int rows : {32, 64, kLeafBasisTcRows}) {
+                std::vector<Chunk> &dst = rows == 32 ? chunks32 : (rows == 64 ? chunks64 : chunks128);
                 for (int64_t rb = r0; rb < r1; rb += rows) {
                     Chunk ch;
                     ch.parent = (int32_t)p;
@@ -1486,6 +1491,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         (st = dev_upload(c, &c->d_leaf_off, P.leaf_off.data(), P.leaf_off.size())) ||
         (st = dev_upload(c, &c->d_chunks32, chunks32.data(), chunks32.size())) ||
         (st = dev_upload(c, &c->d_chunks64, chunks64.data(), chunks64.size())) ||
+        (st = dev_upload(c, &c->d_chunks128, chunks128.data(), chunks128.size())) ||
         (st = dev_upload(c, &c->d_leaves[0], lb[0].data(), lb[0].size())) ||
         (st = dev_upload(c, &c->d_leaves[1], lb[1].data(), lb[1].size())) ||
         (st = dev_upload(c, &c->d_leaves[2], lb[2].data(), lb[2].size())) ||
@@ -1497,6 +1503,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     }
     c->nchunks32 = (int)chunks32.size();
     c->nchunks64 = (int)chunks64.size();
+    c->nchunks128 = (int)chunks128.size();
     for (int k = 0; k < kLeafBuckets; k++) c->nl[k] = (int)lb[k].size();
     c->nl_m = (int)lbm.size();
     c->nbig = (int)big.size();
@@ -1636,6 +1643,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         out->bucket_set = bestc.set;
         out->concurrent = bestc.conc ? 1 : 0;
         out->gram_tensor_cores = c->gram_tc ? 1 : 0;
+        out->leafbasis_tensor_cores = c->lb_tc ? 1 : 0;
         out->leaf_queue = bestc.queue ? 1 : 0;
         out->prior_stages = bestc.prior;
         out->ms_default = first;
@@ -1656,6 +1664,10 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
         c->err = "launch configuration outside the candidates";
         return MRA_EINVAL;
     }
+    if (g->leafbasis_tensor_cores && (c->G.M - 2) * c->RP > kLeafBasisTcMaxK) {
+        c->err = "tensor-core leaf basis: (M - 2) x padded r_hat must not exceed 192 (exact sums)";
+        return MRA_EINVAL;
+    }
     if (stages > 0) {
         const int r = rows > 0 ? rows : (mixed ? 64 : 32), RP = c->RP, M = c->G.M;
         size_t b;
@@ -1673,6 +1685,7 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
     c->bucket_set = g->bucket_set;
     c->concurrent = g->concurrent != 0;
     c->gram_tc = g->gram_tensor_cores != 0;
+    c->lb_tc = g->leafbasis_tensor_cores != 0;
     c->leaf_queue = g->leaf_queue != 0;
     c->prior_st = g->prior_stages;
     drop_graphs(c);
@@ -1978,7 +1991,7 @@ void mra_free(mra_ctx *c)
     }
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
-                    c->d_chunks64, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_leaves_m, c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
+                    c->d_chunks64, c->d_chunks128, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_leaves_m, c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
                     c->d_reg_du, c->d_reg_lw, c->pred.pt, c->pred.tree, c->d_qcnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -189,6 +189,12 @@ template <typename T, int RP>
 int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int rows, int stages,
                      int B, void *stream);
 template <typename T, int RP>
+int launch_leafbasis_tc(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int B, void *stream);
+// Rows per chunk of the tensor-core leaf basis, and the largest (M - 2) RP
+// its exact sums allow.
+constexpr int kLeafBasisTcRows = 128;
+constexpr int kLeafBasisTcMaxK = 192;
+template <typename T, int RP>
 int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves,
                           int nmax, int B, unsigned *queue, void *stream);
 // Tiled large-leaf posterior: one launch per phase; items of that phase.

@@ -6,6 +6,7 @@
 
 #include "mra_kernels.cuh"
 #include "mra_gram_tc.cuh"
+#include "mra_leafbasis_tc.cuh"
 
 namespace mra {
 
@@ -109,6 +110,25 @@ int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, in
     if constexpr (sizeof(T) == 4)
         if (rows == 64) return launch_leafbasis_ch<T, RP, 64>(t, w, chunks, nchunks, stages, B, stream);
     return launch_leafbasis_ch<T, RP, 32>(t, w, chunks, nchunks, stages, B, stream);
+}
+
+// mixed mode: the leaf basis with the remainder products on the tensor cores
+// (128-row chunks); EINVAL where the exactness bound does not hold
+template <typename T, int RP>
+int launch_leafbasis_tc(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int B, void *stream)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (nchunks == 0) return 0;
+        if ((t.M - 2) * RP > kLbTcMaxK) return (int)cudaErrorInvalidValue;
+        static size_t done = 0;
+        const size_t sm = smem_leafbasis_tc_bytes<RP>();
+        if (int e = set_smem(k_leafbasis_tc<RP>, sm, &done)) return e;
+        dim3 grid((unsigned)nchunks, (unsigned)B);
+        k_leafbasis_tc<RP><<<grid, kLbTcThreads, sm, (cudaStream_t)stream>>>(t, w, chunks);
+        return (int)cudaGetLastError();
+    } else {
+        return (int)cudaErrorInvalidValue;
+    }
 }
 
 template <typename T, int RP, int NMAX>
@@ -292,6 +312,7 @@ int launch_predict(const DevTree &t, const Work<T> &w, const PredArgs &q, void *
     template int launch_prior<T, RP>(const DevTree &, const Work<T> &, int, int, int, void *);              \
     template int launch_leafbasis<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, int, int, \
                                          void *);                                                           \
+    template int launch_leafbasis_tc<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, void *); \
     template int launch_leafpost_small<T, RP>(const DevTree &, const Work<T> &, const int64_t *, int, int,   \
                                               int, unsigned *, void *);                                     \
     template size_t smem_big<T, RP>(int);                                                                   \

@@ -397,3 +397,68 @@ def test_tensor_core_gram_ragged_and_grid_workload():
         err = np.abs(got - ref) / nu
         print("tensor-core Gram n=%d |dl|/n:" % nu, err)
         assert np.all(err <= TOLMIX), err
+
+
+# The leaf basis with its remainder products on the tensor cores (exact BF16
+# slices, MRA_MIXED): trees with (M - 2) x padded r_hat <= 192, padding 16 and
+# 32, J = 2 and 4, regions of more than 128 rows (several CTAs), r = 49 on two
+# device levels per level, and the gridded workload at full size.
+@pytest.mark.parametrize("n,M,J,r,seed", [
+    (600, 2, 4, 16, 2),      # one level: no products on the tensor cores
+    (3000, 4, 2, 30, 4),
+    (3000, 5, 4, 32, 5),
+    (4000, 6, 2, 16, 6),
+    (20000, 12, 2, 16, 41),  # (M - 2) 16 = 160; a GP field (the swaths generator) at 20,000 points
+    (3000, 4, 2, 49, 51),    # 7 device levels, r_hat 25 + 24 (padded 32)
+])
+def test_tensor_core_leafbasis_parity(n, M, J, r, seed):
+    if n <= 6000:
+        x, y, z = synth.uniform(n, seed)
+    else:
+        d = synth.swaths(seed=seed, n=n, grid_n=512)
+        x, y, z = d["x"], d["y"], d["z"]
+    th = THETAS[:2]
+    ref, st = oracle.loglik(x, y, z, M, J, r, th)
+    assert st == 0
+    with mra.MRA(x, y, z, M, J, r, precision="mixed") as g:
+        nu = g.stats()["n_used"]
+        cuda_core = g.loglik(th)
+        g.set_launch(leafbasis_tensor_cores=True)
+        assert g.autotune(th[0], reps=1)["leafbasis_tensor_cores"] == 1
+        tensor = g.loglik(th)
+        again = g.loglik(th)
+        g.set_launch(leafbasis_tensor_cores=False)
+        assert np.array_equal(g.loglik(th), cuda_core)
+    assert np.array_equal(tensor, again)
+    err = np.abs(tensor - ref) / nu
+    between = np.abs(tensor - cuda_core) / nu
+    print("tensor-core leaf basis M=%d r=%d |dl|/n:" % (M, r), err, "CUDA-core:", np.abs(cuda_core - ref) / nu,
+          "between:", between)
+    assert np.all(err <= TOLMIX), err
+    assert np.all(between <= 1e-7), between
+
+
+def test_tensor_core_leafbasis_grid_workload_and_limits():
+    d = synth.grid()
+    th = np.array([[1.0, 0.05, 0.01], [1.3, 0.08, 0.02], [2.0, 0.2, 0.005]])
+    ref, st = oracle.loglik(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], th)
+    assert st == 0
+    with mra.MRA(d["x"], d["y"], d["z"], d["M"], d["J"], d["r"], precision="mixed") as g:
+        nu = g.stats()["n_used"]
+        cuda_core = g.loglik(th)
+        g.set_launch(leafbasis_tensor_cores=True)
+        got = g.loglik(th)
+        # the fast mode keeps the CUDA-core kernel (FP32 remainder products)
+        g.set_precision("mixed_fast")
+        fast = g.loglik(th)
+        g.set_launch(leafbasis_tensor_cores=False)
+        assert np.array_equal(g.loglik(th), fast)
+    err = np.abs(got - ref) / nu
+    print("tensor-core leaf basis, grid |dl|/n:", err, "CUDA-core:", np.abs(cuda_core - ref) / nu)
+    assert np.all(err <= TOLMIX), err
+    # beyond the exactness bound: (M - 2) x 32 > 192
+    x, y, z = synth.uniform(3000, 9)
+    with mra.MRA(x, y, z, 9, 2, 30, precision="mixed") as g:
+        with pytest.raises(mra.MRAError) as e:
+            g.set_launch(leafbasis_tensor_cores=True)
+        assert e.value.status == mra.EINVAL
