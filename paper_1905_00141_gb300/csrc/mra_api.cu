@@ -462,6 +462,7 @@ struct Plan {
     size_t prior = 0, prior_lvl[MRA_MAXM + 1] = {0};
     size_t U = 0, leafw = 0, leafdu = 0, V = 0;
     size_t Ain = 0, Ainw = 0, Aindu = 0, Gexp = 0;
+    size_t lbA = 0, lbB = 0, lbB_lvl[MRA_MAXM + 1] = {0}; // bytes (tensor-core leaf basis)
     size_t Atil[MRA_MAXM + 1] = {0}, Atilw[MRA_MAXM + 1] = {0}, Atildu[MRA_MAXM + 1] = {0};
     size_t t_elems = 0, d_elems = 0; // totals
 };
@@ -489,6 +490,17 @@ Plan make_plan(const mra_ctx *c)
         p.Ainw = nP * (size_t)(M - 1) * RP;
         p.Aindu = 2 * nP;
         p.Gexp = nP * (size_t)(M - 1) * RP;
+        if (c->lb_tc && M >= 3) {
+            // fixed-grid slices: 5 planes of BF16 per block
+            const size_t bblk = (size_t)5 * RP * RP * 2, arow = (size_t)5 * kLeafBasisTcRows * RP * 2;
+            p.lbA = (size_t)c->nchunks128 * (size_t)(M - 2) * arow;
+            size_t acc_b = 0;
+            for (int m = 2; m <= M - 1; m++) {
+                p.lbB_lvl[m] = acc_b;
+                acc_b += (size_t)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]) * (size_t)(m - 1) * bblk;
+            }
+            p.lbB = acc_b;
+        }
         for (int m = 2; m <= M - 1; m++) {
             const size_t nr = (size_t)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]);
             p.Atil[m] = nr * (size_t)(m - 1) * m / 2 * B2;
@@ -547,6 +559,15 @@ Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
         off = align256(off + p.Gexp * (size_t)B);
         w.gexp_stride = p.Gexp;
     }
+    if (p.lbA > 0) {
+        w.lbA = base + off;
+        off = align256(off + p.lbA * (size_t)B);
+        w.lbA_stride = p.lbA;
+        w.lbB = base + off;
+        off = align256(off + p.lbB * (size_t)B);
+        w.lbB_stride = p.lbB;
+        for (int m = 0; m <= MRA_MAXM; m++) w.lbB_lvl[m] = p.lbB_lvl[m];
+    }
     for (int m = 2; m <= c->G.M - 1; m++) {
         w.Atil[m] = takeT8(p.Atil[m]);
         w.Atil_stride[m] = p.Atil[m];
@@ -577,6 +598,10 @@ size_t scratch_bytes_for(const Plan &p, const mra_ctx *c, int B)
     addD(p.Ainw);
     addD(p.Aindu);
     s = align256(s + p.Gexp * (size_t)B);
+    if (p.lbA > 0) {
+        s = align256(s + p.lbA * (size_t)B);
+        s = align256(s + p.lbB * (size_t)B);
+    }
     for (int m = 2; m <= c->G.M - 1; m++) {
         addT(p.Atil[m]);
         addD(p.Atilw[m]);
@@ -1685,7 +1710,15 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
     c->bucket_set = g->bucket_set;
     c->concurrent = g->concurrent != 0;
     c->gram_tc = g->gram_tensor_cores != 0;
-    c->lb_tc = g->leafbasis_tensor_cores != 0;
+    if ((g->leafbasis_tensor_cores != 0) != c->lb_tc) {
+        c->lb_tc = g->leafbasis_tensor_cores != 0;
+        if (c->d_sx) {
+            // the slice buffers join or leave the per-theta scratch
+            const int mb = max_batch_for(c, c->hbm_budget);
+            c->max_cap = c->user_max_batch > 0 ? std::min(c->user_max_batch, 1024) : mb;
+            c->cap = 0;
+        }
+    }
     c->leaf_queue = g->leaf_queue != 0;
     c->prior_st = g->prior_stages;
     drop_graphs(c);

@@ -88,6 +88,14 @@ struct Work {
     size_t Ain_stride, Ainw_stride, Aindu_stride;
     int8_t *gexp;   // [nP][(M-1) RP]: per column of Y below each region, e with 2^e > max |Y| (mixed mode)
     size_t gexp_stride;
+    // tensor-core leaf basis (null otherwise): fixed-grid BF16 slices of What,
+    // stored step-major (mra_kernels.cuh, tc_step_off).  lbB: each region of
+    // levels 2..M-1, its m - 1 blocks of RP x RP (at byte offset lbB_lvl[m] +
+    // i (m - 1) 5 RP^2 2); lbA: each 128-row chunk, its rows' What^1..What^{M-2}
+    // (chunk c, level k at (c (M - 2) + k - 1) 5 128 RP 2)
+    unsigned char *lbA, *lbB;
+    size_t lbA_stride, lbB_stride;
+    size_t lbB_lvl[MRA_MAXM + 1];
     T *Atil[MRA_MAXM + 1];
     double *Atil_w[MRA_MAXM + 1];
     double *Atil_du[MRA_MAXM + 1];

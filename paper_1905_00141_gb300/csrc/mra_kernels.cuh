@@ -959,6 +959,77 @@ __device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, i
     __syncthreads();
 }
 
+// ---------------------------------------------- fixed-grid BF16 slices --
+// Entries of the whitened basis at points and knots are bounded by sigma
+// (sum_k |What^k(x)|^2 <= C(x, x) = sigma2), so one grid serves all of them:
+// with 2^e > 2 sigma, v = q0 + ... + q4 with q_i = n_i 2^(e - 7 - 8 i),
+// |n_i| <= 128 (exact BF16 values), exact for an FP32 v down to 2^(e - 40).
+// Each q_i comes from rounding the remainder to its grid by adding and
+// subtracting 1.5 2^(e + 16 - 8 i) (round to nearest even; the subtraction of
+// q_i from the remainder is exact).  The tensor-core leaf basis sums the
+// slices' products by order (mra_leafbasis_tc.cuh); the prior writes its
+// regions' blocks in this form for it.
+constexpr int kTcSlices = 5;
+struct TcGrid {
+    float mag[kTcSlices];
+};
+__device__ __forceinline__ TcGrid tc_grid(double sigma2)
+{
+    const float sg = sqrtf((float)sigma2);
+    const int e = (int)((__float_as_uint(sg) >> 23) & 0xffu) - 127 + 2; // 2^e > 2 sigma
+    TcGrid g;
+#pragma unroll
+    for (int i = 0; i < kTcSlices; i++) g.mag[i] = __fmul_rn(1.5f, __int_as_float((127 + e + 16 - 8 * i) << 23));
+    return g;
+}
+// the slices of v as BF16 bit patterns (absolute units)
+__device__ __forceinline__ void tc_slices(float v, const TcGrid &g, uint32_t (&q)[kTcSlices])
+{
+    float r = v;
+#pragma unroll
+    for (int i = 0; i < kTcSlices; i++) {
+        const float qi = FSUB(FADD(r, g.mag[i]), g.mag[i]);
+        r = FSUB(r, qi);
+        q[i] = __float_as_uint(qi) >> 16; // <= 8 significant bits: the truncation is exact
+    }
+}
+// Eight values of one operand row at K positions 8 g .. 8 g + 7, sliced, as
+// one 16-byte core-matrix row in each of the five slice planes (plane stride
+// `plane` bytes, offset `off` of the row in plane 0).
+__device__ __forceinline__ void tc_put8(unsigned char *base, size_t plane, size_t off, const float (&v)[8],
+                                        const TcGrid &g)
+{
+    uint32_t w[kTcSlices][4];
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        uint32_t a[kTcSlices], b[kTcSlices];
+        tc_slices(v[2 * p], g, a);
+        tc_slices(v[2 * p + 1], g, b);
+#pragma unroll
+        for (int i = 0; i < kTcSlices; i++) w[i][p] = a[i] | (b[i] << 16);
+    }
+#pragma unroll
+    for (int i = 0; i < kTcSlices; i++)
+        *reinterpret_cast<uint4 *>(base + (size_t)i * plane + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+}
+// Sliced operands are stored step-major for the MMAs' K = 16 steps: per step
+// the five slice planes follow each other, and a plane holds the ROWS rows'
+// two no-swizzle K-major core matrices (8 rows x 16 bytes): 8-row groups 256
+// bytes apart (SBO), the step's two K groups 128 bytes apart (LBO).  One step
+// of all slices is contiguous (one bulk copy).
+template <int ROWS>
+__host__ __device__ constexpr size_t tc_step_plane() { return (size_t)ROWS * 32; }
+// byte offset of row r, K group g (values 8 g .. 8 g + 7), slice plane 0
+template <int ROWS>
+__host__ __device__ constexpr size_t tc_step_off(int r, int g)
+{
+    return (size_t)(g / 2) * kTcSlices * tc_step_plane<ROWS>() + (size_t)(r / 8) * 256u + (size_t)(g % 2) * 128u +
+           (size_t)(r % 8) * 16u;
+}
+// bytes of one sliced RP x RP block (the prior's What^k of a region)
+template <int RP>
+__host__ __device__ constexpr size_t tc_block_bytes() { return (size_t)kTcSlices * RP * RP * 2; }
+
 // Bytes of the per-column Cholesky's scratch (chol_small, the FP64 kernels);
 // the mixed kernels' blocked Cholesky needs none.
 template <typename T, int N>
@@ -1142,6 +1213,23 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m, int s
     const double ld = logdet_small(sL, RP + 1, RP, red);
     T *out = pb + w.prior_lvl[m] + (size_t)i * m * RP * RP;
     for (int e = tid; e < (m - 1) * RP * RP; e += NT) out[e] = sU[e];
+    if constexpr (sizeof(T) == 4) {
+        if (w.lbB && m >= 2) {
+            // What^1..What^{m-1} of the region as fixed-grid BF16 slices for the
+            // tensor-core leaf basis: operand rows = the region's knots j, K = the
+            // basis index t (element (j, t) of block k at sU[k RP^2 + t RP + j])
+            const TcGrid gr = tc_grid(th[0]);
+            constexpr size_t BB = tc_block_bytes<RP>();
+            unsigned char *dst = w.lbB + (size_t)b * w.lbB_stride + w.lbB_lvl[m] + (size_t)i * (m - 1) * BB;
+            for (int it = tid; it < (m - 1) * RP * (RP / 8); it += NT) {
+                const int k = it / (RP * (RP / 8)), rem = it % (RP * (RP / 8)), j = rem / (RP / 8), gg = rem % (RP / 8);
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) v[q] = sU[(size_t)k * RP * RP + (size_t)(8 * gg + q) * RP + j];
+                tc_put8(dst + (size_t)k * BB, tc_step_plane<RP>(), tc_step_off<RP>(j, gg), v, gr);
+            }
+        }
+    }
     // Linv stored column-major: element (a, j) at j*RP + a
     trinv_warp<T, RP>(sL, RP + 1, srs, out + (size_t)(m - 1) * RP * RP, RP, RP);
     if (tid == 0) {
