@@ -341,6 +341,8 @@ struct mra_ctx {
     int nchunks32 = 0, nchunks64 = 0;
     Chunk *d_chunks128 = nullptr; // 128-row chunks of the tensor-core leaf basis
     int nchunks128 = 0;
+    Chunk *d_chunks16 = nullptr; // 16-row chunks of the streaming leaf basis (deep trees)
+    int nchunks16 = 0;
     // leaves with 1..kLeafCap[k] observations (and more than the previous cap),
     // one CTA each; larger leaves take the global-memory path
     int64_t *d_leaves[kLeafBuckets] = {nullptr, nullptr, nullptr};
@@ -666,6 +668,15 @@ int timed_launch(mra_ctx *c, int kind, cudaStream_t s, F &&launch)
     return rc;
 }
 
+// The default leaf-basis kernel of a tree: the streaming one (16-row chunks,
+// ancestor blocks staged two at a time) where 32-row chunks in one stage
+// leave room for a single CTA per SM.
+template <typename T, int RP>
+bool leafbasis_streams(int M)
+{
+    return smem_leafbasis_cfg<T, RP>(M, 32, 1) > (size_t)112 * 1024;
+}
+
 template <typename T, int RP>
 int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
 {
@@ -676,10 +687,15 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     for (int m = 1; m < M; m++)
         if ((e = timed_launch(c, K_PRIOR, s, [&] { return launch_prior<T, RP>(t, w, m, B, c->prior_st, s); })))
             return e;
-    int rows = (sizeof(T) == 4 && c->lb_rows == 32) ? 32 : chunk_rows<T>();
-    if (rows == 64 && !c->lb64_fits) rows = 32; // deep trees: 64-row chunks exceed shared memory
-    const Chunk *chunks = rows == 64 ? c->d_chunks64 : c->d_chunks32;
-    const int nchunks = rows == 64 ? c->nchunks64 : c->nchunks32;
+    int rows;
+    if (c->lb_rows == kStreamRows || (c->lb_rows == 0 && leafbasis_streams<T, RP>(M))) {
+        rows = kStreamRows; // the streaming kernel (deep trees)
+    } else {
+        rows = (sizeof(T) == 4 && c->lb_rows == 32) ? 32 : chunk_rows<T>();
+        if (rows == 64 && !c->lb64_fits) rows = 32; // deep trees: 64-row chunks exceed shared memory
+    }
+    const Chunk *chunks = rows == 64 ? c->d_chunks64 : (rows == kStreamRows ? c->d_chunks16 : c->d_chunks32);
+    const int nchunks = rows == 64 ? c->nchunks64 : (rows == kStreamRows ? c->nchunks16 : c->nchunks32);
     const bool lbtc = sizeof(T) == 4 && c->lb_tc && c->precision == MRA_MIXED;
     if (M > 1 && nchunks > 0)
         if ((e = timed_launch(c, K_LEAFBASIS, s, [&] {
@@ -1402,13 +1418,14 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     cudaError_t e = cudaSetDevice(opt.device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     // work lists
-    std::vector<Chunk> chunks32, chunks64, chunks128;
+    std::vector<Chunk> chunks32, chunks64, chunks128, chunks16;
     if (M > 1) {
         const int64_t nP = P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1];
         for (int64_t p = 0; p < nP; p++) {
             const int64_t r0 = P.leaf_off[(size_t)(p * J)], r1 = P.leaf_off[(size_t)((p + 1) * J)];
-            for (int rows : {32, 64, kLeafBasisTcRows}) {
-                std::vector<Chunk> &dst = rows == 32 ? chunks32 : (rows == 64 ? chunks64 : chunks128);
+            for (int rows : {32, 64, kLeafBasisTcRows, kStreamRows}) {
+                std::vector<Chunk> &dst =
+                    rows == 32 ? chunks32 : (rows == 64 ? chunks64 : (rows == kStreamRows ? chunks16 : chunks128));
                 for (int64_t rb = r0; rb < r1; rb += rows) {
                     Chunk ch;
                     ch.parent = (int32_t)p;
@@ -1517,6 +1534,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         (st = dev_upload(c, &c->d_chunks32, chunks32.data(), chunks32.size())) ||
         (st = dev_upload(c, &c->d_chunks64, chunks64.data(), chunks64.size())) ||
         (st = dev_upload(c, &c->d_chunks128, chunks128.data(), chunks128.size())) ||
+        (st = dev_upload(c, &c->d_chunks16, chunks16.data(), chunks16.size())) ||
         (st = dev_upload(c, &c->d_leaves[0], lb[0].data(), lb[0].size())) ||
         (st = dev_upload(c, &c->d_leaves[1], lb[1].data(), lb[1].size())) ||
         (st = dev_upload(c, &c->d_leaves[2], lb[2].data(), lb[2].size())) ||
@@ -1529,6 +1547,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
     c->nchunks32 = (int)chunks32.size();
     c->nchunks64 = (int)chunks64.size();
     c->nchunks128 = (int)chunks128.size();
+    c->nchunks16 = (int)chunks16.size();
     for (int k = 0; k < kLeafBuckets; k++) c->nl[k] = (int)lb[k].size();
     c->nl_m = (int)lbm.size();
     c->nbig = (int)big.size();
@@ -1577,9 +1596,10 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
     std::vector<Cfg> cand;
     const Cfg start{c->lb_rows, c->lb_stages, c->bucket_set, c->concurrent, c->leaf_queue, c->prior_st};
     cand.push_back(start);
-    for (int rows : {64, 32}) {
+    for (int rows : {64, 32, kStreamRows}) {
         if (rows == 64 && !mixed) continue;
         for (int stages : {1, 2}) {
+            if (rows == kStreamRows && stages == 2) continue; // stages do not apply to the streaming kernel
             if (!smem_ok(rows, stages)) continue;
             for (int set : {0, 1}) {
                 if (set == 1 && c->nmax_small < 64) continue;
@@ -1656,8 +1676,11 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
     cudaStreamDestroy(st);
     if (rs != MRA_OK) return rs;
     if (out) {
-        out->leafbasis_rows = bestc.rows > 0 ? bestc.rows : ((mixed && c->lb64_fits) ? 64 : 32);
+        const bool streams = mixed ? (RP == 16 ? leafbasis_streams<float, 16>(M) : leafbasis_streams<float, 32>(M))
+                                   : (RP == 16 ? leafbasis_streams<double, 16>(M) : leafbasis_streams<double, 32>(M));
+        out->leafbasis_rows = bestc.rows > 0 ? bestc.rows : (streams ? kStreamRows : ((mixed && c->lb64_fits) ? 64 : 32));
         int stages = bestc.stages;
+        if (out->leafbasis_rows == kStreamRows) stages = 1;
         if (stages == 0) { // the automatic rule of the launcher
             const int r = out->leafbasis_rows;
             const size_t b2 = mixed ? (RP == 16 ? smem_leafbasis_cfg<float, 16>(M, r, 2) : smem_leafbasis_cfg<float, 32>(M, r, 2))
@@ -1683,7 +1706,8 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
     if (!c || !g) return MRA_EINVAL;
     const bool mixed = c->precision != MRA_FP64;
     const int rows = g->leafbasis_rows, stages = g->leafbasis_stages;
-    if (!(rows == 0 || rows == 32 || (rows == 64 && mixed)) || stages < 0 || stages > 2 || g->bucket_set < 0 ||
+    if (!(rows == 0 || rows == 32 || rows == kStreamRows || (rows == 64 && mixed)) || stages < 0 || stages > 2 ||
+        g->bucket_set < 0 ||
         g->bucket_set > 1 || (g->bucket_set == 1 && c->nmax_small < 64) || g->prior_stages < 0 ||
         g->prior_stages > 2) {
         c->err = "launch configuration outside the candidates";
@@ -2024,7 +2048,7 @@ void mra_free(mra_ctx *c)
     }
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
-                    c->d_chunks64, c->d_chunks128, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_leaves_m, c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
+                    c->d_chunks64, c->d_chunks128, c->d_chunks16, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_leaves_m, c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
                     c->d_reg_du, c->d_reg_lw, c->pred.pt, c->pred.tree, c->d_qcnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -183,6 +183,10 @@ struct BigTile {
 // (n^2), z then y (n), reciprocal pivots (n), (log-det, quadratic form) (2).
 inline int64_t big_leaf_scratch(int64_t n) { return n * n + 2 * n + 2; }
 
+// The streaming leaf basis of deep trees: rows per chunk and ancestor blocks
+// staged at a time (mra_tune_t.leafbasis_rows = 16 selects it).
+constexpr int kStreamRows = 16, kStreamBlocks = 2;
+
 // Observation rows per leaf-basis chunk: 64 in FP32, 32 in FP64 (shared memory).
 template <typename T> __host__ __device__ constexpr int chunk_rows() { return sizeof(T) == 4 ? 64 : 32; }
 

@@ -263,6 +263,26 @@ __device__ __forceinline__ void tile_fma_ff(FF (&acc)[Tile<ROWS, COLS>::RT][Tile
         }
 }
 
+// The grid accumulation of tile_fma_ff over K terms without its start and its
+// rounding (the streaming leaf basis accumulates one staged part of K at a
+// time, in the same order of terms).
+template <int ROWS, int COLS>
+__device__ __forceinline__ void tile_grid_add(grid_acc (&g)[Tile<ROWS, COLS>::RT][Tile<ROWS, COLS>::CT], const float *A,
+                                              int lda, const float *B, int ldb, int K)
+{
+    using TL = Tile<ROWS, COLS>;
+    const int r0 = TL::r0(), c0 = TL::c0();
+    for (int t = 0; t < K; t++) {
+        float a[TL::RT], b[TL::CT];
+        ldv<float, TL::RT>(a, A + t * lda + r0);
+        ldv<float, TL::CT>(b, B + t * ldb + c0);
+#pragma unroll
+        for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+            for (int c = 0; c < TL::CT; c++) grid_add(g[r][c], a[r], b[c]);
+    }
+}
+
 // The remainder C(P, Q) - sum_k What^k(P) What^k(Q)' of one RP-column block
 // (Sec. 1.1 recursion) for FP32 storage, with the covariance in float pairs
 // and the product sum to ~1e-11 sigma2 (tile_fma_ff): the prior evaluates it
@@ -1346,6 +1366,134 @@ __global__ void __launch_bounds__(NT) k_leafbasis(DevTree t, Work<T> w, const Ch
         for (int r = 0; r < TL::RT; r++)
 #pragma unroll
             for (int c = 0; c < TL::CT; c++) out[(c0 + c) * LDC + r0 + r] = acc[r][c];
+        __syncthreads();
+    }
+    const int UC = (M - 1) * RP;
+    T *Ub = w.U + (size_t)b * w.U_stride + (size_t)ch.row0 * UC;
+    for (int e = tid; e < nr * UC; e += NT) {
+        const int a = e / UC, col = e % UC;
+        Ub[e] = sU[(size_t)col * LDC + a];
+    }
+}
+
+// The leaf basis for deep trees: the same rows-by-level recursion as
+// k_leafbasis, with the level's ancestor blocks staged KB at a time instead of
+// all at once, so that 16-row chunks of deep trees fit several CTAs per SM
+// (27 device levels at RP = 32: one CTA per SM with 32 rows and all blocks,
+// three with 16 rows and two blocks).  Every output is formed by the same
+// terms in the same order as in k_leafbasis, so the two give the same U bit
+// for bit.
+template <typename T, int RP, int CH, int KB>
+__host__ __device__ constexpr size_t smem_leafbasis_stream_bytes(int M)
+{
+    return (size_t)(2 * CH + 2 * RP) * sizeof(T) + (size_t)(M - 1) * RP * (CH + 2) * sizeof(T) +
+           (size_t)KB * RP * RP * sizeof(T) + (size_t)RP * (CH + 2) * sizeof(T) + 64;
+}
+
+template <typename T, int RP, int CH, int KB>
+__global__ void __launch_bounds__(NT) k_leafbasis_stream(DevTree t, Work<T> w, const Chunk *chunks)
+{
+    constexpr int LDC = CH + 2;
+    using TL = Tile<CH, RP>;
+    const Chunk ch = chunks[blockIdx.x];
+    const int b = blockIdx.y, tid = threadIdx.x;
+    const double *th = w.theta + 3 * b;
+    if (!theta_ok(th)) return;
+    __shared__ double s_ib;
+    __shared__ ff s_par[2]; // sigma2 and 1/beta as float pairs
+    const float s_cq = grid_constant(th[0]);
+    set_cov_params<T>(th, &s_ib, s_par);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = t.M, P = ch.parent, nr = ch.n;
+    T *sp = (T *)smem_raw;                    // 2 CH rows relative to the ancestor corner
+    T *sa = sp + 2 * CH;                      // 2 RP
+    T *sU = sa + 2 * RP;                      // (M-1) blocks k-major [t][row], stride LDC
+    T *sB = sU + (size_t)(M - 1) * RP * LDC;  // KB ancestor blocks
+    T *sW = sB + (size_t)KB * RP * RP;        // RP x LDC k-major
+    const T *pb = w.prior + (size_t)b * w.prior_stride;
+    const int r0 = TL::r0(), c0 = TL::c0();
+    for (int l = 1; l <= M - 1; l++) {
+        const int64_t ia = anc_index(t, P, M - 1, l);
+        const int64_t ga = t.lvl_off[l] + ia;
+        const int R = t.Rl[l]; // the ancestor's knots
+        const T *anc = pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP;
+        const double ox = t.cx[ga], oy = t.cy[ga];
+        if (tid < CH) {
+            sp[tid] = tid < nr ? (T)(t.sx[ch.row0 + tid] - ox) : T(0);
+            sp[CH + tid] = tid < nr ? (T)(t.sy[ch.row0 + tid] - oy) : T(0);
+        }
+        if (tid < RP) {
+            sa[tid] = (T)(t.kx[ga * RP + tid] - ox);
+            sa[RP + tid] = (T)(t.ky[ga * RP + tid] - oy);
+        }
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (w.exact_rem) {
+                grid_acc g[TL::RT][TL::CT];
+#pragma unroll
+                for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                    for (int c = 0; c < TL::CT; c++) grid_init(g[r][c], s_cq);
+                for (int k0 = 0; k0 < l - 1; k0 += KB) {
+                    const int nb = min(KB, l - 1 - k0);
+                    copy_g2s_async(sB, anc + (size_t)k0 * RP * RP, nb * RP * RP);
+                    cp_async_commit();
+                    cp_async_wait<0>();
+                    __syncthreads();
+                    tile_grid_add<CH, RP>(g, sU + (size_t)k0 * RP * LDC, LDC, sB, RP, nb * RP);
+                    __syncthreads();
+                }
+                __syncthreads(); // sp and sa (written above) before the covariance
+#pragma unroll
+                for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                    for (int c = 0; c < TL::CT; c++) {
+                        const int a = r0 + r, j = c0 + c;
+                        ff cv = ff{0.f, 0.f};
+                        if (a < nr && j < R) cv = ff_cov_exp(s_par[0], s_par[1], sp[a], sp[CH + a], sa[j], sa[RP + j]);
+                        const ff fa = grid_value(g[r][c], s_cq);
+                        sW[(c0 + c) * LDC + r0 + r] = FADD(FSUB(cv.hi, fa.hi), FSUB(cv.lo, fa.lo));
+                    }
+                done = true;
+            }
+        }
+        if (!done) {
+            T acc[TL::RT][TL::CT];
+            tile_zero(acc);
+            for (int k0 = 0; k0 < l - 1; k0 += KB) {
+                const int nb = min(KB, l - 1 - k0);
+                copy_g2s_async(sB, anc + (size_t)k0 * RP * RP, nb * RP * RP);
+                cp_async_commit();
+                cp_async_wait<0>();
+                __syncthreads();
+                tile_fma<T, CH, RP>(acc, sU + (size_t)k0 * RP * LDC, LDC, sB, RP, nb * RP);
+                __syncthreads();
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                for (int c = 0; c < TL::CT; c++) {
+                    const int a = r0 + r, j = c0 + c;
+                    const T cv = (a < nr && j < R) ? cov_d(CovP<T>(th[0], s_ib), sp[a] - sa[j], sp[CH + a] - sa[RP + j]) : T(0);
+                    sW[j * LDC + a] = cv - acc[r][c];
+                }
+        }
+        // What^l = W Linv' with the ancestor's Linv (its last block)
+        copy_g2s_async(sB, anc + (size_t)(l - 1) * RP * RP, RP * RP);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        {
+            T acc[TL::RT][TL::CT];
+            tile_zero(acc);
+            tile_fma<T, CH, RP>(acc, sW, LDC, sB, RP, RP);
+            T *out = sU + (size_t)(l - 1) * RP * LDC;
+#pragma unroll
+            for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                for (int c = 0; c < TL::CT; c++) out[(c0 + c) * LDC + r0 + r] = acc[r][c];
+        }
         __syncthreads();
     }
     const int UC = (M - 1) * RP;

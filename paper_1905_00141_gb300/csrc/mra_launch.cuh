@@ -24,6 +24,7 @@ static int set_smem(K kernel, size_t bytes, size_t *done)
 template <typename T, int RP> size_t smem_prior(int m) { return smem_prior_bytes<T, RP>(m, prior_stages<T, RP>(m)); }
 template <typename T, int RP> size_t smem_leafbasis_cfg(int M, int rows, int stages)
 {
+    if (rows == kStreamRows) return smem_leafbasis_stream_bytes<T, RP, kStreamRows, kStreamBlocks>(M);
     return smem_leafbasis_bytes<T, RP>(M, stages, rows);
 }
 template <typename T, int RP> size_t smem_leafbasis(int M)
@@ -100,13 +101,22 @@ static int launch_leafbasis_ch(const DevTree &t, const Work<T> &w, const Chunk *
     return (int)cudaGetLastError();
 }
 
-// rows: observation rows per chunk (32, or 64 in FP32); stages: 1 or 2 stages
-// of ancestor blocks, 0 = two while two CTAs per SM still fit
+// rows: observation rows per chunk (32, or 64 in FP32; 16: the streaming
+// kernel for deep trees, stages ignored); stages: 1 or 2 stages of ancestor
+// blocks, 0 = two while two CTAs per SM still fit
 template <typename T, int RP>
 int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int rows, int stages,
                      int B, void *stream)
 {
     if (nchunks == 0) return 0;
+    if (rows == kStreamRows) {
+        static size_t done = 0;
+        const size_t sm = smem_leafbasis_stream_bytes<T, RP, kStreamRows, kStreamBlocks>(t.M);
+        if (int e = set_smem(k_leafbasis_stream<T, RP, kStreamRows, kStreamBlocks>, sm, &done)) return e;
+        dim3 grid((unsigned)nchunks, (unsigned)B);
+        k_leafbasis_stream<T, RP, kStreamRows, kStreamBlocks><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, chunks);
+        return (int)cudaGetLastError();
+    }
     if constexpr (sizeof(T) == 4)
         if (rows == 64) return launch_leafbasis_ch<T, RP, 64>(t, w, chunks, nchunks, stages, B, stream);
     return launch_leafbasis_ch<T, RP, 32>(t, w, chunks, nchunks, stages, B, stream);

@@ -173,6 +173,12 @@ def test_parity_deep_binary_trees_r49(n, M, seed):
     err = _parity(x, y, z, M, 2, 49, th, precisions=("mixed",), build_precision="mixed")
     print("deep r=49 M=%d |dl|/n" % M, float(err["mixed"].max()))
     with mra.MRA(x, y, z, M, 2, 49, precision="mixed") as g:
+        # the default leaf basis of this depth streams its ancestor blocks; the
+        # 32-row kernel (one CTA per SM here) gives the same U bit for bit
+        ll = g.loglik(th)
+        g.set_launch(32, 1, 0, True)
+        assert np.array_equal(g.loglik(th), ll)
+        g.set_launch(0, 0, 0, True)
         with pytest.raises(mra.MRAError) as e:
             g.set_precision("fp64")
         assert e.value.status == mra.EINVAL
@@ -303,9 +309,11 @@ def test_launch_configurations_agree_bit_for_bit(precision):
         s = g.stats()
         assert s["max_leaf"] > 64
         ref = g.loglik(THETAS)
-        rows = (32, 64) if precision == "mixed" else (32,)
+        # 16 rows: the streaming kernel of deep trees (ancestor blocks staged two
+        # at a time; stages do not apply)
+        rows = (16, 32, 64) if precision == "mixed" else (16, 32)
         for r in rows:
-            for stages in (1, 2):
+            for stages in ((1,) if r == 16 else (1, 2)):
                 for bset in (0, 1):
                     for conc in (True, False):
                         for queue in (False, True):
