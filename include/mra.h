@@ -156,7 +156,9 @@ mra_status mra_loglik_device(mra_ctx *ctx, const double *theta_dev, int batch, d
  * it).  out (may be NULL) receives the choice and the times.
  */
 typedef struct {
-    int leafbasis_rows;   /* 32 or 64 */
+    int leafbasis_rows;   /* 32 or 64 (FP32 only); 16: the streaming kernel of deep trees (ancestor blocks
+                             staged two at a time, the same results bit for bit), the default where 32-row
+                             chunks leave room for one CTA per SM */
     int leafbasis_stages; /* 1 or 2 */
     int bucket_set;       /* 0: {<=32, <=48, <=64}, 1: {<=32, <=64} */
     int concurrent;       /* 1: leaf-posterior buckets on side streams */
