@@ -1,10 +1,9 @@
 // tc_sm100.cuh -- inline-PTX wrappers for the 5th-generation tensor cores of
 // sm_100-family GPUs (tcgen05: tensor memory, MMA issued by one thread,
-// asynchronous completion through an mbarrier) as the tensor-core leaf Gram
-// and leaf basis use them: TMEM allocation, the kind::tf32 and kind::f16
-// MMAs with operands in shared memory (no-swizzle, K-major core-matrix
-// layout), commit to an mbarrier, bounded mbarrier waits, 32-lane TMEM loads,
-// and bulk global-to-shared copies that complete on an mbarrier.
+// asynchronous completion through an mbarrier) as the leaf Gram kernel uses
+// them.  Only what that kernel needs: TMEM allocation, the kind::tf32 MMA
+// with operands in shared memory (no-swizzle, K-major core-matrix layout),
+// commit to an mbarrier, bounded mbarrier waits and 32-lane TMEM loads.
 //
 // Shared-memory operand layout (no swizzle, K-major): the operand is split
 // into "core matrices" of 8 rows (M or N) x 16 bytes (4 TF32 or 8 BF16 values
