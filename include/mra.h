@@ -84,6 +84,9 @@ typedef struct {
                                    prior, leafbasis, leafpost, leafpost_big, leafgram, up, root */
     int device_levels;          /* levels the kernels run: M, or 2 (M - 1) + 1 when r_hat > 32
                                    (each non-leaf level enters its knots in two halves) */
+    int subtree_level;          /* 0, or the device level S below which the leaf Gram and the upward
+                                   pass run subtree by subtree (mra_tune_t.subtree_level) */
+    int subtree_chunks;         /* chunks of level-S subtrees one pass runs (0 when not streamed) */
 } mra_stats_t;
 
 typedef struct {
@@ -180,13 +183,21 @@ typedef struct {
                                    tensor memory, 128 rows per CTA); trees with (M - 2) x padded r_hat up to 192
                                    (EINVAL beyond).  It differs from the CUDA-core kernel in the last bits, so
                                    the autotuner reports it but does not switch it. */
+    int subtree_level;    /* 0 (default): chosen by the memory plan.  S in 1 .. device levels - 2: the leaf
+                             Gram and the upward pass of device levels M-1 .. S run chunk by chunk of
+                             level-S subtrees (regions contiguous at every level), so that the per-theta
+                             ATilde arrays of those levels hold one chunk instead of the whole level; levels
+                             S-1 .. 1 then run whole.  The plan streams subtrees by itself where one
+                             theta's scratch would not fit the budget otherwise (deep trees: ATilde grows
+                             with the number of regions, not with n).  The same results bit for bit. */
+    int subtree_chunk;    /* level-S regions per chunk; 0: the largest that fits the budget */
 } mra_tune_t;
 
 mra_status mra_autotune(mra_ctx *ctx, const double *theta, int reps, mra_tune_t *out);
 
 /* Set the launch configuration directly (the four configuration fields of
- * cfg, gram_tensor_cores, leaf_queue, prior_stages and leafbasis_tensor_cores;
- * the times are ignored).  leafbasis_rows 0 and
+ * cfg, gram_tensor_cores, leaf_queue, prior_stages, leafbasis_tensor_cores,
+ * subtree_level and subtree_chunk; the times are ignored).  leafbasis_rows 0 and
  * leafbasis_stages 0 select the defaults; EINVAL for a value outside the
  * candidates or one whose shared memory does not fit. */
 mra_status mra_set_launch(mra_ctx *ctx, const mra_tune_t *cfg);

@@ -377,6 +377,10 @@ struct mra_ctx {
     int user_max_batch = 0;
     size_t hbm_budget = 0;   // from the options (0 = 60% of free HBM)
     int ain_chunk = 0;       // level M-1 regions per Ain chunk (0 = the whole level)
+    // subtree streaming: levels below device level sub_level run chunk by
+    // chunk of sub_chunk level-sub_level subtrees (0 = off); sub_req_* force
+    // it (mra_set_launch), 0 = chosen by the memory plan
+    int sub_level = 0, sub_chunk = 0, sub_req_level = 0, sub_req_chunk = 0;
     int status_cap = 0;      // theta the status array holds
     // captured device passes, replayed when the same pass comes again
     struct GraphEntry {
@@ -485,8 +489,17 @@ Plan make_plan(const mra_ctx *c)
     p.leafw = (size_t)P.nleaf() * (size_t)(M - 1) * RP;
     p.leafdu = 2 * (size_t)P.nleaf();
     p.V = (size_t)c->vbig_elems;
+    // regions of level m the per-theta arrays hold: the whole level, or under
+    // subtree streaming the descendants of sub_chunk level-S regions below S
+    const int S = c->sub_level;
+    auto held = [&](int m) {
+        const size_t nr = (size_t)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]);
+        if (S <= 0 || m <= S) return nr;
+        const size_t nS = (size_t)(P.lvl_off[(size_t)S + 1] - P.lvl_off[(size_t)S]);
+        return std::min(nS, (size_t)c->sub_chunk) * (nr / nS);
+    };
     if (M >= 2) {
-        size_t nP = (size_t)(P.lvl_off[(size_t)M] - P.lvl_off[(size_t)M - 1]);
+        size_t nP = held(M - 1);
         if (c->ain_chunk > 0) nP = std::min(nP, (size_t)c->ain_chunk);
         p.Ain = nP * (size_t)(M - 1) * M / 2 * B2;
         p.Ainw = nP * (size_t)(M - 1) * RP;
@@ -504,7 +517,7 @@ Plan make_plan(const mra_ctx *c)
             p.lbB = acc_b;
         }
         for (int m = 2; m <= M - 1; m++) {
-            const size_t nr = (size_t)(P.lvl_off[(size_t)m + 1] - P.lvl_off[(size_t)m]);
+            const size_t nr = held(m);
             p.Atil[m] = nr * (size_t)(m - 1) * m / 2 * B2;
             p.Atilw[m] = nr * (size_t)(m - 1) * RP;
             p.Atildu[m] = 2 * nr;
@@ -579,6 +592,7 @@ Work<T> make_work(const mra_ctx *c, const Plan &p, int B)
         w.Atildu_stride[m] = p.Atildu[m];
     }
     w.status = c->d_status;
+    w.sub_level = c->sub_level;
     return w;
 }
 
@@ -772,7 +786,32 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
         cudaEventRecord(c->join_ev[a], c->aux[a]);
         cudaStreamWaitEvent(s, c->join_ev[a], 0);
     }
-    if (M > 1) {
+    if (M > 1 && c->sub_level > 0) {
+        // subtree streaming: the Gram and the upward pass of levels M-1 .. S
+        // chunk by chunk of level-S subtrees (contiguous at every level), into
+        // arrays that hold one chunk; then levels S-1 .. 1 whole
+        const int S = c->sub_level;
+        auto nreg = [&](int m) { return c->G.lvl_off[(size_t)m + 1] - c->G.lvl_off[(size_t)m]; };
+        const int64_t nS = nreg(S);
+        const bool tc = sizeof(T) == 4 && c->gram_tc;
+        for (int64_t q0 = 0; q0 < nS; q0 += c->sub_chunk) {
+            const int64_t q = std::min<int64_t>(c->sub_chunk, nS - q0);
+            const int64_t dP = nreg(M - 1) / nS;
+            const int p0 = (int)(q0 * dP), cnt = (int)(q * dP);
+            if (tc && (e = timed_launch(c, K_LEAFGRAM, s, [&] { return launch_gram_colexp<T, RP>(t, w, p0, cnt, B, s); })))
+                return e;
+            if ((e = timed_launch(c, K_LEAFGRAM, s, [&] { return launch_leafgram<T, RP>(t, w, p0, cnt, B, tc, s); })))
+                return e;
+            for (int m = M - 1; m >= S; m--) {
+                const int64_t d = nreg(m) / nS;
+                if ((e = timed_launch(c, K_UP, s,
+                                      [&] { return launch_up<T, RP>(t, w, m, (int)(q0 * d), (int)(q * d), B, s); })))
+                    return e;
+            }
+        }
+        for (int m = S - 1; m >= 1; m--)
+            if ((e = timed_launch(c, K_UP, s, [&] { return launch_up<T, RP>(t, w, m, 0, -1, B, s); }))) return e;
+    } else if (M > 1) {
         const int nP = (int)(c->G.lvl_off[(size_t)M] - c->G.lvl_off[(size_t)M - 1]);
         const int chunk = c->ain_chunk > 0 ? c->ain_chunk : nP;
         for (int p0 = 0; p0 < nP; p0 += chunk) {
@@ -816,7 +855,7 @@ size_t smem_need(int M, int nmax)
     }
     upd(smem_big<T, RP>(M));
     upd(smem_leafgram<T, RP>(M));
-    upd(smem_leafbasis_cfg<T, RP>(M, 32, 1));
+    upd(std::min(smem_leafbasis_cfg<T, RP>(M, 32, 1), smem_leafbasis_cfg<T, RP>(M, kStreamRows, 1)));
     upd(smem_leafpost_small<T, RP>(M, 32));
     if (nmax > 0) upd(smem_leafpost_small<T, RP>(M, nmax));
     return mx;
@@ -957,10 +996,68 @@ int max_batch_for(mra_ctx *c, size_t budget)
         budget = (size_t)(0.6 * (double)(fr + c->scratch_bytes));
     }
     c->ain_chunk = 0;
+    c->sub_level = 0;
+    c->sub_chunk = 0;
+    const int M = c->G.M;
+    auto nreg = [&](int m) { return c->G.lvl_off[(size_t)m + 1] - c->G.lvl_off[(size_t)m]; };
+    // bytes of one theta's scratch with subtree streaming below level S in
+    // chunks of q level-S subtrees
+    auto sub_bytes = [&](int S, int64_t q) {
+        c->sub_level = S;
+        c->sub_chunk = (int)q;
+        const size_t v = scratch_bytes_for(make_plan(c), c, 1) + 4096;
+        c->sub_level = 0;
+        c->sub_chunk = 0;
+        return v;
+    };
+    if (c->sub_req_level > 0 && M >= 3) {
+        // forced (mra_set_launch): the requested level, the requested chunk or
+        // the largest that fits the budget
+        const int S = std::min(c->sub_req_level, M - 2);
+        int64_t q = c->sub_req_chunk;
+        if (q <= 0) {
+            const size_t b1 = sub_bytes(S, 1), b2 = sub_bytes(S, 2);
+            const size_t per_sub = b2 > b1 ? b2 - b1 : 1;
+            q = budget > b1 ? 1 + (int64_t)((budget - b1) / per_sub) : 1;
+        }
+        c->sub_level = S;
+        c->sub_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(q, nreg(S)));
+    }
     Plan p = make_plan(c);
     size_t per = scratch_bytes_for(p, c, 1) + 4096;
-    const int M = c->G.M;
-    if (per > budget && M >= 2 && p.Ain > 0) {
+    if (per > budget && M >= 3 && c->sub_level == 0) {
+        // Where even one region's Ain leaves the scratch over the budget (the
+        // ATilde arrays of deep trees grow with the tree, not with n), stream
+        // subtrees: the level S whose chunks of the largest fitting size are
+        // fewest, the deepest of those (fewer levels run chunked).
+        c->ain_chunk = 1;
+        const size_t ain1 = scratch_bytes_for(make_plan(c), c, 1) + 4096;
+        c->ain_chunk = 0;
+        if (ain1 > budget) {
+            int bestS = 0;
+            int64_t bestq = 0, bestn = 0;
+            for (int S = M - 2; S >= 1; S--) {
+                const size_t b1 = sub_bytes(S, 1);
+                if (b1 > budget) continue;
+                const size_t b2 = nreg(S) > 1 ? sub_bytes(S, 2) : b1 + 1;
+                const size_t per_sub = b2 > b1 ? b2 - b1 : 1;
+                const int64_t q = std::min<int64_t>(nreg(S), 1 + (int64_t)((budget - b1) / per_sub));
+                const int64_t nch = (nreg(S) + q - 1) / q;
+                if (bestS == 0 || nch < bestn) {
+                    bestS = S;
+                    bestq = q;
+                    bestn = nch;
+                }
+            }
+            if (bestS > 0) {
+                c->sub_level = bestS;
+                c->sub_chunk = (int)bestq;
+                p = make_plan(c);
+                per = scratch_bytes_for(p, c, 1) + 4096;
+            }
+        }
+    }
+    if (per > budget && M >= 2 && p.Ain > 0 && c->sub_level == 0) {
         const int64_t nP = c->G.lvl_off[(size_t)M] - c->G.lvl_off[(size_t)M - 1];
         const size_t full_ain = scratch_bytes_for(p, c, 1);
         c->ain_chunk = 1;
@@ -1694,6 +1791,8 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         out->leafbasis_tensor_cores = c->lb_tc ? 1 : 0;
         out->leaf_queue = bestc.queue ? 1 : 0;
         out->prior_stages = bestc.prior;
+        out->subtree_level = c->sub_req_level;
+        out->subtree_chunk = c->sub_req_chunk;
         out->ms_default = first;
         out->ms_best = best;
         out->tried = tried;
@@ -1711,6 +1810,10 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
         g->bucket_set > 1 || (g->bucket_set == 1 && c->nmax_small < 64) || g->prior_stages < 0 ||
         g->prior_stages > 2) {
         c->err = "launch configuration outside the candidates";
+        return MRA_EINVAL;
+    }
+    if (g->subtree_level < 0 || g->subtree_chunk < 0 || (g->subtree_level > 0 && g->subtree_level > c->G.M - 2)) {
+        c->err = "subtree_level must be 0 (chosen by the memory plan) or a device level in 1 .. device levels - 2";
         return MRA_EINVAL;
     }
     if (g->leafbasis_tensor_cores && (c->G.M - 2) * c->RP > kLeafBasisTcMaxK) {
@@ -1734,10 +1837,14 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
     c->bucket_set = g->bucket_set;
     c->concurrent = g->concurrent != 0;
     c->gram_tc = g->gram_tensor_cores != 0;
-    if ((g->leafbasis_tensor_cores != 0) != c->lb_tc) {
+    const bool sub_change = g->subtree_level != c->sub_req_level || g->subtree_chunk != c->sub_req_chunk;
+    c->sub_req_level = g->subtree_level;
+    c->sub_req_chunk = g->subtree_level > 0 ? g->subtree_chunk : 0;
+    if ((g->leafbasis_tensor_cores != 0) != c->lb_tc || sub_change) {
         c->lb_tc = g->leafbasis_tensor_cores != 0;
         if (c->d_sx) {
-            // the slice buffers join or leave the per-theta scratch
+            // the slice buffers join or leave the per-theta scratch, or its
+            // chunk-local arrays change size
             const int mb = max_batch_for(c, c->hbm_budget);
             c->max_cap = c->user_max_batch > 0 ? std::min(c->user_max_batch, 1024) : mb;
             c->cap = 0;
@@ -1974,6 +2081,12 @@ mra_status mra_stats(const mra_ctx *c, mra_stats_t *o)
     o->launches_per_pass = c->launches_last;
     for (int k = 0; k < 8; k++) o->flops_by_kernel[k] = c->flops_k[k];
     o->device_levels = c->G.M;
+    o->subtree_level = c->sub_level;
+    o->subtree_chunks = 0;
+    if (c->sub_level > 0 && c->sub_chunk > 0) {
+        const int64_t nS = c->G.lvl_off[(size_t)c->sub_level + 1] - c->G.lvl_off[(size_t)c->sub_level];
+        o->subtree_chunks = (int)((nS + c->sub_chunk - 1) / c->sub_chunk);
+    }
     return MRA_OK;
 }
 

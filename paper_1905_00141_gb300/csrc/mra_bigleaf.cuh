@@ -68,20 +68,30 @@ __host__ __device__ constexpr size_t smem_big_assemble_bytes(int M)
     return (size_t)2 * TB * ((M - 1) * RP + 4) * sizeof(T) + (size_t)4 * TB * 8 + 64;
 }
 
+// Deep trees (mixed modes): the U rows of the two tiles in KP column parts.
+template <typename T, int RP, int KP>
+__host__ __device__ constexpr size_t smem_big_assemble_parts_bytes(int M)
+{
+    return (size_t)2 * TB * ((M - 1) * RP / KP + 4) * sizeof(T) + (size_t)4 * TB * 8 + 64;
+}
+
 // V tile (I, J), I >= J, of a large leaf: C(S_I, S_J) - U_I U_J' (+ tau2 on
 // the diagonal), lower part only for I == J.  U U' is the exact float-float
 // product sum: large leaves are the dense clusters, where C and U U' agree
 // to many digits.
-template <typename T, int RP>
+// KP > 1 (FP32 storage only): the rows are read and summed in KP column
+// parts, the grid accumulation carried from part to part (the same sums).
+template <typename T, int RP, int KP = 1>
 __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const BigLeaf *leaves, const BigTile *items)
 {
     using F = typename FacT<T>::type;
+    static_assert(KP == 1 || sizeof(T) == 4, "column parts: FP32 storage only");
     const BigTile it = items[blockIdx.x];
     const int b = blockIdx.y, tid = threadIdx.x;
     const double *th = w.theta + 3 * b;
     if (!theta_ok(th)) return;
     const BigView<F> v = big_view(t, w, leaves[it.bl], b);
-    const int M = t.M, n = v.n, UC = (M - 1) * RP, LDU = UC + 4;
+    const int M = t.M, n = v.n, UC = (M - 1) * RP, KC = UC / KP, LDU = KC + 4;
     const int rI = it.i * TB, rJ = it.j * TB;
     const int nI = min(TB, n - rI), nJ = min(TB, n - rJ);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -89,7 +99,7 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
     T *sUJ = sUI + (size_t)TB * LDU;
     double *sc = (double *)(sUJ + (size_t)TB * LDU); // x_I, y_I, x_J, y_J relative to the parent corner
     const T *Ub = w.U + (size_t)b * w.U_stride + (size_t)v.o0 * UC;
-    {
+    if (KP == 1) {
         const int cpr = UC * (int)sizeof(T) / 16;
         for (int e = tid; e < nI * cpr; e += NT) {
             const int a = e / cpr, q = e % cpr;
@@ -120,13 +130,49 @@ __global__ void __launch_bounds__(NT) k_big_assemble(DevTree t, Work<T> w, const
     __shared__ ff s_par[3]; // sigma2, 1/beta, tau2 as float pairs
     set_cov_params<T>(th, &s_ib, s_par);
     if (tid == 2) s_par[2] = ff_from_double(th[2]);
-    cp_async_wait<0>();
-    __syncthreads();
-    const double tau2 = th[2], ib64 = s_ib;
     const int a0 = 2 * (tid / (TB / 2)), q0 = 2 * (tid % (TB / 2));
     T hi[2][2], lo[2][2];
-    dot2x2_exact(sUI + a0 * LDU, sUI + min(a0 + 1, TB - 1) * LDU, sUJ + q0 * LDU, sUJ + min(q0 + 1, TB - 1) * LDU, UC,
-                 grid_constant(th[0]), hi, lo);
+    if constexpr (KP == 1) {
+        cp_async_wait<0>();
+        __syncthreads();
+        dot2x2_exact(sUI + a0 * LDU, sUI + min(a0 + 1, TB - 1) * LDU, sUJ + q0 * LDU, sUJ + min(q0 + 1, TB - 1) * LDU,
+                     UC, grid_constant(th[0]), hi, lo);
+    } else {
+        const float Cq = grid_constant(th[0]);
+        grid_acc g[2][2];
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) grid_init(g[i][j], Cq);
+        const int cpr = KC * (int)sizeof(T) / 16;
+        for (int p = 0; p < KP; p++) {
+            for (int e = tid; e < nI * cpr; e += NT) {
+                const int a = e / cpr, q = e % cpr;
+                cp_async16((char *)(sUI + (size_t)a * LDU) + 16 * q,
+                           (const char *)(Ub + (size_t)(rI + a) * UC + (size_t)p * KC) + 16 * q);
+            }
+            for (int e = tid; e < nJ * cpr; e += NT) {
+                const int a = e / cpr, q = e % cpr;
+                cp_async16((char *)(sUJ + (size_t)a * LDU) + 16 * q,
+                           (const char *)(Ub + (size_t)(rJ + a) * UC + (size_t)p * KC) + 16 * q);
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+            dot2x2_grid_add(g, sUI + a0 * LDU, sUI + min(a0 + 1, TB - 1) * LDU, sUJ + q0 * LDU,
+                            sUJ + min(q0 + 1, TB - 1) * LDU, KC);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const ff gv = grid_value(g[i][j], Cq);
+                hi[i][j] = gv.hi;
+                lo[i][j] = gv.lo;
+            }
+    }
+    const double tau2 = th[2], ib64 = s_ib; // after the barriers above (s_ib)
     const ff s2f = s_par[0], ibf = s_par[1], tau2f = s_par[2];
 #pragma unroll
     for (int i = 0; i < 2; i++)

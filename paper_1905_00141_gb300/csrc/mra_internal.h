@@ -101,6 +101,10 @@ struct Work {
     double *Atil_du[MRA_MAXM + 1];
     size_t Atil_stride[MRA_MAXM + 1], Atilw_stride[MRA_MAXM + 1], Atildu_stride[MRA_MAXM + 1];
     int exact_rem;  // FP32 storage: remainder recursions with float-pair covariance and exact products
+    // subtree streaming (0: off): levels m > sub_level run chunk by chunk of
+    // level-sub_level subtrees, and their Atil arrays (and Ain) hold only the
+    // current chunk's regions, indexed from the chunk's first region
+    int sub_level;
     double *reg_du; // [nreg][2] or null
     double *reg_lw; // [n_nonleaf] or null
     size_t regdu_stride, reglw_stride;
@@ -186,6 +190,13 @@ inline int64_t big_leaf_scratch(int64_t n) { return n * n + 2 * n + 2; }
 // The streaming leaf basis of deep trees: rows per chunk and ancestor blocks
 // staged at a time (mra_tune_t.leafbasis_rows = 16 selects it).
 constexpr int kStreamRows = 16, kStreamBlocks = 2;
+
+// Deep levels whose shared-memory footprint exceeds one CTA's: the prior
+// stages its ancestor's blocks kPriorStreamBlocks at a time, the upward pass
+// the right-hand blocks of its solve kUpStreamBlocks at a time, and the
+// large-leaf assembly reads its U rows in kBigAssembleParts column parts.
+// Each sums the same terms in the same order as the whole-staged kernel.
+constexpr int kPriorStreamBlocks = 4, kUpStreamBlocks = 4, kBigAssembleParts = 2;
 
 // Observation rows per leaf-basis chunk: 64 in FP32, 32 in FP64 (shared memory).
 template <typename T> __host__ __device__ constexpr int chunk_rows() { return sizeof(T) == 4 ? 64 : 32; }

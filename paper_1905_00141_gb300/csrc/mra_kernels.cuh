@@ -437,6 +437,24 @@ __device__ __forceinline__ void dot2x2(const double *a0, const double *a1, const
             lo[i][j] = 0.0;
         }
 }
+// The grid accumulation of dot2x2_exact over K terms without its start and
+// its rounding (large leaves of deep trees read their rows in parts).
+__device__ __forceinline__ void dot2x2_grid_add(grid_acc (&g)[2][2], const float *a0, const float *a1, const float *q0,
+                                                const float *q1, int K)
+{
+    for (int k = 0; k < K; k += 4) {
+        const float4 x4[2] = {*(const float4 *)(a0 + k), *(const float4 *)(a1 + k)};
+        const float4 y4[2] = {*(const float4 *)(q0 + k), *(const float4 *)(q1 + k)};
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const float x[2] = {(&x4[0].x)[e], (&x4[1].x)[e]}, y[2] = {(&y4[0].x)[e], (&y4[1].x)[e]};
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 2; j++) grid_add(g[i][j], x[i], y[j]);
+        }
+    }
+}
 __device__ __forceinline__ void dot2x2_exact(const double *a0, const double *a1, const double *q0, const double *q1,
                                              int K, float, double (&hi)[2][2], double (&lo)[2][2])
 {
@@ -1078,7 +1096,18 @@ __host__ __device__ constexpr int prior_stages(int m)
     return smem_prior_bytes<T, RP>(m, 2) <= kSmemMax ? 2 : 1;
 }
 
-template <typename T, int RP>
+// Deep levels (one stage of the ancestor's blocks does not fit beside the
+// region's own): k_prior<T, RP, KB> stages them KB at a time.  Each output
+// sums the same terms in the same order, so the two give the same blocks and
+// factors bit for bit.
+template <typename T, int RP, int KB>
+__host__ __device__ constexpr size_t smem_prior_stream_bytes(int m)
+{
+    return (size_t)RP * (RP + 1) * 8 + (RP + 2) * 8 + 8 * 8 + chol_scratch_bytes<T, RP>() + 64 +
+           4 * RP * sizeof(T) + (size_t)((m - 1) + KB + 1) * RP * RP * sizeof(T) + RP * sizeof(T) + 64;
+}
+
+template <typename T, int RP, int KB = 0>
 __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m, int stages)
 {
     using TL = Tile<RP, RP>;
@@ -1101,7 +1130,8 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m, int s
     T *sa = sq + 2 * RP;                    // ancestor knots: 2 RP
     T *sU = sa + 2 * RP;                    // (m-1) blocks k-major [t][row]
     T *sB0 = sU + (size_t)(m - 1) * RP * RP; // `stages` stages of up to m-1 ancestor blocks (column-major)
-    T *sW = sB0 + (size_t)stages * (m > 1 ? m - 1 : 1) * RP * RP; // RP x RP k-major
+    // RP x RP k-major (KB > 0: after KB staged blocks)
+    T *sW = sB0 + (KB > 0 ? (size_t)KB * RP * RP : (size_t)stages * (m > 1 ? m - 1 : 1) * RP * RP);
 
     const int Rm = t.Rl[m]; // own knots
     const int64_t g = t.lvl_off[m] + i;
@@ -1119,8 +1149,90 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m, int s
         copy_g2s_async(slot(l), pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP, l * RP * RP);
         cp_async_commit();
     };
-    if (m > 1 && stages == 2) fetch(1);
+    if (KB == 0 && m > 1 && stages == 2) fetch(1);
     for (int l = 1; l < m; l++) {
+      if constexpr (KB > 0) {
+        // the ancestor's blocks KB at a time through sB0: What^1..What^{l-1}
+        // against the region's own, then its Linv
+        const int64_t ia = anc_index(t, i, m, l);
+        const int64_t ga = t.lvl_off[l] + ia;
+        const int Ra = t.Rl[l];
+        const T *anc = pb + w.prior_lvl[l] + (size_t)ia * l * RP * RP;
+        if (tid < RP) {
+            const double ox = t.cx[ga], oy = t.cy[ga];
+            sq[tid] = (T)(t.kx[g * RP + tid] - ox);
+            sq[RP + tid] = (T)(t.ky[g * RP + tid] - oy);
+            sa[tid] = (T)(t.kx[ga * RP + tid] - ox);
+            sa[RP + tid] = (T)(t.ky[ga * RP + tid] - oy);
+        }
+        T acc[TL::RT][TL::CT];
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (w.exact_rem) {
+                grid_acc ga4[TL::RT][TL::CT];
+#pragma unroll
+                for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                    for (int c = 0; c < TL::CT; c++) grid_init(ga4[r][c], s_cq);
+                for (int k0 = 0; k0 < l - 1; k0 += KB) {
+                    const int nb = min(KB, l - 1 - k0);
+                    copy_g2s_async(sB0, anc + (size_t)k0 * RP * RP, nb * RP * RP);
+                    cp_async_commit();
+                    cp_async_wait<0>();
+                    __syncthreads();
+                    tile_grid_add<RP, RP>(ga4, sU + (size_t)k0 * RP * RP, RP, sB0, RP, nb * RP);
+                    __syncthreads();
+                }
+                __syncthreads(); // sq and sa before the covariance
+#pragma unroll
+                for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                    for (int c = 0; c < TL::CT; c++) {
+                        const int a = r0 + r, j = c0 + c;
+                        ff cv = ff{0.f, 0.f};
+                        if (a < Rm && j < Ra) cv = ff_cov_exp(s_par[0], s_par[1], sq[a], sq[RP + a], sa[j], sa[RP + j]);
+                        const ff fa = grid_value(ga4[r][c], s_cq);
+                        sW[(c0 + c) * RP + r0 + r] = FADD(FSUB(cv.hi, fa.hi), FSUB(cv.lo, fa.lo));
+                    }
+                done = true;
+            }
+        }
+        if (!done) {
+            tile_zero(acc);
+            for (int k0 = 0; k0 < l - 1; k0 += KB) {
+                const int nb = min(KB, l - 1 - k0);
+                copy_g2s_async(sB0, anc + (size_t)k0 * RP * RP, nb * RP * RP);
+                cp_async_commit();
+                cp_async_wait<0>();
+                __syncthreads();
+                tile_fma<T, RP, RP>(acc, sU + (size_t)k0 * RP * RP, RP, sB0, RP, nb * RP);
+                __syncthreads();
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                for (int c = 0; c < TL::CT; c++) {
+                    const int a = r0 + r, j = c0 + c;
+                    const T cv = (a < Rm && j < Ra) ? cov_d(CovP<T>(th[0], s_ib), sq[a] - sa[j], sq[RP + a] - sa[RP + j]) : T(0);
+                    sW[j * RP + a] = cv - acc[r][c];
+                }
+        }
+        // What^l = W Linv' with the ancestor's Linv (its last block)
+        __syncthreads();
+        copy_g2s_async(sB0, anc + (size_t)(l - 1) * RP * RP, RP * RP);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        tile_zero(acc);
+        tile_fma<T, RP, RP>(acc, sW, RP, sB0, RP, RP);
+        T *outl = sU + (size_t)(l - 1) * RP * RP;
+#pragma unroll
+        for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+            for (int c = 0; c < TL::CT; c++) outl[(c0 + c) * RP + r0 + r] = acc[r][c];
+        __syncthreads();
+      } else {
         const int64_t ia = anc_index(t, i, m, l);
         const int64_t ga = t.lvl_off[l] + ia;
         const int Ra = t.Rl[l]; // the ancestor's knots
@@ -1175,6 +1287,7 @@ __global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m, int s
 #pragma unroll
             for (int c = 0; c < TL::CT; c++) out[(c0 + c) * RP + r0 + r] = acc[r][c];
         __syncthreads();
+      }
     }
     // self block W^m = C(Q,Q) - sum_k What^k What^k' (identity on the padding)
     if (tid < RP) {
@@ -1949,7 +2062,19 @@ __host__ __device__ constexpr size_t smem_up_bytes(int m)
            (size_t)4 * RP * sizeof(T) + 64;
 }
 
-template <typename T, int RP>
+// Deep levels (the m blocks of column m and the m - 1 of Z exceed one CTA's
+// shared memory): k_up<T, RP, KB> keeps A^{m,m} and stages the right-hand
+// blocks of the solve KB at a time; every column of Z is solved by the same
+// operations as with all blocks staged.
+template <typename T, int RP, int KB>
+__host__ __device__ constexpr size_t smem_up_stream_bytes(int m)
+{
+    return (size_t)RP * (RP + 1) * 8 + (size_t)(m * RP) * 8 + (size_t)(RP + RP + 2 + 8) * 8 +
+           chol_scratch_bytes<T, RP>() + 64 + (size_t)(KB + 1 + m - 1) * RP * RP * sizeof(T) +
+           (size_t)4 * RP * sizeof(T) + 64;
+}
+
+template <typename T, int RP, int KB = 0>
 __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0)
 {
     using TL = Tile<RP, RP>;
@@ -1977,8 +2102,11 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
     double *red = (double *)(srs + RP + 2);      // 8
     F *sr2 = (F *)(red + 8);                     // RP + 1 (FP64 only)
     int *flag = (int *)((unsigned char *)sr2 + chol_scratch_bytes<T, RP>());
-    T *sC = (T *)(flag + 16);                    // m blocks A^{k,m}, row-major
-    T *sZ = sC + (size_t)m * B2;                 // RP x ((m-1) RP + 4)
+    T *sC = (T *)(flag + 16);                    // m blocks A^{k,m}, row-major (KB > 0: A^{m,m}, then KB staged)
+    T *sZ = sC + (size_t)(KB > 0 ? KB + 1 : m) * B2; // RP x ((m-1) RP + 4)
+    // subtree streaming: levels below sub_level keep only the chunk's regions
+    const bool loc_out = w.sub_level > 0 && m > w.sub_level, loc_in = w.sub_level > 0 && m >= w.sub_level;
+    const int64_t io = loc_out ? (int64_t)il : (int64_t)i, ic = loc_in ? (int64_t)il : (int64_t)i;
     const T *blk[4];
     const double *wv[4], *dus[4];
     for (int s = 0; s < nsrc; s++) {
@@ -1987,7 +2115,7 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
             wv[s] = w.Ain_w + (size_t)b * w.Ainw_stride + (size_t)il * m * RP;
             dus[s] = w.Ain_du + (size_t)b * w.Aindu_stride + 2 * (size_t)il;
         } else {
-            const int64_t ch = (int64_t)i * J + s;
+            const int64_t ch = ic * J + s;
             blk[s] = w.Atil[m + 1] + (size_t)b * w.Atil_stride[m + 1] + (size_t)ch * np * B2;
             wv[s] = w.Atil_w[m + 1] + (size_t)b * w.Atilw_stride[m + 1] + (size_t)ch * m * RP;
             dus[s] = w.Atil_du[m + 1] + (size_t)b * w.Atildu_stride[m + 1] + 2 * (size_t)ch;
@@ -1995,15 +2123,18 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
     }
     if (tid == 0) flag[0] = 0;
     // column m: A^{k,m}, k = 1..m, contiguous blocks pidx(1,m) .. pidx(m,m)
+    // (KB > 0: only A^{m,m} here, the others staged for the solve)
     const size_t c0off = (size_t)pidx(1, m) * B2;
+    const int nfirst = KB > 0 ? 1 : m;
+    const size_t f0off = c0off + (size_t)(m - nfirst) * B2;
     if (direct) {
-        copy_g2s_async(sC, blk[0] + c0off, m * B2);
+        copy_g2s_async(sC, blk[0] + f0off, nfirst * B2);
         cp_async_commit();
     } else {
 #pragma unroll 4
-        for (int e = tid; e < m * B2; e += NT) {
-            T v = blk[0][c0off + e];
-            for (int s = 1; s < nsrc; s++) v += blk[s][c0off + e];
+        for (int e = tid; e < nfirst * B2; e += NT) {
+            T v = blk[0][f0off + e];
+            for (int s = 1; s < nsrc; s++) v += blk[s][f0off + e];
             sC[e] = v;
         }
     }
@@ -2019,7 +2150,7 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
     }
     if (direct) cp_async_wait<0>();
     __syncthreads();
-    const T *Cm = sC + (size_t)(m - 1) * B2;
+    const T *Cm = sC + (size_t)(nfirst - 1) * B2;
     for (int e = tid; e < B2; e += NT) {
         const int a = e / RP, c = e % RP;
         if (c <= a) {
@@ -2038,7 +2169,28 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
     // right-hand column (k, bc) is A^{m,k}[.][bc] = A^{k,m}[bc][.], contiguous in sC
     const int ncol = (m - 1) * RP, ldz = ncol + 4;
     for (int a = tid; a < RP; a += NT) sz[a] = f_of<F>(sw[(m - 1) * RP + a]);
-    fwd_solve_warp<T, RP>(sL, RP + 1, srs, sC, RP, 1, sZ, ldz, ncol);
+    if constexpr (KB > 0) {
+        T *stg = sC + B2;
+        for (int k0 = 0; k0 < m - 1; k0 += KB) {
+            const int nb = min(KB, m - 1 - k0);
+            const size_t off = c0off + (size_t)k0 * B2;
+            if (direct) {
+                copy_g2s_async(stg, blk[0] + off, nb * B2);
+                cp_async_commit();
+                cp_async_wait<0>();
+            } else {
+                for (int e = tid; e < nb * B2; e += NT) {
+                    T v = blk[0][off + e];
+                    for (int s = 1; s < nsrc; s++) v += blk[s][off + e];
+                    stg[e] = v;
+                }
+            }
+            __syncthreads();
+            fwd_solve_warp<T, RP>(sL, RP + 1, srs, stg, RP, 1, sZ + (size_t)k0 * RP, ldz, nb * RP);
+        }
+    } else {
+        fwd_solve_warp<T, RP>(sL, RP + 1, srs, sC, RP, 1, sZ, ldz, ncol);
+    }
     fwd_solve_vec_lead<F, RP>(sL, RP + 1, srs, RP, sz);
     if (tid < 32) {
         F q = tid < RP ? f_sqr(sz[tid]) : f_of<F>(0.0);
@@ -2067,7 +2219,7 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
         }
     }
     if (m > 1) {
-        T *out = w.Atil[m] + (size_t)b * w.Atil_stride[m] + (size_t)i * npo * B2;
+        T *out = w.Atil[m] + (size_t)b * w.Atil_stride[m] + (size_t)io * npo * B2;
         const int i0 = TL::r0(), j0 = TL::c0();
         // pair p = pidx(k, l), l = 1..m-1, k = 1..l, in order; each thread's source
         // elements are loaded before its product so the loads overlap the FMAs
@@ -2096,14 +2248,14 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
                         out[(size_t)p * B2 + (i0 + r) * RP + j0 + c] = v[r][c] - acc[r][c];
             }
         }
-        double *wo = w.Atil_w[m] + (size_t)b * w.Atilw_stride[m] + (size_t)i * (m - 1) * RP;
+        double *wo = w.Atil_w[m] + (size_t)b * w.Atilw_stride[m] + (size_t)io * (m - 1) * RP;
         for (int e = tid; e < (m - 1) * RP; e += NT) {
             F acc = f_of<F>(0.0);
             for (int q = 0; q < RP; q++) acc = f_add(acc, f_mul(f_of_T(sZ[q * ldz + e]), sz[q]));
             wo[e] = sw[e] - f_dbl(acc);
         }
         if (tid == 0) {
-            double *du = w.Atil_du[m] + (size_t)b * w.Atildu_stride[m] + 2 * (size_t)i;
+            double *du = w.Atil_du[m] + (size_t)b * w.Atildu_stride[m] + 2 * (size_t)io;
             du[0] = dR;
             du[1] = uR;
         }

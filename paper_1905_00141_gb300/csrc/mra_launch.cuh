@@ -21,7 +21,15 @@ static int set_smem(K kernel, size_t bytes, size_t *done)
     return 0;
 }
 
-template <typename T, int RP> size_t smem_prior(int m) { return smem_prior_bytes<T, RP>(m, prior_stages<T, RP>(m)); }
+// Deep levels run the streamed prior and upward pass (their footprints grow by
+// one block per level instead of two)
+template <typename T, int RP> bool prior_streams(int m) { return smem_prior_bytes<T, RP>(m, 1) > kSmemMax; }
+template <typename T, int RP> bool up_streams(int m) { return smem_up_bytes<T, RP>(m) > kSmemMax; }
+template <typename T, int RP> size_t smem_prior(int m)
+{
+    if (prior_streams<T, RP>(m)) return smem_prior_stream_bytes<T, RP, kPriorStreamBlocks>(m);
+    return smem_prior_bytes<T, RP>(m, prior_stages<T, RP>(m));
+}
 template <typename T, int RP> size_t smem_leafbasis_cfg(int M, int rows, int stages)
 {
     if (rows == kStreamRows) return smem_leafbasis_stream_bytes<T, RP, kStreamRows, kStreamBlocks>(M);
@@ -32,11 +40,21 @@ template <typename T, int RP> size_t smem_leafbasis(int M)
     return smem_leafbasis_bytes<T, RP>(M, leafbasis_stages<T, RP>(M));
 }
 template <typename T, int RP> size_t smem_leafpost_small(int M, int nmax) { return smem_leafpost_bytes<T, RP>(M, nmax); }
-template <typename T, int RP> size_t smem_up(int m) { return smem_up_bytes<T, RP>(m); }
+template <typename T, int RP> size_t smem_up(int m)
+{
+    return up_streams<T, RP>(m) ? smem_up_stream_bytes<T, RP, kUpStreamBlocks>(m) : smem_up_bytes<T, RP>(m);
+}
+// large-leaf assembly of deep trees (FP32 storage): U rows in column parts
+template <typename T, int RP> bool big_assemble_parts(int M)
+{
+    return sizeof(T) == 4 && smem_big_assemble_bytes<T, RP>(M) > kSmemMax;
+}
 template <typename T, int RP> size_t smem_leafgram(int M) { return smem_leafgram_bytes<T, RP>(M); }
 template <typename T, int RP> size_t smem_big(int M)
 {
-    size_t a = smem_big_assemble_bytes<T, RP>(M), p = smem_big_potrf_bytes<T, RP>(M);
+    size_t a = big_assemble_parts<T, RP>(M) ? smem_big_assemble_parts_bytes<T, RP, kBigAssembleParts>(M)
+                                            : smem_big_assemble_bytes<T, RP>(M);
+    size_t p = smem_big_potrf_bytes<T, RP>(M);
     return a > p ? a : p;
 }
 
@@ -78,8 +96,15 @@ static int prior_stages_for(int m, long long ctas, int stages_req, size_t *done)
 template <typename T, int RP>
 int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, int stages_req, void *stream)
 {
-    static size_t done = 0;
+    static size_t done = 0, done_s = 0;
     const long long nreg = (long long)(t.lvl_off[m + 1] - t.lvl_off[m]);
+    if (prior_streams<T, RP>(m)) {
+        const size_t sm = smem_prior_stream_bytes<T, RP, kPriorStreamBlocks>(m);
+        if (int e = set_smem(k_prior<T, RP, kPriorStreamBlocks>, sm, &done_s)) return e;
+        dim3 grid((unsigned)nreg, (unsigned)B);
+        k_prior<T, RP, kPriorStreamBlocks><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, 1);
+        return (int)cudaGetLastError();
+    }
     const int stages = prior_stages_for<T, RP>(m, nreg * B, stages_req, &done);
     const size_t sm = smem_prior_bytes<T, RP>(m, stages);
     if (int e = set_smem(k_prior<T, RP>, sm, &done)) return e;
@@ -198,6 +223,15 @@ int launch_big(const DevTree &t, const Work<T> &w, int phase, const BigLeaf *lea
     size_t sm;
     switch (phase) {
     case BIG_ASSEMBLE:
+        if constexpr (sizeof(T) == 4) {
+            if (big_assemble_parts<T, RP>(t.M)) {
+                static size_t done_ap = 0;
+                sm = smem_big_assemble_parts_bytes<T, RP, kBigAssembleParts>(t.M);
+                if (int e = set_smem(k_big_assemble<T, RP, kBigAssembleParts>, sm, &done_ap)) return e;
+                k_big_assemble<T, RP, kBigAssembleParts><<<grid, NT, sm, s>>>(t, w, leaves, items);
+                break;
+            }
+        }
         sm = smem_big_assemble_bytes<T, RP>(t.M);
         if (int e = set_smem(k_big_assemble<T, RP>, sm, &done_a)) return e;
         k_big_assemble<T, RP><<<grid, NT, sm, s>>>(t, w, leaves, items);
@@ -272,11 +306,17 @@ int launch_gram_colexp(const DevTree &t, const Work<T> &w, int reg0, int nP, int
 template <typename T, int RP>
 int launch_up(const DevTree &t, const Work<T> &w, int m, int reg0, int nreg, int B, void *stream)
 {
-    static size_t done = 0;
-    const size_t sm = smem_up_bytes<T, RP>(m);
-    if (int e = set_smem(k_up<T, RP>, sm, &done)) return e;
+    static size_t done = 0, done_s = 0;
     if (nreg < 0) nreg = (int)(t.lvl_off[m + 1] - t.lvl_off[m]);
     dim3 grid((unsigned)nreg, (unsigned)B);
+    if (up_streams<T, RP>(m)) {
+        const size_t sm = smem_up_stream_bytes<T, RP, kUpStreamBlocks>(m);
+        if (int e = set_smem(k_up<T, RP, kUpStreamBlocks>, sm, &done_s)) return e;
+        k_up<T, RP, kUpStreamBlocks><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, reg0);
+        return (int)cudaGetLastError();
+    }
+    const size_t sm = smem_up_bytes<T, RP>(m);
+    if (int e = set_smem(k_up<T, RP>, sm, &done)) return e;
     k_up<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, reg0);
     return (int)cudaGetLastError();
 }

@@ -32,6 +32,11 @@ Workloads (sizes follow the configurations the library is measured on):
                circulant embedding on a 2048^2 grid (sigma2=1, beta=0.05,
                tau2=0.01); M=14, J=2, r=49.  Stand-in for the AMSR scene of
                the paper (satellite passes with gaps, its r = 49 binary tree).
+* ``modis18``  n=4,194,304 by the swaths recipe (another seed) on the tree
+               of the paper's large MODIS run: M=18, J=2, r=49 (35 device
+               levels, 131,071 regions).  Its number of points is a tenth
+               of that scene's: one GPU holds this tree's prior and leaf
+               basis, the upward pass streams subtrees.
 """
 from __future__ import annotations
 
@@ -45,6 +50,7 @@ WORKLOADS = {
     "clustered": dict(n=2097152, M=9, J=4, r=32, theta=(1.0, 0.05, 0.01)),
     "massive": dict(n=47185920, M=12, J=4, r=16, theta=(1.0, 0.02, 0.01)),
     "swaths": dict(n=2439827, M=14, J=2, r=49, theta=(1.0, 0.05, 0.01)),
+    "modis18": dict(n=4194304, M=18, J=2, r=49, theta=(1.0, 0.05, 0.01)),
 }
 
 SEED_BASE = 1905
@@ -230,6 +236,41 @@ def swaths(seed: int = SEED_BASE + 7, n: int = 2439827, grid_n: int = 2048, peri
     return dict(x=x, y=y, z=z, M=w["M"], J=w["J"], r=w["r"], theta=np.array([[s2, b, t2]]))
 
 
+def modis18(seed: int = SEED_BASE + 8, n: int = 4194304, grid_n: int = 2048):
+    """The swaths recipe (slanted passes with gaps, a GP field) at n points on
+    the tree shape of the paper's large MODIS run: J=2, M=18, r=49 (131,072
+    finest regions, about 32 points each)."""
+    d = swaths(seed=seed, n=n, grid_n=grid_n)
+    w = WORKLOADS["modis18"]
+    d.update(M=w["M"], J=w["J"], r=w["r"])
+    return d
+
+
+def sparse_clusters(n: int, seed: int, k: int = 6, sd: float = 0.015, sprinkle: int = 200, grid_n: int = 1024,
+                    sigma2: float = 1.0, beta: float = 0.05, tau2: float = 0.01):
+    """n points: k isotropic Gaussian clusters (sd, centres uniform on
+    [0.1, 0.9]^2) holding n - sprinkle - 2 points, `sprinkle` uniform points,
+    and the corners (0, 0) and (1, 1), which fix the domain to the unit
+    square; z from an exponential GP (sigma2, beta) by circulant embedding on
+    a grid_n^2 grid, nearest-cell value plus a N(0, tau2) nugget.  On a deep
+    tree most subtrees stay empty, which a reference that skips empty
+    subtrees evaluates quickly; the device path runs every region all the
+    same."""
+    rng = np.random.default_rng(seed)
+    nc = n - sprinkle - 2
+    c = 0.1 + 0.8 * rng.random((k, 2))
+    lab = rng.integers(0, k, nc)
+    x = np.concatenate([c[lab, 0] + sd * rng.standard_normal(nc), rng.random(sprinkle), [0.0, 1.0]])
+    y = np.concatenate([c[lab, 1] + sd * rng.standard_normal(nc), rng.random(sprinkle), [0.0, 1.0]])
+    x = np.clip(x, 0.0, 1.0)
+    y = np.clip(y, 0.0, 1.0)
+    h = 1.0 / (grid_n - 1)
+    field = gp_grid(grid_n, grid_n, h, h, sigma2, beta, rng)
+    ix = np.clip(np.rint(x / h).astype(np.int64), 0, grid_n - 1)
+    iy = np.clip(np.rint(y / h).astype(np.int64), 0, grid_n - 1)
+    return x, y, field[ix, iy] + math.sqrt(tau2) * rng.standard_normal(n)
+
+
 def uniform(n: int, seed: int, sigma2=1.0, beta=0.1, tau2=0.05, exact=True):
     """Small uniform draw for tests (exact GP values when exact=True)."""
     rng = np.random.default_rng(seed)
@@ -243,4 +284,5 @@ def uniform(n: int, seed: int, sigma2=1.0, beta=0.1, tau2=0.05, exact=True):
 
 
 def make(name: str, **kw):
-    return {"small": small, "grid": grid, "clustered": clustered, "massive": massive, "swaths": swaths}[name](**kw)
+    return {"small": small, "grid": grid, "clustered": clustered, "massive": massive, "swaths": swaths,
+            "modis18": modis18}[name](**kw)

@@ -13,7 +13,8 @@ the same workload is the one the stored value belongs to.
 The clustered workload (n = 2,097,152, M = 9) takes about 80 s per theta on 8
 cores; the 47M-observation tree (M = 12) about 10 minutes for its one theta;
 the swaths workload (n = 2,439,827, J = 2, M = 14, r = 49) is checked at two
-theta.
+theta; the modis18 workload (n = 4,194,304 on the J = 2, M = 18, r = 49 tree)
+at its generating theta.
 """
 import os
 import sys
@@ -35,7 +36,7 @@ OUT = os.path.join(HERE, "full_size_oracle.txt")
 # 60 of the 4x4x4 log grid (60 is the corner sigma2 = 2, beta = 0.2,
 # tau2 = 0.005); the 47M tree is checked at its generating theta; the swaths
 # tree at its generating theta and at a longer range with a smaller nugget
-PICKS = {"clustered": [0, 21, 42, 60], "massive": None, "swaths": None}
+PICKS = {"clustered": [0, 21, 42, 60], "massive": None, "swaths": None, "modis18": None}
 SWATHS_EXTRA = [1.5, 0.15, 0.005]
 
 

@@ -187,6 +187,35 @@ def test_parity_deep_binary_trees_r49(n, M, seed):
     assert e.value.status == mra.EINVAL
 
 
+def test_parity_m18_binary_tree_r49():
+    """The paper's large-MODIS tree shape, J = 2, M = 18, r = 49: 35 device
+    levels and 131,071 regions.  This deep, the prior and the upward pass
+    stage their blocks in parts, the large-leaf assembly reads its rows in
+    two parts, and the ATilde arrays of the whole tree (hundreds of GB) do not
+    fit, so the memory plan streams subtrees by itself.  The data (tight
+    clusters, a sprinkle of points) leaves most subtrees empty, which the
+    oracle skips; the device path runs every region."""
+    x, y, z = synth.sparse_clusters(30000, 81, sd=0.006)
+    th = np.array([[1.0, 0.05, 0.01], [1.5, 0.15, 0.005]])
+    ref, st = oracle.loglik(x, y, z, 18, 2, 49, th)
+    assert st == 0
+    with mra.MRA(x, y, z, 18, 2, 49, precision="mixed") as g:
+        s = g.stats()
+        assert s["device_levels"] == 35 and s["n_regions"] == 2 ** 18 - 1
+        assert s["subtree_level"] > 0 and s["subtree_chunks"] >= 1
+        assert s["max_leaf"] > 64
+        ll = g.loglik(th)
+        n = s["n_used"]
+        print("M=18 r=49: subtree level %d, %d chunks, |dl|/n" % (s["subtree_level"], s["subtree_chunks"]),
+              np.abs(ll - ref) / n)
+        assert np.all(np.abs(ll - ref) / n <= TOLMIX)
+        # another level and chunking (6 chunks of 3 of the 16 real-level-5
+        # subtrees) gives the same values bit for bit
+        g.set_launch(subtree_level=9, subtree_chunk=3)
+        assert g.stats()["subtree_chunks"] == 6
+        assert np.array_equal(g.loglik(th), ll)
+
+
 def test_batch_with_invalid_theta():
     x, y, z = synth.uniform(1200, 31)
     th = np.array([[1.0, 0.1, 0.05], [np.nan, 0.1, 0.05], [1.0, -0.1, 0.05], [1.0, 0.1, 0.0],
@@ -257,6 +286,64 @@ def test_streamed_level_gram_matches_whole_level(precision):
         n = g.stats()["n_used"]
     assert np.array_equal(a, b)
     assert np.all(np.abs(b - ref) / n <= (TOL64 if precision == "fp64" else TOLMIX))
+
+
+def _clustered_uniform(n, seed):
+    # uniform points plus two tight clusters (leaves beyond the shared-memory
+    # buckets, so the large-leaf pipeline runs too)
+    x, y, z = synth.uniform(n, seed, exact=False)
+    rng = np.random.default_rng(seed + 1)
+    cx = np.concatenate([0.31 + 0.004 * rng.standard_normal(400), 0.77 + 0.003 * rng.standard_normal(300)])
+    cy = np.concatenate([0.62 + 0.004 * rng.standard_normal(400), 0.18 + 0.003 * rng.standard_normal(300)])
+    return np.concatenate([x, cx]), np.concatenate([y, cy]), np.concatenate([z, rng.standard_normal(700)])
+
+
+@pytest.mark.parametrize("precision,M,J,r,cases", [
+    ("fp64", 5, 4, 16, [(1, 0), (2, 1), (3, 5), (3, 0)]),
+    ("mixed", 5, 4, 16, [(2, 3), (3, 7), (3, 1)]),
+    # r_hat = 49: device levels 2l-1 and 2l hold the same regions (one child)
+    ("mixed", 6, 2, 49, [(4, 3), (5, 2), (9, 5), (7, 0)]),
+])
+def test_subtree_streaming_matches_whole_levels(precision, M, J, r, cases):
+    """The leaf Gram and the upward pass of the levels below S run chunk by
+    chunk of level-S subtrees, with ATilde arrays that hold one chunk: the
+    same log-likelihoods and per-region terms bit for bit, for every level
+    and chunk size (uneven last chunks included), batched theta and graph
+    replay."""
+    x, y, z = _clustered_uniform(20000, 71)
+    with mra.MRA(x, y, z, M, J, r, precision=precision) as g:
+        st = g.stats()
+        assert st["max_leaf"] > 64 and st["subtree_level"] == 0 and st["subtree_chunks"] == 0
+        ref = g.loglik(THETAS)
+        terms = g.region_terms(THETAS[1])
+        lv = st["device_levels"]
+        for S, C in cases:
+            g.set_launch(subtree_level=S, subtree_chunk=C)
+            s2 = g.stats()
+            assert s2["subtree_level"] == S
+            assert s2["subtree_chunks"] >= 1
+            if C > 0:
+                k = S if r <= 32 else (S + 1) // 2  # real level of device level S
+                assert s2["subtree_chunks"] == -(-(J ** (k - 1)) // C)
+            for _ in range(2):  # the second call replays the captured pass
+                assert np.array_equal(g.loglik(THETAS), ref)
+            t2 = g.region_terms(THETAS[1])
+            for key in ("d", "u", "logdetW"):
+                assert np.array_equal(t2[key], terms[key], equal_nan=True), (S, C, key)
+            assert t2["loglik"] == terms["loglik"]
+        if precision == "mixed":
+            # the tensor-core Gram's column exponents follow the chunks too
+            g.set_launch(gram_tensor_cores=True)
+            tc = g.loglik(THETAS)
+            g.set_launch(gram_tensor_cores=True, subtree_level=lv - 3, subtree_chunk=2)
+            assert np.array_equal(g.loglik(THETAS), tc)
+        for bad in (lv - 1, -1):
+            with pytest.raises(mra.MRAError) as e:
+                g.set_launch(subtree_level=bad)
+            assert e.value.status == mra.EINVAL
+        g.set_launch()
+        assert g.stats()["subtree_level"] == 0
+        assert np.array_equal(g.loglik(THETAS), ref)
 
 
 def test_precision_switch_resizes_scratch():

@@ -60,6 +60,21 @@ def test_massive_recipe_scaled_down():
     assert 0.5 * expected < empty < 1.6 * expected, (empty, expected)
 
 
+def test_sparse_clusters_recipe():
+    """n points in the unit square with its corners, all but the sprinkle
+    within a few sd of k centres, a smooth field of variance near
+    sigma2 + tau2; the same draw for the same seed."""
+    x, y, z = synth.sparse_clusters(30000, 81, k=6, sd=0.006, sprinkle=200, grid_n=256)
+    assert len(x) == len(y) == len(z) == 30000
+    assert x.min() == 0.0 and y.min() == 0.0 and x.max() == 1.0 and y.max() == 1.0
+    h, _, _ = np.histogram2d(x, y, bins=100, range=[[0, 1], [0, 1]])
+    # 6 clusters of sd 0.006 fit in a few cells each of a 100 x 100 histogram
+    assert np.sort(h.ravel())[::-1][:6 * 9].sum() > 0.9 * (30000 - 202)
+    assert 0.2 < np.var(z) < 2.5
+    x2, _, z2 = synth.sparse_clusters(30000, 81, k=6, sd=0.006, sprinkle=200, grid_n=256)
+    assert np.array_equal(x2, x) and np.array_equal(z2, z)
+
+
 def test_theta_designs():
     th = synth.theta_grid_4x4x4()
     assert th.shape == (64, 3)
