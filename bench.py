@@ -77,10 +77,10 @@ def parse():
                    help="pin the launch configuration (mra_set_launch) instead of running the autotuner, "
                         "e.g. 64,1,0,1 (QUEUE 1: leaf buckets as persistent work queues; PRIOR 0/1/2: the "
                         "prior's ancestor blocks in one or two buffers by occupancy, one, two)")
-    p.add_argument("--workload", default="grid", choices=["grid", "clustered", "massive", "swaths"],
+    p.add_argument("--workload", default="grid", choices=["grid", "clustered", "massive", "swaths", "modis18"],
                    help="grid: n=131,072, 1 theta per call (default); clustered: n=2,097,152 with 64 theta per "
                         "call; massive: n=47,185,920, 1 theta per call; swaths: n=2,439,827, J=2, M=14, "
-                        "r=49, 1 theta per call")
+                        "r=49, 1 theta per call; modis18: n=4,194,304, J=2, M=18, r=49, 1 theta per call")
     return p.parse_args()
 
 
@@ -122,6 +122,10 @@ WORKLOAD_INFO = {
                    data="synthetic: n=2439827 uniform on [0,1]^2 in slanted bands (80% coverage, straight gaps); "
                         "z from an exponential GP (sigma2=1, beta=0.05, tau2=0.01) by circulant embedding, "
                         "seed 1912"),
+    "modis18": dict(desc="modis18 n=4194304 M=18 J=2 r=49 (35 device levels), 1 theta per call", per_call=1,
+                    data="synthetic: n=4194304 uniform on [0,1]^2 in slanted bands (80% coverage, straight gaps); "
+                         "z from an exponential GP (sigma2=1, beta=0.05, tau2=0.01) by circulant embedding, "
+                         "seed 1913"),
 }
 
 
@@ -262,10 +266,10 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": "the FP64 CPU oracle is not run on the 47M-observation "
                           "tree (about 5 TFLOP and tens of GB of host memory per evaluation)"}), flush=True)
         return 0
-    if args.workload == "swaths":
+    if args.workload in ("swaths", "modis18"):
         print(json.dumps({"impl": "reference", "unavailable": "the FP64 CPU oracle takes minutes per evaluation of "
-                          "the r=49 swaths tree; its stored values are checked in tests/test_zv_swaths_gpu.py"}),
-              flush=True)
+                          "the r=49 %s tree; its stored values are checked in tests/test_zv_%s_gpu.py" %
+                          (args.workload, args.workload)}), flush=True)
         return 0
     d = workload(args.workload)
     thetas = step_thetas(args.workload).reshape(-1, 3)
@@ -389,7 +393,7 @@ def run_ours(args):
     # the other precision on the same theta, for the mixed-vs-FP64 comparison
     other = "fp64" if args.precision != "fp64" else "mixed"
     other_line, ll_o = None, None
-    if name not in ("massive", "swaths"):
+    if name not in ("massive", "swaths", "modis18"):
         oargs = argparse.Namespace(**vars(args))
         if name != "grid":
             oargs.steps, oargs.warmup = min(args.steps, 2), 1
@@ -441,9 +445,8 @@ def run_ours(args):
             acc["mixed_fast"] = float(np.max(np.abs(ll_f - ref)) / n)
     elif ll_o is not None:
         acc = {"against": "FP64 GPU path", args.precision: float(np.max(np.abs(ll - ll_o)) / n)}
-    elif name == "swaths":
-        acc = {"against": None, "note": "the FP64 kernels do not fit this depth (27 device levels); the stored "
-                                        "oracle values are checked in tests/test_zv_swaths_gpu.py"}
+    elif name in ("swaths", "modis18"):
+        acc = stored_accuracy(name, d, thetas, ll, n, args.precision)
     else:
         acc = {"against": None, "note": "FP64 does not fit one theta of this tree; sampled leaves against the "
                                         "oracle in tests/test_zx_massive_gpu.py"}
@@ -546,6 +549,32 @@ def run_ours(args):
         dist.barrier()
     g.close()
     return 0
+
+
+def stored_accuracy(name, d, thetas, ll, n, precision):
+    """|dl|/n of the timed calls whose theta has a stored FP64 CPU oracle
+    value (tests/golden/full_size_oracle.txt, used only when this draw of the
+    workload matches the value's fingerprint); the FP64 kernels do not fit
+    these depths."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    try:
+        from golden_values import fingerprint_matches, golden
+    finally:
+        sys.path.pop(0)
+    rows = golden(name)
+    th = thetas.reshape(-1, 3)
+    vals = np.asarray(ll).reshape(-1)
+    errs = []
+    for r in rows:
+        if not fingerprint_matches(d, r[3]):
+            continue
+        for k in range(th.shape[0]):
+            if np.allclose(th[k], r[0], rtol=1e-12, atol=0):
+                errs.append(abs(vals[k] - r[1]) / n)
+    if not errs:
+        return {"against": None, "note": "no stored oracle value matches these calls; the FP64 kernels do not "
+                                         "fit this depth"}
+    return {"against": "FP64 CPU oracle (stored values)", "calls_checked": len(errs), precision: float(max(errs))}
 
 
 def family_fractions(prof, st, per_call, steps, alu_peak, precision, name):

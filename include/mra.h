@@ -150,7 +150,7 @@ mra_status mra_loglik_device(mra_ctx *ctx, const double *theta_dev, int batch, d
  * precision by timing it on this tree.  Candidates: observation rows per
  * leaf-basis CTA (32 or, in the mixed mode, 64), one or two shared-memory
  * stages of ancestor blocks, the leaf-size buckets of the leaf posterior
- * ({<=32, <=48, <=64} or {<=32, <=64}), running those buckets on side
+ * ({<=32, <=40, <=48, <=64} or {<=32, <=64}), running those buckets on side
  * streams or one after another, and each bucket as one CTA per leaf or as a
  * persistent work queue.  Every candidate computes the same loglik,
  * bit for bit; only the time differs.  Each candidate runs 2 untimed and
@@ -163,7 +163,7 @@ typedef struct {
                              staged two at a time, the same results bit for bit), the default where 32-row
                              chunks leave room for one CTA per SM */
     int leafbasis_stages; /* 1 or 2 */
-    int bucket_set;       /* 0: {<=32, <=48, <=64}, 1: {<=32, <=64} */
+    int bucket_set;       /* 0: {<=32, <=40, <=48, <=64}, 1: {<=32, <=64} */
     int concurrent;       /* 1: leaf-posterior buckets on side streams */
     double ms_default;    /* mean pass time with the configuration before the call */
     double ms_best;       /* mean pass time with the chosen configuration */
@@ -191,13 +191,18 @@ typedef struct {
                              theta's scratch would not fit the budget otherwise (deep trees: ATilde grows
                              with the number of regions, not with n).  The same results bit for bit. */
     int subtree_chunk;    /* level-S regions per chunk; 0: the largest that fits the budget */
+    int leafbasis_whole_chunks; /* 0 (default): a region's last leaf-basis chunk of at most half the rows (32-
+                                   or 64-row chunks) runs in the kernel of half the rows, on a side stream
+                                   beside the full chunks (less padding); 1: every chunk at full size.  The
+                                   same results bit for bit; the autotuner keeps the setting in force. */
 } mra_tune_t;
 
 mra_status mra_autotune(mra_ctx *ctx, const double *theta, int reps, mra_tune_t *out);
 
 /* Set the launch configuration directly (the four configuration fields of
  * cfg, gram_tensor_cores, leaf_queue, prior_stages, leafbasis_tensor_cores,
- * subtree_level and subtree_chunk; the times are ignored).  leafbasis_rows 0 and
+ * subtree_level, subtree_chunk and leafbasis_whole_chunks; the times are
+ * ignored).  leafbasis_rows 0 and
  * leafbasis_stages 0 select the defaults; EINVAL for a value outside the
  * candidates or one whose shared memory does not fit. */
 mra_status mra_set_launch(mra_ctx *ctx, const mra_tune_t *cfg);
@@ -258,6 +263,9 @@ mra_status mra_predict(mra_ctx *ctx, const double *theta, const double *px, cons
  * mra_profile -- enable (1) or disable (0) per-kernel device timing: every
  *   later launch is bracketed by two CUDA events recorded on the call's
  *   stream.  Enabling clears the records.  Costs two event records per launch.
+ *   A profiled pass runs the kernels that otherwise share the GPU on side
+ *   streams (leaf-posterior buckets, leaf-basis tail chunks) one after
+ *   another, so each pair of events times one kernel alone.
  */
 mra_status mra_profile(mra_ctx *ctx, int enable);
 

@@ -339,28 +339,32 @@ struct mra_ctx {
     int64_t *d_leaf_off = nullptr;
     Chunk *d_chunks32 = nullptr, *d_chunks64 = nullptr; // leaf-basis chunks of 32 / 64 rows
     int nchunks32 = 0, nchunks64 = 0;
+    // the last ntail32 (ntail64) chunks of each list are the regions' tails
+    // of at most half a chunk, which run as chunks of half the rows
+    int ntail32 = 0, ntail64 = 0;
     Chunk *d_chunks128 = nullptr; // 128-row chunks of the tensor-core leaf basis
     int nchunks128 = 0;
     Chunk *d_chunks16 = nullptr; // 16-row chunks of the streaming leaf basis (deep trees)
     int nchunks16 = 0;
     // leaves with 1..kLeafCap[k] observations (and more than the previous cap),
     // one CTA each; larger leaves take the global-memory path
-    int64_t *d_leaves[kLeafBuckets] = {nullptr, nullptr, nullptr};
-    int nl[kLeafBuckets] = {0, 0, 0};
+    int64_t *d_leaves[kLeafBuckets] = {};
+    int nl[kLeafBuckets] = {};
     int nmax_small = 64; // largest bucket cap whose shared memory fits
     bool lb64_fits = true; // mixed modes: 64-row leaf-basis chunks fit in shared memory
     bool fp64_fits = true; // the FP64 kernels fit in shared memory on this tree
-    // the 48- and 64-observation buckets as one list (bucket set 1)
+    // the buckets above the first as one list (bucket set 1)
     int64_t *d_leaves_m = nullptr;
     int nl_m = 0;
     // launch configuration (mra_autotune): leaf-basis rows per chunk (0 = the
     // precision's default) and prefetch stages (0 = automatic), bucket set
-    // (0: 32/48/64, 1: 32/64), side streams for the leaf posterior
+    // (0: 32/40/48/64, 1: 32/64), side streams for the leaf posterior
     int lb_rows = 0, lb_stages = 0, bucket_set = 0;
     bool concurrent = true;
     bool gram_tc = false; // mixed modes: leaf Gram on the tensor cores (exact slices)
     bool lb_tc = false;   // MRA_MIXED: leaf basis with its remainder products on the tensor cores
     bool leaf_queue = false; // shared-memory leaf buckets as persistent work-queue kernels
+    bool lb_whole = false;   // leaf basis: tails of 32/64-row chunks kept in full-size chunks
     int prior_st = 0;        // prior: 0 one or two stages by occupancy, 1 one stage, 2 two where they fit
     unsigned *d_qcnt = nullptr; // their counters: kLeafBuckets x status_cap
     BigLeaf *d_big = nullptr;
@@ -399,8 +403,9 @@ struct mra_ctx {
     // independent leaf-posterior launches (size buckets, the large-leaf
     // pipeline) run side by side on these streams, forked from and joined to
     // the pass's stream by events
-    cudaStream_t aux[kLeafBuckets] = {nullptr, nullptr, nullptr};
-    cudaEvent_t fork_ev = nullptr, join_ev[kLeafBuckets] = {nullptr, nullptr, nullptr};
+    cudaStream_t aux[kLeafBuckets] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kLeafBuckets] = {};
+    cudaEvent_t lbt_fork = nullptr, lbt_join = nullptr; // the leaf basis's tail chunks on aux[0]
     unsigned char *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     size_t per_theta_bytes = 0;
@@ -711,12 +716,40 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
     const Chunk *chunks = rows == 64 ? c->d_chunks64 : (rows == kStreamRows ? c->d_chunks16 : c->d_chunks32);
     const int nchunks = rows == 64 ? c->nchunks64 : (rows == kStreamRows ? c->nchunks16 : c->nchunks32);
     const bool lbtc = sizeof(T) == 4 && c->lb_tc && c->precision == MRA_MIXED;
-    if (M > 1 && nchunks > 0)
+    // the regions' short tails (at most half a chunk, listed last) run as
+    // chunks of half the rows beside the full chunks, on a side stream
+    const int ntail = (lbtc || c->lb_whole) ? 0 : (rows == 64 ? c->ntail64 : (rows == 32 ? c->ntail32 : 0));
+    const int nmain = nchunks - ntail;
+    // (a profiled pass runs them one after another, so that each kernel's
+    // events time that kernel alone)
+    const bool tail_side = ntail > 0 && nmain > 0 && c->concurrent && !c->prof_on;
+    if (tail_side) {
+        if (!c->lbt_fork && cudaEventCreateWithFlags(&c->lbt_fork, cudaEventDisableTiming) != cudaSuccess)
+            return (int)cudaErrorLaunchFailure;
+        if (!c->lbt_join && cudaEventCreateWithFlags(&c->lbt_join, cudaEventDisableTiming) != cudaSuccess)
+            return (int)cudaErrorLaunchFailure;
+        if (!c->aux[0] && cudaStreamCreateWithFlags(&c->aux[0], cudaStreamNonBlocking) != cudaSuccess)
+            return (int)cudaErrorLaunchFailure;
+        cudaEventRecord(c->lbt_fork, s);
+    }
+    if (M > 1 && nmain > 0)
         if ((e = timed_launch(c, K_LEAFBASIS, s, [&] {
                  return lbtc ? launch_leafbasis_tc<T, RP>(t, w, c->d_chunks128, c->nchunks128, B, s)
-                             : launch_leafbasis<T, RP>(t, w, chunks, nchunks, rows, c->lb_stages, B, s);
+                             : launch_leafbasis<T, RP>(t, w, chunks, nmain, rows, c->lb_stages, B, s);
              })))
             return e;
+    if (M > 1 && ntail > 0) {
+        cudaStream_t q = tail_side ? c->aux[0] : s;
+        if (tail_side) cudaStreamWaitEvent(q, c->lbt_fork, 0);
+        if ((e = timed_launch(c, K_LEAFBASIS, q, [&] {
+                 return launch_leafbasis_half<T, RP>(t, w, chunks + nmain, ntail, rows, c->lb_stages, B, q);
+             })))
+            return e;
+        if (tail_side) {
+            cudaEventRecord(c->lbt_join, q);
+            cudaStreamWaitEvent(s, c->lbt_join, 0);
+        }
+    }
     // leaf posterior: the size buckets and the large-leaf pipeline touch
     // disjoint leaves, so they run concurrently: the large leaves (or the first
     // bucket) on s, every other bucket on a side stream forked from s
@@ -728,7 +761,7 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
         int nlist = 0;
         const bool merged = c->bucket_set == 1 && c->nmax_small >= 64;
         for (int k = 0; k < kLeafBuckets; k++) {
-            if (merged && kLeafCap[k] == 48) continue;
+            if (merged && kLeafCap[k] > kLeafCap[0] && kLeafCap[k] < 64) continue;
             lists[nlist] = (merged && kLeafCap[k] == 64) ? c->d_leaves_m : c->d_leaves[k];
             counts[nlist] = (merged && kLeafCap[k] == 64) ? c->nl_m : c->nl[k];
             caps[nlist] = kLeafCap[k];
@@ -736,7 +769,7 @@ int run_pass(mra_ctx *c, const Work<T> &w, int B, cudaStream_t s)
         }
         int jobs = c->nbig > 0 ? 1 : 0;
         for (int k = 0; k < nlist; k++) jobs += counts[k] > 0;
-        const bool fork = jobs > 1 && c->concurrent;
+        const bool fork = jobs > 1 && c->concurrent && !c->prof_on;
         if (fork) {
             if (!c->fork_ev && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess)
                 return (int)cudaErrorLaunchFailure;
@@ -1533,12 +1566,22 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
             }
         }
     }
+    // a region's last chunk of at most half the rows (the padding of a 32- or
+    // 64-row chunk otherwise) goes to the end of its list, where the launcher
+    // runs it as a chunk of half the rows
+    auto tails_last = [](std::vector<Chunk> &v, int rows) {
+        std::stable_partition(v.begin(), v.end(), [rows](const Chunk &ch) { return 2 * ch.n > rows; });
+        return (int)std::count_if(v.begin(), v.end(), [rows](const Chunk &ch) { return 2 * ch.n <= rows; });
+    };
+    c->ntail32 = tails_last(chunks32, 32);
+    c->ntail64 = tails_last(chunks64, 64);
     // The leaf buckets are sized where the FP64 kernels fit (they take twice
     // the bytes); on trees too deep for them only the mixed modes run.
     c->fp64_fits = max_smem_needed(c, kLeafCap[0], true) <= kSmemMax;
     const bool f64 = c->fp64_fits;
-    int nmax_small = kLeafCap[kLeafBuckets - 1];
-    while (nmax_small > kLeafCap[0] && max_smem_needed(c, nmax_small, f64) > kSmemMax) nmax_small -= 16;
+    int kcap = kLeafBuckets - 1;
+    while (kcap > 0 && max_smem_needed(c, kLeafCap[kcap], f64) > kSmemMax) kcap--;
+    const int nmax_small = kLeafCap[kcap];
     if (max_smem_needed(c, nmax_small, f64) > kSmemMax) {
         c->err = "M too large for the shared-memory kernels at this r";
         *out = c;
@@ -1570,7 +1613,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         }
     }
     c->vbig_elems = voff;
-    // bucket set 1: the 48- and 64-observation leaves as one list
+    // bucket set 1: the leaves of every bucket above the first as one list
     std::vector<int64_t> lbm;
     for (int64_t l = 0; l < P.nleaf(); l++) {
         const int64_t nl = P.leaf_off[(size_t)l + 1] - P.leaf_off[(size_t)l];
@@ -1635,6 +1678,7 @@ static mra_status build_ctx(const double *lon, const double *lat, const double *
         (st = dev_upload(c, &c->d_leaves[0], lb[0].data(), lb[0].size())) ||
         (st = dev_upload(c, &c->d_leaves[1], lb[1].data(), lb[1].size())) ||
         (st = dev_upload(c, &c->d_leaves[2], lb[2].data(), lb[2].size())) ||
+        (st = dev_upload(c, &c->d_leaves[3], lb[3].data(), lb[3].size())) ||
         (st = dev_upload(c, &c->d_leaves_m, lbm.data(), lbm.size())) ||
         (st = dev_upload(c, &c->d_big, big.data(), big.size())) ||
         (st = dev_upload(c, &c->d_bigitems, items.data(), items.size()))) {
@@ -1790,6 +1834,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         out->gram_tensor_cores = c->gram_tc ? 1 : 0;
         out->leafbasis_tensor_cores = c->lb_tc ? 1 : 0;
         out->leaf_queue = bestc.queue ? 1 : 0;
+        out->leafbasis_whole_chunks = c->lb_whole ? 1 : 0;
         out->prior_stages = bestc.prior;
         out->subtree_level = c->sub_req_level;
         out->subtree_chunk = c->sub_req_chunk;
@@ -1851,6 +1896,7 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
         }
     }
     c->leaf_queue = g->leaf_queue != 0;
+    c->lb_whole = g->leafbasis_whole_chunks != 0;
     c->prior_st = g->prior_stages;
     drop_graphs(c);
     return MRA_OK;
@@ -2160,8 +2206,10 @@ void mra_free(mra_ctx *c)
         if (c->join_ev[k]) cudaEventDestroy(c->join_ev[k]);
     }
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->lbt_fork) cudaEventDestroy(c->lbt_fork);
+    if (c->lbt_join) cudaEventDestroy(c->lbt_join);
     void *ptrs[] = {c->d_kx, c->d_ky, c->d_cx, c->d_cy, c->d_sx, c->d_sy, c->d_sz, c->d_leaf_off, c->d_chunks32,
-                    c->d_chunks64, c->d_chunks128, c->d_chunks16, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_leaves_m, c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
+                    c->d_chunks64, c->d_chunks128, c->d_chunks16, c->d_leaves[0], c->d_leaves[1], c->d_leaves[2], c->d_leaves[3], c->d_leaves_m, c->d_big, c->d_bigitems, c->d_scratch, c->d_status, c->d_theta_stage, c->d_ll_stage,
                     c->d_reg_du, c->d_reg_lw, c->pred.pt, c->pred.tree, c->d_qcnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);

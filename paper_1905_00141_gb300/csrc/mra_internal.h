@@ -159,9 +159,11 @@ __host__ __device__ inline size_t predict_warp_doubles(int M, int RP, int nl)
 
 
 // Leaf-posterior buckets: a leaf with n observations runs in the kernel of the
-// smallest cap >= n (shared-memory footprint grows as cap^2).
-constexpr int kLeafBuckets = 3;
-constexpr int kLeafCap[kLeafBuckets] = {32, 48, 64};
+// smallest cap >= n (shared-memory footprint grows as cap^2, so a cap close
+// above the common leaf sizes keeps more CTAs per SM: a 40-observation bucket
+// runs four CTAs per SM where the 48 one runs three at r = 32).
+constexpr int kLeafBuckets = 4;
+constexpr int kLeafCap[kLeafBuckets] = {32, 40, 48, 64};
 
 struct Chunk {
     int32_t parent; // level M-1 region index
@@ -211,6 +213,9 @@ int launch_predict(const DevTree &t, const Work<T> &w, const PredArgs &q, void *
 template <typename T, int RP>
 int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int rows, int stages,
                      int B, void *stream);
+template <typename T, int RP>
+int launch_leafbasis_half(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int rows, int stages,
+                          int B, void *stream);
 template <typename T, int RP>
 int launch_leafbasis_tc(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int B, void *stream);
 // Rows per chunk of the tensor-core leaf basis, and the largest (M - 2) RP

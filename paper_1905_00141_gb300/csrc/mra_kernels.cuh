@@ -1818,9 +1818,22 @@ __device__ __forceinline__ void leafpost_small_leaf(const DevTree &t, const Work
     }
 }
 
+// CTAs per SM the register budget must allow in the mixed modes: as many as
+// the bucket's shared memory fits on trees of M = 7 at RP = 32 (five, four
+// and three for caps 32, 40 and 48).  Left to itself the compiler spends 86
+// to 110 registers a thread on the Cholesky's register-resident panel, which
+// holds every bucket to two CTAs per SM.
+template <typename T, int RP, int NMAX>
+constexpr int leafpost_min_ctas()
+{
+    if (sizeof(T) != 4) return 1;
+    return NMAX <= 32 ? 5 : (NMAX <= 40 ? 4 : (NMAX <= 48 ? 3 : 1));
+}
+
 // One CTA per leaf of the list (grid.x), theta grid.y.
 template <typename T, int RP, int NMAX>
-__global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, const int64_t *leaves)
+__global__ void __launch_bounds__(NT, (leafpost_min_ctas<T, RP, NMAX>())) k_leafpost_small(DevTree t, Work<T> w,
+                                                                                           const int64_t *leaves)
 {
     const int b = blockIdx.y;
     if (!theta_ok(w.theta + 3 * b)) return;
@@ -1835,7 +1848,7 @@ __global__ void __launch_bounds__(NT) k_leafpost_small(DevTree t, Work<T> w, con
 // leaf is computed by the same code as above, so the results are the same bit
 // for bit.
 template <typename T, int RP, int NMAX>
-__global__ void __launch_bounds__(NT) k_leafpost_queue(DevTree t, Work<T> w, const int64_t *leaves, int nleaves,
+__global__ void __launch_bounds__(NT, (leafpost_min_ctas<T, RP, NMAX>())) k_leafpost_queue(DevTree t, Work<T> w, const int64_t *leaves, int nleaves,
                                                        unsigned *counter)
 {
     const int b = blockIdx.y;

@@ -147,6 +147,20 @@ int launch_leafbasis(const DevTree &t, const Work<T> &w, const Chunk *chunks, in
     return launch_leafbasis_ch<T, RP, 32>(t, w, chunks, nchunks, stages, B, stream);
 }
 
+// chunks of at most rows / 2 observation rows (the regions' tails of a 32- or
+// 64-row chunk list) in the kernel of half the rows: each output sums the same
+// terms in the same order, so U is the same bit for bit
+template <typename T, int RP>
+int launch_leafbasis_half(const DevTree &t, const Work<T> &w, const Chunk *chunks, int nchunks, int rows, int stages,
+                          int B, void *stream)
+{
+    if (nchunks == 0) return 0;
+    if constexpr (sizeof(T) == 4)
+        if (rows == 64) return launch_leafbasis_ch<T, RP, 32>(t, w, chunks, nchunks, stages, B, stream);
+    if (rows != 32) return (int)cudaErrorInvalidValue;
+    return launch_leafbasis_ch<T, RP, 16>(t, w, chunks, nchunks, stages, B, stream);
+}
+
 // mixed mode: the leaf basis with the remainder products on the tensor cores
 // (128-row chunks); EINVAL where the exactness bound does not hold
 template <typename T, int RP>
@@ -199,15 +213,19 @@ static int launch_leafpost_n(const DevTree &t, const Work<T> &w, const int64_t *
     return (int)cudaGetLastError();
 }
 
-// nmax: a bucket cap (32, 48 or 64); the leaves of the list have at most nmax
-// observations.  queue: null for one CTA per leaf, else B zeroed counters for
-// the persistent work-queue kernel.
+// nmax: a bucket cap (32, 40, 48 or 64); the leaves of the list have at most
+// nmax observations.  queue: null for one CTA per leaf, else B zeroed counters
+// for the persistent work-queue kernel.  The 40 cap has its own kernel at
+// RP = 32 (its Y = L^{-1} U tile does not divide at RP = 16, where the 48
+// kernel takes it).
 template <typename T, int RP>
 int launch_leafpost_small(const DevTree &t, const Work<T> &w, const int64_t *leaves, int nleaves, int nmax,
                           int B, unsigned *queue, void *stream)
 {
     if (nleaves == 0) return 0;
     if (nmax <= 32) return launch_leafpost_n<T, RP, 32>(t, w, leaves, nleaves, B, queue, stream);
+    if constexpr (RP == 32)
+        if (nmax <= 40) return launch_leafpost_n<T, RP, 40>(t, w, leaves, nleaves, B, queue, stream);
     if (nmax <= 48) return launch_leafpost_n<T, RP, 48>(t, w, leaves, nleaves, B, queue, stream);
     return launch_leafpost_n<T, RP, 64>(t, w, leaves, nleaves, B, queue, stream);
 }
@@ -363,6 +381,8 @@ int launch_predict(const DevTree &t, const Work<T> &w, const PredArgs &q, void *
     template int launch_leafbasis<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, int, int, \
                                          void *);                                                           \
     template int launch_leafbasis_tc<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, void *); \
+    template int launch_leafbasis_half<T, RP>(const DevTree &, const Work<T> &, const Chunk *, int, int, int,  \
+                                              int, void *);                                                 \
     template int launch_leafpost_small<T, RP>(const DevTree &, const Work<T> &, const int64_t *, int, int,   \
                                               int, unsigned *, void *);                                     \
     template size_t smem_big<T, RP>(int);                                                                   \

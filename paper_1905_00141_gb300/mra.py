@@ -63,7 +63,8 @@ class Tune(ctypes.Structure):
                 ("concurrent", ctypes.c_int), ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double),
                 ("tried", ctypes.c_int), ("gram_tensor_cores", ctypes.c_int), ("leaf_queue", ctypes.c_int),
                 ("prior_stages", ctypes.c_int), ("leafbasis_tensor_cores", ctypes.c_int),
-                ("subtree_level", ctypes.c_int), ("subtree_chunk", ctypes.c_int)]
+                ("subtree_level", ctypes.c_int), ("subtree_chunk", ctypes.c_int),
+                ("leafbasis_whole_chunks", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -227,10 +228,12 @@ class MRA:
         return {k: getattr(out, k) for k, _ in Tune._fields_}
 
     def set_launch(self, leafbasis_rows=0, leafbasis_stages=0, bucket_set=0, concurrent=True, gram_tensor_cores=False,
-                   leaf_queue=False, prior_stages=0, leafbasis_tensor_cores=False, subtree_level=0, subtree_chunk=0):
+                   leaf_queue=False, prior_stages=0, leafbasis_tensor_cores=False, subtree_level=0, subtree_chunk=0,
+                   leafbasis_whole_chunks=False):
         cfg = Tune(int(leafbasis_rows), int(leafbasis_stages), int(bucket_set), int(bool(concurrent)), 0.0, 0.0, 0,
                    int(bool(gram_tensor_cores)), int(bool(leaf_queue)), int(prior_stages),
-                   int(bool(leafbasis_tensor_cores)), int(subtree_level), int(subtree_chunk))
+                   int(bool(leafbasis_tensor_cores)), int(subtree_level), int(subtree_chunk),
+                   int(bool(leafbasis_whole_chunks)))
         self._check(lib().mra_set_launch(self._h, ctypes.byref(cfg)))
 
     def loglik_status(self, theta):

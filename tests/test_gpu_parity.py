@@ -50,6 +50,7 @@ def _parity(x, y, z, M, J, r, thetas=THETAS, precisions=("fp64", "mixed"), build
     (3000, 5, 4, 32, 5),
     (4000, 6, 2, 16, 6),
     (1500, 4, 4, 2, 7),     # r_hat = 2
+    (2300, 4, 4, 32, 8),    # leaves of about 36: the <=32, <=40, <=48 and <=64 buckets
 ])
 def test_parity_small_trees(n, M, J, r, seed):
     x, y, z = synth.uniform(n, seed)
@@ -386,7 +387,7 @@ def test_graph_replay_equals_direct_launches(precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_launch_configurations_agree_bit_for_bit(precision):
-    # leaves of every bucket (<=32, <=48, <=64) and larger ones
+    # leaves of every bucket (<=32, <=40, <=48, <=64) and larger ones
     rng = np.random.default_rng(31)
     x, y, z = synth.uniform(6000, 24)
     cx = 0.25 + 0.01 * rng.standard_normal(500)
@@ -406,6 +407,10 @@ def test_launch_configurations_agree_bit_for_bit(precision):
                         for queue in (False, True):
                             g.set_launch(r, stages, bset, conc, leaf_queue=queue)
                             assert np.array_equal(g.loglik(THETAS), ref), (r, stages, bset, conc, queue)
+                # the regions' short tails in chunks of half the rows (default) or in full chunks
+                if r != 16:
+                    g.set_launch(r, 0, 0, True, leafbasis_whole_chunks=True)
+                    assert np.array_equal(g.loglik(THETAS), ref), (r, "whole chunks")
         # the prior's ancestor blocks in one buffer, in two, or by occupancy
         for ps in (1, 2, 0):
             g.set_launch(prior_stages=ps)
@@ -417,6 +422,32 @@ def test_launch_configurations_agree_bit_for_bit(precision):
         assert np.array_equal(g.loglik(THETAS), ref)
         with pytest.raises(mra.MRAError):
             g.set_launch(48, 1, 0, True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_leaf_buckets_and_leafbasis_tails_r32_bit_for_bit(precision):
+    # r = 32: leaves of about 36 observations fill the <=32, <=40, <=48 and
+    # <=64 buckets (the 40 cap has a kernel of its own at this padding), and
+    # level-3 regions of about 144 rows end in tails of at most half a chunk.
+    # Every arrangement computes the same terms in the same order.
+    x, y, z = synth.uniform(2300, 8)
+    ref, st = oracle.loglik(x, y, z, 4, 4, 32, THETAS)
+    assert st == 0
+    with mra.MRA(x, y, z, 4, 4, 32, precision=precision) as g:
+        n = g.stats()["n_used"]
+        sizes = np.diff(g.tree()["leaf_off"])
+        assert all(np.any((sizes > lo) & (sizes <= hi)) for lo, hi in ((0, 32), (32, 40), (40, 48), (48, 64)))
+        base = g.loglik(THETAS)
+        tol = 1e-10 if precision == "fp64" else 1e-6
+        assert np.all(np.abs(base - ref) / n <= tol)
+        rows = (32, 64) if precision == "mixed" else (32,)
+        for r in rows:
+            for whole in (False, True):
+                for bset in (0, 1):
+                    for conc in (True, False):
+                        for queue in (False, True):
+                            g.set_launch(r, 1, bset, conc, leaf_queue=queue, leafbasis_whole_chunks=whole)
+                            assert np.array_equal(g.loglik(THETAS), base), (r, whole, bset, conc, queue)
 
 
 @pytest.mark.parametrize("n,M,r,seed", [(20000, 14, 16, 41), (30000, 18, 9, 42)])
