@@ -1747,10 +1747,12 @@ __device__ __forceinline__ void leafpost_small_leaf(const DevTree &t, const Work
         }
     }
     __syncthreads();
-    if constexpr (sizeof(T) == 4)
-        chol_blocked<NMAX>(sV, LDV, n, srs, flag, MRA_SINGULAR, red);
-    else
-        chol_small<F, (tri_count(NMAX) + NT - 1) / NT>(sV, LDV, n, srs, sr2, flag, MRA_SINGULAR);
+    // the per-column factor: with several leaves per SM the kernel is bound by
+    // issue, not by one factor's latency, and the blocked factor's
+    // register-resident panel costs more instructions and registers here (it
+    // stays in the prior and the upward pass, whose top levels are latency
+    // chains of one CTA)
+    chol_small<F, (tri_count(NMAX) + NT - 1) / NT>(sV, LDV, n, srs, sr2, flag, MRA_SINGULAR);
     const double dv = logdet_small(sV, LDV, n, red);
     trinv_warp<T, NMAX>(sV, LDV, srs, sLi, nmax, n);
     // Y = L^{-1} U, block column by block column, straight to global; row r
@@ -1820,9 +1822,8 @@ __device__ __forceinline__ void leafpost_small_leaf(const DevTree &t, const Work
 
 // CTAs per SM the register budget must allow in the mixed modes: as many as
 // the bucket's shared memory fits on trees of M = 7 at RP = 32 (five, four
-// and three for caps 32, 40 and 48).  Left to itself the compiler spends 86
-// to 110 registers a thread on the Cholesky's register-resident panel, which
-// holds every bucket to two CTAs per SM.
+// and three for caps 32, 40 and 48).  Left to itself the compiler spends up to
+// 110 registers a thread, which holds every bucket to two CTAs per SM.
 template <typename T, int RP, int NMAX>
 constexpr int leafpost_min_ctas()
 {
