@@ -75,8 +75,8 @@ def parse():
                    help="skip the clustered 64-theta object of the default grid line")
     p.add_argument("--launch", default=None, metavar="ROWS,STAGES,BUCKETS,CONCURRENT[,QUEUE[,PRIOR]]",
                    help="pin the launch configuration (mra_set_launch) instead of running the autotuner, "
-                        "e.g. 64,1,0,1 (QUEUE 1: leaf buckets as persistent work queues; PRIOR 0/1/2: the "
-                        "prior's ancestor blocks in one or two buffers by occupancy, one, two)")
+                        "e.g. 64,1,0,1 (QUEUE 1: leaf buckets as persistent work queues; PRIOR 0/1/2/3: the "
+                        "prior's ancestor blocks staged by occupancy, in one buffer, two, two blocks at a time)")
     p.add_argument("--workload", default="grid", choices=["grid", "clustered", "massive", "swaths", "modis18"],
                    help="grid: n=131,072, 1 theta per call (default); clustered: n=2,097,152 with 64 theta per "
                         "call; massive: n=47,185,920, 1 theta per call; swaths: n=2,439,827, J=2, M=14, "

@@ -175,9 +175,11 @@ typedef struct {
     int leaf_queue;       /* 1: each leaf-size bucket runs as a persistent work-queue kernel (CTAs resident at
                              once take the leaves, largest first, through an atomic counter) instead of one CTA
                              per leaf; the same results bit for bit, so the autotuner tries both */
-    int prior_stages;     /* ancestor blocks of the prior staged in 0: one or two buffers per level by occupancy
-                             (one where it fits more CTAs per SM and saves a wave), 1: one buffer, 2: two
-                             where they fit (the next level prefetched); the same results bit for bit */
+    int prior_stages;     /* ancestor blocks of the prior staged in 0: a form per level chosen by occupancy (two
+                             blocks at a time where that fits more CTAs per SM on a level of more than one
+                             wave, else one buffer where it fits more CTAs per SM and saves a wave, else two),
+                             1: one buffer, 2: two where they fit (the next level prefetched), 3: two blocks
+                             at a time; the same results bit for bit */
     int leafbasis_tensor_cores; /* MRA_MIXED: 1 runs the leaf basis's remainder products on the tensor cores
                                    (tcgen05 BF16 MMAs of five exact fixed-grid slices per value, sums exact in
                                    tensor memory, 128 rows per CTA); trees with (M - 2) x padded r_hat up to 192

@@ -365,7 +365,7 @@ struct mra_ctx {
     bool lb_tc = false;   // MRA_MIXED: leaf basis with its remainder products on the tensor cores
     bool leaf_queue = false; // shared-memory leaf buckets as persistent work-queue kernels
     bool lb_whole = false;   // leaf basis: tails of 32/64-row chunks kept in full-size chunks
-    int prior_st = 0;        // prior: 0 one or two stages by occupancy, 1 one stage, 2 two where they fit
+    int prior_st = 0;        // prior: 0 by occupancy, 1 one stage, 2 two where they fit, 3 two blocks at a time
     unsigned *d_qcnt = nullptr; // their counters: kLeafBuckets x status_cap
     BigLeaf *d_big = nullptr;
     int nbig = 0;
@@ -1800,7 +1800,7 @@ mra_status mra_autotune(mra_ctx *c, const double *theta, int reps, mra_tune_t *o
         }
     }
     const Cfg lead = bestc;
-    for (int ps : {0, 1, 2}) {
+    for (int ps : {0, 1, 2, 3}) {
         if (rs != MRA_OK || ps == lead.prior) continue;
         Cfg g = lead;
         g.prior = ps;
@@ -1853,7 +1853,7 @@ mra_status mra_set_launch(mra_ctx *c, const mra_tune_t *g)
     if (!(rows == 0 || rows == 32 || rows == kStreamRows || (rows == 64 && mixed)) || stages < 0 || stages > 2 ||
         g->bucket_set < 0 ||
         g->bucket_set > 1 || (g->bucket_set == 1 && c->nmax_small < 64) || g->prior_stages < 0 ||
-        g->prior_stages > 2) {
+        g->prior_stages > 3) {
         c->err = "launch configuration outside the candidates";
         return MRA_EINVAL;
     }

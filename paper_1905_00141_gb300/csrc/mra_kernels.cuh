@@ -1942,8 +1942,16 @@ __host__ __device__ constexpr size_t smem_leafgram_bytes(int M)
     return (size_t)2 * 2 * kGramRows * kGramTile * sizeof(T) + 64;
 }
 
+// FP32: four CTAs per SM (64 registers, no spills; 80 otherwise, which
+// allows three while the shared memory fits six)
+template <typename T>
+constexpr int leafgram_min_ctas()
+{
+    return sizeof(T) == 4 ? 4 : 1;
+}
+
 template <typename T, int RP>
-__global__ void __launch_bounds__(NT) k_leafgram(DevTree t, Work<T> w, int reg0)
+__global__ void __launch_bounds__(NT, (leafgram_min_ctas<T>())) k_leafgram(DevTree t, Work<T> w, int reg0)
 {
     constexpr int TS = kGramTile, RW = kGramRows;
     using TL = Tile<TS, TS>;

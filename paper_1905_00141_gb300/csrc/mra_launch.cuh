@@ -58,45 +58,60 @@ template <typename T, int RP> size_t smem_big(int M)
     return a > p ? a : p;
 }
 
-// Stages of ancestor blocks for level m of the prior: stages_req 1 or 2
-// forces one (two where they fit); 0 takes one stage where that fits more
-// CTAs per SM and saves a wave of the level's CTAs (the prefetch of the
-// second stage then buys less than the extra CTAs hide), else two where
-// they fit.
+// How level m of the prior stages its ancestor blocks: 1 or 2 buffers of a
+// whole level's blocks (the next level prefetched into the second), or 3: the
+// streamed kernel, two blocks at a time (kPriorPairBlocks).  stages_req 1, 2
+// or 3 forces that form (2 only where it fits); 0 decides by occupancy: the
+// streamed kernel where it fits more CTAs per SM than one buffer and the
+// level has more CTAs than one wave of the one-buffer kernel (its extra
+// barriers cost less than the extra CTAs hide), else one buffer where that
+// fits more CTAs per SM and saves a wave, else two where they fit.  All three
+// sum the same terms in the same order.
+constexpr int kPriorPairBlocks = 2;
 template <typename T, int RP>
-static int prior_stages_for(int m, long long ctas, int stages_req, size_t *done)
+static int prior_mode_for(int m, long long ctas, int stages_req, size_t *done, size_t *done_p)
 {
     const int fit = prior_stages<T, RP>(m);
-    if (stages_req == 1 || fit == 1) return 1;
+    if (stages_req == 1 || stages_req == 3) return stages_req;
     if (stages_req == 2) return fit;
     // decided once per (level, CTA count): the first pass runs uncaptured, so
     // the queries below stay out of graph capture
     static long long seen_ctas[MRA_MAXM + 1] = {0};
-    static int seen_stages[MRA_MAXM + 1] = {0};
-    if (seen_ctas[m] == ctas && seen_stages[m] > 0) return seen_stages[m];
-    if (set_smem(k_prior<T, RP>, smem_prior_bytes<T, RP>(m, 2), done)) return fit;
-    int dev = 0, sms = 0, o1 = 0, o2 = 0;
+    static int seen_mode[MRA_MAXM + 1] = {0};
+    if (seen_ctas[m] == ctas && seen_mode[m] > 0) return seen_mode[m];
+    const size_t b3 = smem_prior_stream_bytes<T, RP, kPriorPairBlocks>(m);
+    if (set_smem(k_prior<T, RP>, smem_prior_bytes<T, RP>(m, fit), done) ||
+        set_smem(k_prior<T, RP, kPriorPairBlocks>, b3, done_p))
+        return fit;
+    int dev = 0, sms = 0, o1 = 0, o2 = 0, o3 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_prior<T, RP>, NT, smem_prior_bytes<T, RP>(m, 1)) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_prior<T, RP>, NT, smem_prior_bytes<T, RP>(m, 2)) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_prior<T, RP>, NT, smem_prior_bytes<T, RP>(m, fit)) !=
             cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_prior<T, RP, kPriorPairBlocks>, NT, b3) != cudaSuccess ||
         sms <= 0 || o1 <= 0 || o2 <= 0) {
         cudaGetLastError();
         return fit;
     }
-    const long long w1 = (ctas + (long long)sms * o1 - 1) / ((long long)sms * o1);
-    const long long w2 = (ctas + (long long)sms * o2 - 1) / ((long long)sms * o2);
+    int mode;
+    if (o3 > o1 && ctas > (long long)sms * o1) {
+        mode = 3;
+    } else {
+        const long long w1 = (ctas + (long long)sms * o1 - 1) / ((long long)sms * o1);
+        const long long w2 = (ctas + (long long)sms * o2 - 1) / ((long long)sms * o2);
+        mode = (fit == 1 || w1 < w2) ? 1 : 2;
+    }
     seen_ctas[m] = ctas;
-    seen_stages[m] = w1 < w2 ? 1 : 2;
-    return seen_stages[m];
+    seen_mode[m] = mode;
+    return mode;
 }
 
 template <typename T, int RP>
 int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, int stages_req, void *stream)
 {
-    static size_t done = 0, done_s = 0;
+    static size_t done = 0, done_s = 0, done_p = 0;
     const long long nreg = (long long)(t.lvl_off[m + 1] - t.lvl_off[m]);
     if (prior_streams<T, RP>(m)) {
         const size_t sm = smem_prior_stream_bytes<T, RP, kPriorStreamBlocks>(m);
@@ -105,11 +120,17 @@ int launch_prior(const DevTree &t, const Work<T> &w, int m, int B, int stages_re
         k_prior<T, RP, kPriorStreamBlocks><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, 1);
         return (int)cudaGetLastError();
     }
-    const int stages = prior_stages_for<T, RP>(m, nreg * B, stages_req, &done);
-    const size_t sm = smem_prior_bytes<T, RP>(m, stages);
-    if (int e = set_smem(k_prior<T, RP>, sm, &done)) return e;
+    const int mode = prior_mode_for<T, RP>(m, nreg * B, stages_req, &done, &done_p);
     dim3 grid((unsigned)nreg, (unsigned)B);
-    k_prior<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, stages);
+    if (mode == 3) {
+        const size_t sm = smem_prior_stream_bytes<T, RP, kPriorPairBlocks>(m);
+        if (int e = set_smem(k_prior<T, RP, kPriorPairBlocks>, sm, &done_p)) return e;
+        k_prior<T, RP, kPriorPairBlocks><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, 1);
+        return (int)cudaGetLastError();
+    }
+    const size_t sm = smem_prior_bytes<T, RP>(m, mode);
+    if (int e = set_smem(k_prior<T, RP>, sm, &done)) return e;
+    k_prior<T, RP><<<grid, NT, sm, (cudaStream_t)stream>>>(t, w, m, mode);
     return (int)cudaGetLastError();
 }
 

@@ -411,12 +411,12 @@ def test_launch_configurations_agree_bit_for_bit(precision):
                 if r != 16:
                     g.set_launch(r, 0, 0, True, leafbasis_whole_chunks=True)
                     assert np.array_equal(g.loglik(THETAS), ref), (r, "whole chunks")
-        # the prior's ancestor blocks in one buffer, in two, or by occupancy
-        for ps in (1, 2, 0):
+        # the prior's ancestor blocks in one buffer, in two, two blocks at a time, or by occupancy
+        for ps in (1, 2, 3, 0):
             g.set_launch(prior_stages=ps)
             assert np.array_equal(g.loglik(THETAS), ref), ps
         with pytest.raises(mra.MRAError):
-            g.set_launch(prior_stages=3)
+            g.set_launch(prior_stages=4)
         rep = g.autotune(THETAS[0], reps=2)
         assert rep["tried"] >= 2 and rep["ms_best"] <= rep["ms_default"]
         assert np.array_equal(g.loglik(THETAS), ref)
