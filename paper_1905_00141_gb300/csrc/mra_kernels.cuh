@@ -854,11 +854,11 @@ __device__ void fwd_solve_vec(const F *A, int lda, const F *rs, int n, F *y)
 // registers first: each step is a scale, one shuffle and one update per lane,
 // with no shared-memory load on the chain.  By warp 0; ends with a barrier.
 template <typename F, int N>
-__device__ void fwd_solve_vec_lead(const F *A, int lda, const F *rs, int n, F *y)
+__device__ void fwd_solve_vec_lead_warp(const F *A, int lda, const F *rs, int n, F *y)
 {
     static_assert(N <= 32, "one row per lane");
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    {
+        const int lane = threadIdx.x & 31;
         F Lr[N];
 #pragma unroll
         for (int q = 0; q < N; q++) Lr[q] = (q < lane && lane < n) ? f_lead(A[q * lda + lane]) : f_of<F>(0.0);
@@ -874,6 +874,11 @@ __device__ void fwd_solve_vec_lead(const F *A, int lda, const F *rs, int n, F *y
         }
         if (lane < n) y[lane] = yl;
     }
+}
+template <typename F, int N>
+__device__ void fwd_solve_vec_lead(const F *A, int lda, const F *rs, int n, F *y)
+{
+    if (threadIdx.x < 32) fwd_solve_vec_lead_warp<F, N>(A, lda, rs, n, y);
     __syncthreads();
 }
 
@@ -962,13 +967,16 @@ __device__ void trinv_warp(const F *A, int lda, const F *rs, T *out, int ldo, in
 // own columns (col = warp + 8j, four at a time), lanes own rows; each lane
 // keeps its row of L and its reciprocal pivot in registers, and at step i the
 // owner of row i scales x_i and one shuffle broadcasts it.
+// The columns of fwd_solve_warp by the warps w0 .. w0 + nw - 1 of the CTA
+// (column col by warp w0 + col % nw); no barrier.
 template <typename T, int N, typename F>
-__device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, int cs, int ls, T *X, int ldx,
-                               int ncol, int nrow = N)
+__device__ void fwd_solve_warps(const F *A, int lda, const F *rs, const T *src, int cs, int ls, T *X, int ldx,
+                                int ncol, int nrow, int w0, int NW)
 {
     static_assert(N <= 32, "one row per lane");
-    constexpr int NW = NT / 32, CB = 4;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int CB = 4;
+    const int warp = (threadIdx.x >> 5) - w0, lane = threadIdx.x & 31;
+    if (warp < 0 || warp >= NW) return;
     T Lr[N];
 #pragma unroll
     for (int i = 0; i < N; i++) Lr[i] = (lane > i && lane < N) ? (T)f_hi(A[i * lda + lane]) : T(0);
@@ -994,6 +1002,12 @@ __device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, i
             if (col < ncol && lane < N) X[(size_t)lane * ldx + col] = x[cc];
         }
     }
+}
+template <typename T, int N, typename F>
+__device__ void fwd_solve_warp(const F *A, int lda, const F *rs, const T *src, int cs, int ls, T *X, int ldx,
+                               int ncol, int nrow = N)
+{
+    fwd_solve_warps<T, N, F>(A, lda, rs, src, cs, ls, X, ldx, ncol, nrow, 0, NT / 32);
     __syncthreads();
 }
 
@@ -2096,6 +2110,84 @@ __host__ __device__ constexpr size_t smem_up_stream_bytes(int m)
            (size_t)4 * RP * sizeof(T) + 64;
 }
 
+// dst[e] = sum over the NS children of src[s][e], e < count (a multiple of
+// 16 bytes), added in the order s = 0, 1, ..: 16-byte loads, two per child
+// and thread in flight (the children's blocks come from L2 or HBM, and one
+// region's chain of such sums is the latency of the upward pass's top levels)
+template <typename T, int NS>
+__device__ __forceinline__ void sum_children(T *dst, const T *const *src, size_t off, int count)
+{
+    constexpr int V = 16 / (int)sizeof(T);
+    const T *p[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) p[s] = src[s] + off;
+    const int nv = count / V;
+#pragma unroll 2
+    for (int e = threadIdx.x; e < nv; e += NT) {
+        T a[NS][V];
+#pragma unroll
+        for (int s = 0; s < NS; s++) ldv<T, V>(a[s], p[s] + (size_t)e * V);
+#pragma unroll
+        for (int q = 0; q < V; q++) {
+            T v = a[0][q];
+#pragma unroll
+            for (int s = 1; s < NS; s++) v += a[s][q];
+            dst[(size_t)e * V + q] = v;
+        }
+    }
+}
+
+// The parent's blocks of the upward step: for every pair p = pidx(k, l),
+// l = 1..m-1, k = 1..l, out_p = sum of the NS sources' block p minus
+// Z_k' Z_l (Z rows of RP, k-major at sZ + (k-1) RP, ld ldz).  The next pair's
+// source elements are loaded before this pair's product, so their latency
+// hides behind the FMAs; each output is formed as in one pass per pair.
+template <typename T, int RP, int NS>
+__device__ __forceinline__ void up_parent_blocks(T *out, const T *const *blk, const T *sZ, int ldz, int m)
+{
+    using TL = Tile<RP, RP>;
+    constexpr int B2 = RP * RP;
+    const int i0 = TL::r0(), j0 = TL::c0();
+    const int np = npairs(m - 1);
+    T cur[NS][TL::RT][TL::CT], nxt[NS][TL::RT][TL::CT];
+    auto load = [&](T (&v)[NS][TL::RT][TL::CT], int p) {
+#pragma unroll
+        for (int s = 0; s < NS; s++)
+#pragma unroll
+            for (int r = 0; r < TL::RT; r++)
+                ldv<T, TL::CT>(v[s][r], blk[s] + (size_t)p * B2 + (i0 + r) * RP + j0);
+    };
+    if (np > 0) load(cur, 0);
+    int k = 1, l = 1;
+    for (int p = 0; p < np; p++) {
+        if (p + 1 < np) load(nxt, p + 1);
+        T acc[TL::RT][TL::CT];
+        tile_zero(acc);
+        tile_fma<T, RP, RP>(acc, sZ + (k - 1) * RP, ldz, sZ + (l - 1) * RP, ldz, RP);
+#pragma unroll
+        for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+            for (int c = 0; c < TL::CT; c++) {
+                T v = cur[0][r][c];
+#pragma unroll
+                for (int s = 1; s < NS; s++) v += cur[s][r][c];
+                out[(size_t)p * B2 + (i0 + r) * RP + j0 + c] = v - acc[r][c];
+            }
+        if (p + 1 < np) {
+#pragma unroll
+            for (int s = 0; s < NS; s++)
+#pragma unroll
+                for (int r = 0; r < TL::RT; r++)
+#pragma unroll
+                    for (int c = 0; c < TL::CT; c++) cur[s][r][c] = nxt[s][r][c];
+        }
+        if (++k > l) {
+            l++;
+            k = 1;
+        }
+    }
+}
+
 template <typename T, int RP, int KB = 0>
 __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0)
 {
@@ -2152,13 +2244,12 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
     if (direct) {
         copy_g2s_async(sC, blk[0] + f0off, nfirst * B2);
         cp_async_commit();
+    } else if (nsrc == 4) {
+        sum_children<T, 4>(sC, blk, f0off, nfirst * B2);
+    } else if (nsrc == 2) {
+        sum_children<T, 2>(sC, blk, f0off, nfirst * B2);
     } else {
-#pragma unroll 4
-        for (int e = tid; e < nfirst * B2; e += NT) {
-            T v = blk[0][f0off + e];
-            for (int s = 1; s < nsrc; s++) v += blk[s][f0off + e];
-            sC[e] = v;
-        }
+        sum_children<T, 1>(sC, blk, f0off, nfirst * B2);
     }
     for (int e = tid; e < m * RP; e += NT) {
         double v = wv[0][e];
@@ -2210,10 +2301,17 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
             __syncthreads();
             fwd_solve_warp<T, RP>(sL, RP + 1, srs, stg, RP, 1, sZ + (size_t)k0 * RP, ldz, nb * RP);
         }
+        fwd_solve_vec_lead<F, RP>(sL, RP + 1, srs, RP, sz);
     } else {
-        fwd_solve_warp<T, RP>(sL, RP + 1, srs, sC, RP, 1, sZ, ldz, ncol);
+        // the vector solve (a 32-step chain) on warp 0 beside the columns of Z
+        // on the other warps: the same operations on each column and on z
+        __syncwarp();
+        if (tid < 32)
+            fwd_solve_vec_lead_warp<F, RP>(sL, RP + 1, srs, RP, sz);
+        else
+            fwd_solve_warps<T, RP>(sL, RP + 1, srs, sC, RP, 1, sZ, ldz, ncol, RP, 1, NT / 32 - 1);
+        __syncthreads();
     }
-    fwd_solve_vec_lead<F, RP>(sL, RP + 1, srs, RP, sz);
     if (tid < 32) {
         F q = tid < RP ? f_sqr(sz[tid]) : f_of<F>(0.0);
         q = warp_sum_f(q);
@@ -2242,34 +2340,13 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
     }
     if (m > 1) {
         T *out = w.Atil[m] + (size_t)b * w.Atil_stride[m] + (size_t)io * npo * B2;
-        const int i0 = TL::r0(), j0 = TL::c0();
-        // pair p = pidx(k, l), l = 1..m-1, k = 1..l, in order; each thread's source
-        // elements are loaded before its product so the loads overlap the FMAs
-        int p = 0;
-        for (int l = 1; l <= m - 1; l++) {
-            for (int k = 1; k <= l; k++, p++) {
-                T v[TL::RT][TL::CT];
-#pragma unroll
-                for (int r = 0; r < TL::RT; r++) {
-                    const size_t e = (size_t)p * B2 + (i0 + r) * RP + j0;
-                    ldv<T, TL::CT>(v[r], blk[0] + e);
-                    for (int s = 1; s < nsrc; s++) {
-                        T u[TL::CT];
-                        ldv<T, TL::CT>(u, blk[s] + e);
-#pragma unroll
-                        for (int c = 0; c < TL::CT; c++) v[r][c] += u[c];
-                    }
-                }
-                T acc[TL::RT][TL::CT];
-                tile_zero(acc);
-                tile_fma<T, RP, RP>(acc, sZ + (k - 1) * RP, ldz, sZ + (l - 1) * RP, ldz, RP);
-#pragma unroll
-                for (int r = 0; r < TL::RT; r++)
-#pragma unroll
-                    for (int c = 0; c < TL::CT; c++)
-                        out[(size_t)p * B2 + (i0 + r) * RP + j0 + c] = v[r][c] - acc[r][c];
-            }
-        }
+        // pair p = pidx(k, l), l = 1..m-1, k = 1..l, in order
+        if (nsrc == 4)
+            up_parent_blocks<T, RP, 4>(out, blk, sZ, ldz, m);
+        else if (nsrc == 2)
+            up_parent_blocks<T, RP, 2>(out, blk, sZ, ldz, m);
+        else
+            up_parent_blocks<T, RP, 1>(out, blk, sZ, ldz, m);
         double *wo = w.Atil_w[m] + (size_t)b * w.Atilw_stride[m] + (size_t)io * (m - 1) * RP;
         for (int e = tid; e < (m - 1) * RP; e += NT) {
             F acc = f_of<F>(0.0);
