@@ -204,7 +204,7 @@ __host__ __device__ constexpr size_t smem_big_potrf_bytes(int M)
 // Step k, diagonal tile: factor, log-determinant, and the diagonal solves of
 // the two right-hand sides.
 template <typename T, int RP>
-__global__ void __launch_bounds__(NT) k_big_potrf(DevTree t, Work<T> w, const BigLeaf *leaves, const BigTile *items,
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 4 : 1)) k_big_potrf(DevTree t, Work<T> w, const BigLeaf *leaves, const BigTile *items,
                                                   int k)
 {
     using F = typename FacT<T>::type;

@@ -1121,8 +1121,20 @@ __host__ __device__ constexpr size_t smem_prior_stream_bytes(int m)
            4 * RP * sizeof(T) + (size_t)((m - 1) + KB + 1) * RP * RP * sizeof(T) + RP * sizeof(T) + 64;
 }
 
+// CTAs per SM the registers must allow: in FP32 five for the two-block
+// kernel, which exists to fit five where shared memory allows them, six for
+// the whole-staged one (40 registers; small-RP trees fit six), one for the
+// deep levels' four-block kernel (its shared memory holds one); FP64 four.
+// (A kernel declared without a CTA count gets a register budget of the
+// compiler's choosing, which a count of one does not reproduce.)
+template <typename T, int KB>
+constexpr int prior_min_ctas()
+{
+    return sizeof(T) != 4 ? 4 : (KB == 2 ? 5 : (KB == 0 ? 6 : 1));
+}
+
 template <typename T, int RP, int KB = 0>
-__global__ void __launch_bounds__(NT) k_prior(DevTree t, Work<T> w, int m, int stages)
+__global__ void __launch_bounds__(NT, (prior_min_ctas<T, KB>())) k_prior(DevTree t, Work<T> w, int m, int stages)
 {
     using TL = Tile<RP, RP>;
     using F = typename FacT<T>::type;
@@ -1841,8 +1853,10 @@ __device__ __forceinline__ void leafpost_small_leaf(const DevTree &t, const Work
 template <typename T, int RP, int NMAX>
 constexpr int leafpost_min_ctas()
 {
-    if (sizeof(T) != 4) return 1;
-    return NMAX <= 32 ? 5 : (NMAX <= 40 ? 4 : (NMAX <= 48 ? 3 : 1));
+    // FP64 (shared memory fits at most three): the register counts of the
+    // kernels without a budget; the 64 cap runs one CTA per SM
+    if (sizeof(T) != 4) return NMAX <= 48 ? 3 : 1;
+    return NMAX <= 32 ? 5 : (NMAX <= 40 ? 4 : 3);
 }
 
 // One CTA per leaf of the list (grid.x), theta grid.y.
@@ -1957,11 +1971,11 @@ __host__ __device__ constexpr size_t smem_leafgram_bytes(int M)
 }
 
 // FP32: four CTAs per SM (64 registers, no spills; 80 otherwise, which
-// allows three while the shared memory fits six)
+// allows three while the shared memory fits six); FP64: two
 template <typename T>
 constexpr int leafgram_min_ctas()
 {
-    return sizeof(T) == 4 ? 4 : 1;
+    return sizeof(T) == 4 ? 4 : 2;
 }
 
 template <typename T, int RP>
@@ -2291,12 +2305,12 @@ __global__ void __launch_bounds__(NT) k_up(DevTree t, Work<T> w, int m, int reg0
                 copy_g2s_async(stg, blk[0] + off, nb * B2);
                 cp_async_commit();
                 cp_async_wait<0>();
+            } else if (nsrc == 4) {
+                sum_children<T, 4>(stg, blk, off, nb * B2);
+            } else if (nsrc == 2) {
+                sum_children<T, 2>(stg, blk, off, nb * B2);
             } else {
-                for (int e = tid; e < nb * B2; e += NT) {
-                    T v = blk[0][off + e];
-                    for (int s = 1; s < nsrc; s++) v += blk[s][off + e];
-                    stg[e] = v;
-                }
+                sum_children<T, 1>(stg, blk, off, nb * B2);
             }
             __syncthreads();
             fwd_solve_warp<T, RP>(sL, RP + 1, srs, stg, RP, 1, sZ + (size_t)k0 * RP, ldz, nb * RP);
