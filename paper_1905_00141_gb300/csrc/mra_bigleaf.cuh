@@ -280,11 +280,14 @@ constexpr int kBigUcChunk = 64;
 template <typename T, int RP>
 __host__ __device__ constexpr size_t smem_big_trsm_bytes()
 {
-    return (size_t)2 * TB * (TB + 1) * 8 + (size_t)2 * TB * 8 + (size_t)TB * kBigUcChunk * sizeof(T) + 64;
+    return (size_t)2 * TB * (TB + 1) * 8 + (size_t)2 * TB * 8 + (size_t)2 * TB * kBigUcChunk * sizeof(T) + 64;
 }
 
 // Step k, tile column below the diagonal: L_ik = V_ik L_kk^{-T}, then the
-// right-hand sides of row block i take their share of block k.
+// right-hand sides of row block i take their share of block k.  The rows of
+// Y_k (final since step k's diagonal tile) are staged kBigUcChunk columns at
+// a time into two buffers by asynchronous copies, the first before the
+// solve, each next one while the previous is used.
 template <typename T, int RP>
 __global__ void __launch_bounds__(NT) k_big_trsm(DevTree t, Work<T> w, const BigLeaf *leaves, const BigTile *items,
                                                  int k)
@@ -302,7 +305,26 @@ __global__ void __launch_bounds__(NT) k_big_trsm(DevTree t, Work<T> w, const Big
     F *sA = sK + TB * (TB + 1);     // tile (i,k), then L_ik
     F *srs = sA + TB * (TB + 1);    // TB
     F *syk = srs + TB;              // TB
-    T *sY = (T *)(syk + TB);        // TB x kBigUcChunk
+    T *sY = (T *)(syk + TB);        // 2 x TB x kBigUcChunk
+    T *Ui = w.U + (size_t)b * w.U_stride + (size_t)(v.o0 + ri) * UC;
+    const T *Yk = w.U + (size_t)b * w.U_stride + (size_t)(v.o0 + rk) * UC;
+    // columns [cb, cb + kBigUcChunk) of the nk rows of Y_k into buffer q, zeros
+    // past the tile and past UC (a multiple of 16 elements, so a 16-byte
+    // vector is all in or all out)
+    auto stage_y = [&](int cb, int q) {
+        constexpr int V = 16 / (int)sizeof(T), VPR = kBigUcChunk / V;
+        T *dst = sY + (size_t)q * TB * kBigUcChunk;
+        for (int e = tid; e < TB * VPR; e += NT) {
+            const int m = e / VPR, cc = (e % VPR) * V;
+            if (m < nk && cb + cc < UC)
+                cp_async16(dst + m * kBigUcChunk + cc, Yk + (size_t)m * UC + cb + cc);
+            else
+#pragma unroll
+                for (int q2 = 0; q2 < V; q2++) dst[m * kBigUcChunk + cc + q2] = T(0);
+        }
+        cp_async_commit();
+    };
+    stage_y(0, 0);
     for (int e = tid; e < nk * nk; e += NT) {
         const int m = e / nk, c = e % nk;
         if (c >= m) sK[m * (TB + 1) + c] = v.V[(size_t)(rk + m) * n + rk + c];
@@ -354,30 +376,37 @@ __global__ void __launch_bounds__(NT) k_big_trsm(DevTree t, Work<T> w, const Big
         }
     }
     // U_i -= L_ik Y_k, kBigUcChunk columns at a time
-    T *Ui = w.U + (size_t)b * w.U_stride + (size_t)(v.o0 + ri) * UC;
-    const T *Yk = w.U + (size_t)b * w.U_stride + (size_t)(v.o0 + rk) * UC;
     constexpr int CPT = TB * kBigUcChunk / NT; // outputs per thread (8)
     const int r = tid / (kBigUcChunk / CPT), c0 = (tid % (kBigUcChunk / CPT)) * CPT;
-    for (int cb = 0; cb < UC; cb += kBigUcChunk) {
-        __syncthreads();
-        for (int e = tid; e < TB * kBigUcChunk; e += NT) {
-            const int m = e / kBigUcChunk, cc = e % kBigUcChunk;
-            sY[e] = (m < nk && cb + cc < UC) ? Yk[(size_t)m * UC + cb + cc] : T(0);
+    const int nchunk = (UC + kBigUcChunk - 1) / kBigUcChunk;
+    for (int ci = 0; ci < nchunk; ci++) {
+        const int cb = ci * kBigUcChunk;
+        if (ci + 1 < nchunk) {
+            stage_y(cb + kBigUcChunk, (ci + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const T *sYc = sY + (size_t)(ci & 1) * TB * kBigUcChunk;
         if (r < ni) {
+            // this thread's U values, loaded before the products
+            T uo[CPT];
+#pragma unroll
+            for (int cc = 0; cc < CPT; cc++) uo[cc] = cb + c0 + cc < UC ? Ui[(size_t)r * UC + cb + c0 + cc] : T(0);
             T acc[CPT];
 #pragma unroll
             for (int cc = 0; cc < CPT; cc++) acc[cc] = T(0);
             for (int m = 0; m < nk; m++) {
                 const T l = (T)f_hi(sA[r * (TB + 1) + m]);
 #pragma unroll
-                for (int cc = 0; cc < CPT; cc++) acc[cc] = fma(l, sY[m * kBigUcChunk + c0 + cc], acc[cc]);
+                for (int cc = 0; cc < CPT; cc++) acc[cc] = fma(l, sYc[m * kBigUcChunk + c0 + cc], acc[cc]);
             }
 #pragma unroll
             for (int cc = 0; cc < CPT; cc++)
-                if (cb + c0 + cc < UC) Ui[(size_t)r * UC + cb + c0 + cc] -= acc[cc];
+                if (cb + c0 + cc < UC) Ui[(size_t)r * UC + cb + c0 + cc] = uo[cc] - acc[cc];
         }
+        __syncthreads();
     }
 }
 
