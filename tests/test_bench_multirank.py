@@ -62,3 +62,25 @@ def test_single_rank_rate():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.whole_job_rate(131072, 1, 200, 0.4, 1) == 131072 * 200 / 0.4
+
+
+def test_stored_accuracy_uses_only_matching_draws(monkeypatch):
+    """bench.py's accuracy of the r = 49 workloads: the stored oracle values
+    are used only for calls whose theta they hold and only when the data's
+    fingerprint matches the one stored with them."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import bench
+    import golden_values
+    rng = np.random.default_rng(5)
+    d = {"x": rng.random(50), "y": rng.random(50), "z": rng.standard_normal(50)}
+    fp = (50, float(np.sum(d["x"])), float(np.sum(d["y"])), float(np.sum(d["z"])), float(np.sum(np.abs(d["z"]))))
+    th = np.array([[1.0, 0.05, 0.01], [1.2, 0.06, 0.012]])[:, None, :]
+    ll = np.array([[-10.0], [-12.0]])
+    monkeypatch.setattr(golden_values, "golden", lambda name: [(np.array([1.2, 0.06, 0.012]), -12.5, 50, fp)])
+    acc = bench.stored_accuracy("swaths", d, th, ll, 50, "mixed")
+    assert acc["calls_checked"] == 1 and abs(acc["mixed"] - 0.5 / 50) < 1e-15
+    other = (51,) + fp[1:]
+    monkeypatch.setattr(golden_values, "golden", lambda name: [(np.array([1.2, 0.06, 0.012]), -12.5, 50, other)])
+    assert bench.stored_accuracy("swaths", d, th, ll, 50, "mixed")["against"] is None
